@@ -1,0 +1,333 @@
+#!/usr/bin/env python
+"""Benchmark of the grouped Barnes-Hut force calculation on GB300.
+
+Workload: Plummer sphere, N = 1,048,576 equal masses, theta = 0.5, N_leaf = 16,
+eps = 0.01, G = 1 (synthetic, seeded). One step = one tree walk + evaluation
+of all N particles (the fused sm_103a kernel) on the tree already resident in
+HBM; L2 is flushed (256 MiB write) before every timed step, outside the timed
+events. The line also reports:
+  e2e           the same metric through the one-shot C-ABI call with host
+                buffers (host FP64 tree build + upload + kernel + download);
+  roofline      paper-convention flops (38 per particle-particle, 70 per
+                particle-cell interaction, Sec. 3.3) per launch / kernel time,
+                against the FP32 CUDA-core peak (SMs x 128 lanes x 2 x max clock);
+  cpu_baseline  the FP64 CPU oracle on the host cores (full tree build plus a
+                bounded sample of groups, scaled to N);
+  accuracy      FP32 kernel vs FP64 oracle on sampled groups (relative RMS) and
+                vs direct summation on sampled particles (median / p99 Delta a/a).
+
+Multi-GPU (torchrun): every rank computes its own independent system
+(seed + rank); value = total particles over all ranks / max time over ranks.
+--impl reference times the CPU oracle instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1005_5384_gb300 import workloads as W  # noqa: E402
+
+METRIC = "particle forces/sec and GFLOP/s (frac of FP32 peak) at N=1M θ=0.5, at median rel err 1e-3"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="octgrav", choices=["octgrav", "reference"])
+    ap.add_argument("--n", type=int, default=1 << 20)
+    ap.add_argument("--theta", type=float, default=0.5)
+    ap.add_argument("--eps", type=float, default=0.01)
+    ap.add_argument("--n-leaf", type=int, default=16)
+    ap.add_argument("--n-group", type=int, default=64)
+    ap.add_argument("--ppl", type=int, default=2)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(a):
+    return ("plummer N=%d theta=%g N_leaf=%d N_group=%d eps=%g G=1" %
+            (a.n, a.theta, a.n_leaf, a.n_group, a.eps))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([v.strip() for v in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].lower().startswith("active"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def fp32_peak_tflops(torch):
+    """FP32 CUDA-core peak: SMs x 128 lanes x 2 flops (FMA) x max SM clock."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    except (OSError, ValueError):
+        pass
+    return sms * 128 * 2 * mhz * 1e6 / 1e12, sms, mhz
+
+
+def cpu_baseline(pos, m, a, budget_s):
+    """Oracle timed on all host cores: full tree build + forces on a group sample."""
+    import oracle as O
+    threads = O.default_threads()
+    t0 = time.perf_counter()
+    R = O.Tree(pos, m, a.n_leaf, a.n_group)
+    t_build = time.perf_counter() - t0
+    # calibrate on a small sample, then size the timed sample to the budget
+    rng = np.random.default_rng(123)
+    probe = np.sort(rng.choice(R.n_groups, size=min(R.n_groups, 64), replace=False))
+    t0 = time.perf_counter()
+    R.forces(a.eps, a.theta, groups=probe, nthreads=threads, counts=False)
+    t_probe = max(1e-6, time.perf_counter() - t0)
+    ng = int(min(R.n_groups, max(64, 64 * budget_s / t_probe)))
+    gs = np.sort(rng.choice(R.n_groups, size=ng, replace=False))
+    npart = int(R.count[R.groups[gs]].sum())
+    t0 = time.perf_counter()
+    R.forces(a.eps, a.theta, groups=gs, nthreads=threads, counts=False)
+    t_forces = time.perf_counter() - t0
+    t_total = t_build + t_forces * (a.n / npart)
+    return {"value": a.n / t_total, "unit": "forces/s", "cores": threads, "kind": "oracle",
+            "sample": "full FP64 tree build (%.2fs) + forces of %d random groups (%d particles, %.2fs), "
+                      "scaled to N=%d" % (t_build, ng, npart, t_forces, a.n),
+            "t_build_s": t_build, "t_forces_sample_s": t_forces}, R
+
+
+def accuracy(acc, pos, m, a, R):
+    import oracle as O
+    gsel = np.unique(W.sample_indices(R.n_groups, 200, seed=9))
+    ra, _, _, _, _ = R.forces(a.eps, a.theta, groups=gsel, counts=False)
+    idx = np.concatenate([R.cell_members(int(R.groups[g])) for g in gsel])
+    rms = O.rel_rms(acc[idx], ra[idx])
+    samp = W.sample_indices(a.n, 1024, seed=17)
+    ad, _ = O.direct(pos, m, a.eps, targets=samp)
+    e = O.rel_err(acc[samp], ad)
+    return {"rel_rms_vs_fp64_oracle": rms, "oracle_particles": int(len(idx)),
+            "median_rel_err_vs_direct": float(np.median(e)), "p99_rel_err_vs_direct": float(np.percentile(e, 99)),
+            "direct_sample": int(len(samp))}
+
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return
+    import oracle as O
+    pos, m = W.plummer(a.n, seed=a.seed)
+    threads = O.default_threads()
+    R = O.Tree(pos, m, a.n_leaf, a.n_group)
+    rng = np.random.default_rng(5)
+    budget = max(1.0, 120.0 / max(1, a.steps + a.warmup))
+    probe = np.sort(rng.choice(R.n_groups, size=min(R.n_groups, 64), replace=False))
+    t0 = time.perf_counter()
+    R.forces(a.eps, a.theta, groups=probe, counts=False)
+    tp = max(1e-6, time.perf_counter() - t0)
+    ng = int(min(R.n_groups, max(16, 64 * budget / tp)))
+    times = []
+    for step in range(a.warmup + a.steps):
+        gs = np.sort(rng.choice(R.n_groups, size=ng, replace=False))
+        npart = int(R.count[R.groups[gs]].sum())
+        t0 = time.perf_counter()
+        R.forces(a.eps, a.theta, groups=gs, counts=False)
+        dt = time.perf_counter() - t0
+        if step >= a.warmup:
+            times.append(dt / npart)
+    per = statistics.mean(times)
+    value = 1.0 / per
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "forces/s", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": per * a.n * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a), "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "forces/s", "cores": threads, "kind": "oracle",
+                             "sample": "%d random groups per step of the N=%d tree, forces only" % (ng, a.n)},
+            "e2e": {"value": value, "unit": "forces/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+        return
+
+    import torch
+    from paper_1005_5384_gb300 import octgrav as G
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    pos, m = W.plummer(a.n, seed=a.seed + rank)
+    G.load()
+    T = G.Tree.build(pos, m, a.n_leaf, a.n_group)
+    T.set_launch(a.ppl)
+    T.upload()
+    out = torch.empty((T.n, 4), dtype=torch.float32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    for _ in range(a.warmup):
+        T.forces_device(a.eps, a.theta, out, stream=stream)
+    torch.cuda.synchronize()
+    st = T.status()
+    if st != G.OK:
+        raise SystemExit("device status %d: %s" % (st, G.load().octgrav_last_error().decode()))
+    counts = T.interaction_counts()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    w0 = time.perf_counter()
+    for k in range(a.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        T.forces_device(a.eps, a.theta, out, stream=stream)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - w0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = [s.elapsed_time(e) for s, e in ev]
+    ms_step = statistics.mean(ms)
+    if dist:
+        tt = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_step = float(tt.item())
+    st = T.status()
+    if st != G.OK:
+        raise SystemExit("device status %d after timing" % st)
+
+    value = world * a.n / (ms_step * 1e-3)
+    peak, sms, mhz = fp32_peak_tflops(torch)
+    achieved = counts["flops"] / (ms_step * 1e-3) / 1e12
+
+    # e2e through the one-shot C-ABI call with host buffers
+    e2e_t = []
+    for k in range(a.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        acc_h, pot_h = G.forces(pos, m, a.eps, a.theta, a.n_leaf, a.n_group, stream=stream)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = statistics.mean(e2e_t[1:])
+    s = T.stats
+    h2d = 32 * a.n + 88 * s["n_cells"] + 64 * s["n_items"]
+    d2h = 16 * a.n
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "forces/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_name(a), "seed": a.seed, "particles_per_lane": a.ppl,
+                   "l2": "flushed (256 MiB write) before every timed step, outside the events",
+                   "parallelism": "replica per GPU" if world > 1 else "1 GPU"},
+        "gflops": achieved * 1e3, "frac_fp32_peak": achieved / peak,
+        "interactions": {"n_pp": counts["n_pp"], "n_pc": counts["n_pc"], "flops_per_step": counts["flops"],
+                         "flops_per_particle": counts["flops"] / a.n},
+        "e2e": {"value": world * a.n / e2e_s, "unit": "forces/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "seconds_per_step": e2e_s,
+                "path": "octgrav_forces_ex: host FP64 build + upload + kernel + download + unpermute"},
+        "gpu_launches": a.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz" % (sms, mhz),
+                     "kernel": "walk_eval_kernel (fused walk + evaluation)"},
+        "clocks": clk,
+        "wall_s_timed_loop_incl_flush": wall,
+        "tree": s,
+    }
+    if not a.no_accuracy:
+        acc = np.empty((a.n, 3))
+        perm = T.perm()
+        acc[perm] = out.cpu().numpy()[:, :3]
+        import oracle as O  # noqa: F401
+        R = None
+        if not a.no_cpu_baseline:
+            line["cpu_baseline"], R = cpu_baseline(pos, m, a, a.cpu_seconds)
+        if R is None:
+            import oracle as O
+            R = O.Tree(pos, m, a.n_leaf, a.n_group)
+        line["accuracy"] = accuracy(acc, pos, m, a, R)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

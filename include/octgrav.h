@@ -1,0 +1,176 @@
+/*
+ * octgrav.h -- C ABI of the GB300 (sm_103a) grouped Barnes-Hut force library.
+ *
+ * Method: Gaburov, Bedorf & Portegies Zwart (2010), "Gravitational tree-code
+ * on graphics processing units: implementation in CUDA". The octree, the
+ * tight boxes, boundary cubes and multipole moments are built on the host in
+ * FP64 (Sec. 2.1); the per-group tree walk that sorts cells into an
+ * interaction list (Sec. 2.2, Listings 1-2) and the evaluation of that list
+ * (Sec. 2.3, Listings 3-4) run on the GPU in one fused CUDA kernel.
+ *
+ * Conventions shared by every entry point:
+ *  - Positions are xyz-interleaved FP64 arrays of length 3*n, masses FP64 of
+ *    length n, both in the caller's ("input") order and owned by the caller.
+ *    Outputs named acc/pot are caller-owned host arrays in input order:
+ *    acc[3*i+k] = a_k of particle i, pot[i] = its potential.
+ *  - Plummer softening eps > 0, gravitational constant G (1 by default);
+ *    the self term is excluded; potentials are negative.
+ *  - Opening test (Sec. 2.2): a cell whose boundary-cube side l satisfies
+ *    l < theta * d, with d the distance between the group's tight box and
+ *    the cell's cube, is accepted as a multipole; otherwise it is opened.
+ *  - Every call returns an octgrav status (0 = OK, negative = error) and never
+ *    aborts or throws. On error, octgrav_last_error() gives a message (per
+ *    calling thread).
+ *  - stream arguments are a cudaStream_t passed as void* (NULL = the legacy
+ *    default stream). Device memory owned by a tree is allocated by the
+ *    library (cudaMalloc) on the current CUDA device and freed by
+ *    octgrav_free_tree.
+ *  - Thread safety: distinct trees may be used from distinct threads; one tree
+ *    must not be used by two threads at once.
+ */
+#ifndef OCTGRAV_H
+#define OCTGRAV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OCTGRAV_OK 0
+#define OCTGRAV_ERR_ARG (-1)       /* invalid argument (sizes, eps <= 0, theta < 0, ...) */
+#define OCTGRAV_ERR_CUDA (-2)      /* a CUDA runtime call failed (message has the name) */
+#define OCTGRAV_ERR_OOM (-3)       /* host or device allocation failed */
+#define OCTGRAV_ERR_STACK (-4)     /* a walk overflowed its on-chip node stack */
+#define OCTGRAV_ERR_LIST (-5)      /* a capture buffer (debug lists) was too small */
+#define OCTGRAV_ERR_TIMEOUT (-6)   /* a bounded device-side wait ran out; results invalid */
+#define OCTGRAV_ERR_NONFINITE (-7) /* NaN/Inf in positions or masses, or a negative mass */
+#define OCTGRAV_ERR_STATE (-8)     /* call order violated (e.g. counts before any launch) */
+#define OCTGRAV_ERR_INDEX (-9)     /* a walk met a cell index outside the tree (corrupt tree) */
+
+#define OCTGRAV_MAX_DEPTH 21       /* octree depth limit (Morton keys fit one 64-bit word) */
+#define OCTGRAV_MAX_ITEM 64        /* particles evaluated by one warp (larger groups are split) */
+
+typedef struct octgrav_tree octgrav_tree; /* opaque, library-owned */
+
+/* Build the octree of one system on the host in FP64 (Sec. 2.1).
+ *   pos[3n], mass[n]: input order, caller-owned, only read during the call.
+ *   n >= 1; 1 <= n_leaf (a leaf holds at most n_leaf particles unless it sits
+ *   at depth OCTGRAV_MAX_DEPTH); n_group >= n_leaf (groups are the largest
+ *   cells holding at most n_group particles, Sec. 2.1-2.2).
+ *   *out receives a new tree; free it with octgrav_free_tree.
+ * No device work is done. Errors: ERR_ARG, ERR_NONFINITE, ERR_OOM. */
+int octgrav_build_tree(const double *pos, const double *mass, int64_t n, int n_leaf,
+                       int n_group, octgrav_tree **out);
+
+/* Build one tree holding n_sys independent systems (the batched form).
+ * System s owns particles offsets[s] .. offsets[s+1]-1 of pos/mass
+ * (offsets has n_sys+1 entries, offsets[0] = 0, strictly increasing).
+ * Each system gets its own octree; all systems share one set of device
+ * arrays and are walked by one kernel launch. Errors as octgrav_build_tree. */
+int octgrav_build_batch(int n_sys, const int64_t *offsets, const double *pos,
+                        const double *mass, int n_leaf, int n_group, octgrav_tree **out);
+
+/* Copy the tree's device arrays to the current CUDA device (library-owned
+ * memory), asynchronously on stream. Called implicitly by the force calls
+ * when needed. Errors: ERR_CUDA, ERR_OOM. */
+int octgrav_tree_upload(octgrav_tree *t, void *stream);
+
+/* Tree walk + evaluation on the GPU, asynchronous on stream (Sec. 2.2-2.3).
+ *   acc4_dev: device array of 4*n floats (caller-owned, e.g. a torch tensor),
+ *   written in TREE order: (a_x, a_y, a_z, phi) per particle; map to input
+ *   order with octgrav_tree_perm.
+ *   eps > 0, theta >= 0, G finite. For a batched tree the values apply to every
+ *   system unless octgrav_set_system_params was called.
+ * Launches exactly one kernel. Device-side failures (stack overflow, timeout)
+ * are recorded in a status word read by octgrav_status. Errors: ERR_ARG,
+ * ERR_CUDA. */
+int octgrav_forces_device(octgrav_tree *t, double eps, double theta, double G, float *acc4_dev,
+                          void *stream);
+
+/* Per-system eps and theta for a batched tree (arrays of n_sys entries);
+ * used by later octgrav_forces_device / octgrav_forces_tree calls, whose
+ * scalar eps/theta arguments are then ignored. Pass NULL to clear.
+ * Errors: ERR_ARG. */
+int octgrav_set_system_params(octgrav_tree *t, const double *eps, const double *theta);
+
+/* Forces with host outputs in input order: uploads if needed, launches,
+ * copies the result back, waits for the stream and checks the device status.
+ *   acc[3n], pot[n] (pot may be NULL). Errors: ERR_ARG, ERR_CUDA, ERR_STACK,
+ *   ERR_TIMEOUT, ERR_INDEX. */
+int octgrav_forces_tree(octgrav_tree *t, double eps, double theta, double G, double *acc,
+                        double *pot, void *stream);
+
+/* One-shot call: build (n_group = n_leaf), upload, forces, free, on the
+ * default stream with G = 1. Device buffers are cached between calls on the
+ * calling thread's current device. */
+int octgrav_forces(const double *pos, const double *mass, int64_t n, double eps, double theta,
+                   int n_leaf, double *acc, double *pot);
+
+/* octgrav_forces with every knob: G, n_group and stream. */
+int octgrav_forces_ex(const double *pos, const double *mass, int64_t n, double eps, double theta,
+                      double G, int n_leaf, int n_group, double *acc, double *pot, void *stream);
+
+/* Wait for stream and return the status of the last launch on this tree:
+ * OK, ERR_STACK, ERR_TIMEOUT or ERR_INDEX. Clears nothing. */
+int octgrav_status(octgrav_tree *t, void *stream);
+
+/* Tree statistics: out[0..n_out) receives, in this order, n (particles),
+ * n_cells, n_leaves, n_groups, n_items (warp work items), depth reached,
+ * n_sys, max group size. */
+int octgrav_tree_stats(const octgrav_tree *t, int64_t *out, int n_out);
+
+/* perm[k] = input index of the particle at tree position k (n entries). */
+int octgrav_tree_perm(const octgrav_tree *t, int64_t *perm);
+
+/* Layout-independent cell keys: key = (1 << 3*depth) | octant path, in the
+ * library's cell order (n_cells entries). In a batched tree keys restart in
+ * every system; octgrav_item_info's sys field tells the systems apart. */
+int octgrav_tree_cell_keys(const octgrav_tree *t, uint64_t *keys);
+
+/* FP64 cell properties in the library's cell order (n_cells entries each;
+ * any pointer may be NULL): tight box bmin[3], bmax[3], boundary cube
+ * cube[4] = (centre xyz, half side), mass, centre of mass com[3], second
+ * moments S[6] = (xx, yy, zz, xy, xz, yz) about the centre of mass, and the
+ * particle count (Sec. 2.1, Fig. 1). */
+int octgrav_tree_cell_props(const octgrav_tree *t, double *bmin, double *bmax, double *cube,
+                            double *mass, double *com, double *S, int64_t *count);
+
+/* Per work item: key of its group cell, first tree position, particle count,
+ * system index (arrays of n_items entries; any may be NULL). */
+int octgrav_item_info(const octgrav_tree *t, uint64_t *group_key, int64_t *first,
+                      int32_t *count, int32_t *sys);
+
+/* Interaction counts of the last launch (waits for stream):
+ * out[0] = sum over particles of particle-particle interactions (n_pp),
+ * out[1] = sum over particles of particle-cell interactions (n_pc),
+ * out[2] = flops by the paper's convention, 38 n_pp + 70 n_pc (Sec. 3.3). */
+int octgrav_interaction_counts(octgrav_tree *t, int64_t *out, void *stream);
+
+/* Test hook: run the fused kernel once in capture mode and return each work
+ * item's interaction lists as cell keys. cell_keys/leaf_keys are host arrays
+ * of n_items*cap entries (row = item); n_cell/n_leaf receive the true list
+ * lengths. A list longer than cap is truncated and the call returns
+ * ERR_LIST. Synchronous. */
+int octgrav_debug_lists(octgrav_tree *t, double theta, int cap, uint64_t *cell_keys,
+                        int32_t *n_cell, uint64_t *leaf_keys, int32_t *n_leaf, void *stream);
+
+/* Choose the kernel variant: particles per lane (1 or 2; work items hold at
+ * most 32*ppl particles) and CTAs per SM (0 = as many as fit). Applies to
+ * later launches on this tree; n_items may change. Errors: ERR_ARG. */
+int octgrav_set_launch(octgrav_tree *t, int particles_per_lane, int ctas_per_sm);
+
+void octgrav_free_tree(octgrav_tree *t);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *octgrav_last_error(void);
+
+/* Library version (major*10000 + minor*100 + patch). */
+int octgrav_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OCTGRAV_H */

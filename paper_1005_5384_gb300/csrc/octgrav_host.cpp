@@ -1,0 +1,1079 @@
+// octgrav_host.cpp -- host side of the GB300 tree-code library: FP64 octree
+// build, cell properties and groups (Sec. 2.1), device-array layout, upload,
+// launch and the C ABI declared in include/octgrav.h.
+//
+// Tree definition (shared with any independent implementation):
+//  - root cube: centre = centre of the bounding box of the system, side =
+//    longest box side * (1 + 2^-20) (1.0 when all particles coincide);
+//  - quantised coordinate q = floor((x - lo) / side * 2^21) clamped to
+//    [0, 2^21 - 1]; the octant of a depth-L cell's child is bit (20 - L) of q
+//    on each axis (x = octant bit 0), so cells are Morton-key prefixes;
+//  - a cell is a leaf when it holds <= n_leaf particles or has depth 21;
+//  - groups are the cells reached first from the root that are leaves or hold
+//    <= n_group particles (Sec. 2.1-2.2);
+//  - per cell: tight box, boundary cube (centre = box centre, half side = half
+//    the longest box side, Fig. 1), mass, centre of mass and second moments.
+// The build sorts particles by Morton key (parallel LSD radix sort), splits
+// key ranges level by level, and combines moments bottom-up with the
+// parallel-axis theorem, all in FP64. Compile with -ffp-contract=off.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/octgrav.h"
+#include "octgrav_internal.h"
+
+namespace {
+
+constexpr int kMaxDepth = OCTGRAV_MAX_DEPTH;
+
+// ---------------------------------------------------------------- errors
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CUDA_TRY(call)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(OCTGRAV_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));     \
+  } while (0)
+
+// ---------------------------------------------------------------- thread pool
+
+class Pool {
+ public:
+  static Pool& get() {
+    static Pool p;
+    return p;
+  }
+  int size() const { return static_cast<int>(threads_.size()) + 1; }
+
+  // Run fn(chunk) for chunk in [0, nchunks) on all workers and the caller.
+  void run(int nchunks, const std::function<void(int)>& fn) {
+    if (nchunks <= 0) return;
+    if (threads_.empty() || nchunks == 1 || in_pool_) {
+      for (int c = 0; c < nchunks; ++c) fn(c);
+      return;
+    }
+    std::unique_lock<std::mutex> lk(run_mu_);  // one parallel region at a time
+    {
+      std::lock_guard<std::mutex> g(mu_);
+      job_ = &fn;
+      nchunks_ = nchunks;
+      next_.store(0);
+      pending_ = static_cast<int>(threads_.size());
+      ++gen_;
+    }
+    cv_.notify_all();
+    work();
+    std::unique_lock<std::mutex> g(mu_);
+    done_cv_.wait(g, [&] { return pending_ == 0; });
+    job_ = nullptr;
+  }
+
+ private:
+  Pool() {
+    unsigned hc = std::thread::hardware_concurrency();
+    int n = static_cast<int>(hc ? hc : 1);
+    if (const char* e = getenv("OCTGRAV_THREADS")) n = std::max(1, atoi(e));
+    n = std::min(n, 64);
+    for (int t = 1; t < n; ++t) threads_.emplace_back([this] { loop(); });
+  }
+  ~Pool() {
+    {
+      std::lock_guard<std::mutex> g(mu_);
+      stop_ = true;
+      ++gen_;
+    }
+    cv_.notify_all();
+    for (auto& t : threads_) t.join();
+  }
+  void work() {
+    in_pool_ = true;
+    for (;;) {
+      int c = next_.fetch_add(1);
+      if (c >= nchunks_) break;
+      (*job_)(c);
+    }
+    in_pool_ = false;
+  }
+  void loop() {
+    uint64_t seen = 0;
+    for (;;) {
+      {
+        std::unique_lock<std::mutex> g(mu_);
+        cv_.wait(g, [&] { return gen_ != seen; });
+        seen = gen_;
+        if (stop_) return;
+      }
+      work();
+      {
+        std::lock_guard<std::mutex> g(mu_);
+        if (--pending_ == 0) done_cv_.notify_all();
+      }
+    }
+  }
+  std::vector<std::thread> threads_;
+  std::mutex mu_, run_mu_;
+  std::condition_variable cv_, done_cv_;
+  const std::function<void(int)>* job_ = nullptr;
+  int nchunks_ = 0;
+  std::atomic<int> next_{0};
+  int pending_ = 0;
+  uint64_t gen_ = 0;
+  bool stop_ = false;
+  static thread_local bool in_pool_;
+};
+thread_local bool Pool::in_pool_ = false;
+
+// parallel_for over [0, n) in chunks of at least `grain` elements.
+void parallel_for(int64_t n, int64_t grain, const std::function<void(int64_t, int64_t)>& fn) {
+  if (n <= 0) return;
+  Pool& P = Pool::get();
+  int64_t chunks = std::min<int64_t>((n + grain - 1) / grain, 8 * P.size());
+  if (chunks <= 1) {
+    fn(0, n);
+    return;
+  }
+  const int64_t step = (n + chunks - 1) / chunks;
+  P.run(static_cast<int>(chunks), [&](int c) {
+    int64_t lo = c * step, hi = std::min(n, lo + step);
+    if (lo < hi) fn(lo, hi);
+  });
+}
+
+// ---------------------------------------------------------------- Morton keys
+
+inline uint64_t spread21(uint64_t v) {
+  v &= 0x1fffffull;
+  v = (v | v << 32) & 0x1f00000000ffffull;
+  v = (v | v << 16) & 0x1f0000ff0000ffull;
+  v = (v | v << 8) & 0x100f00f00f00f00full;
+  v = (v | v << 4) & 0x10c30c30c30c30c3ull;
+  v = (v | v << 2) & 0x1249249249249249ull;
+  return v;
+}
+
+// Stable LSD radix sort of (key, val) by key (63 significant bits, 7 x 9-bit digits).
+void radix_sort(std::vector<uint64_t>& key, std::vector<uint32_t>& val, bool parallel) {
+  const int64_t n = static_cast<int64_t>(key.size());
+  std::vector<uint64_t> k2(n);
+  std::vector<uint32_t> v2(n);
+  constexpr int BITS = 9, B = 1 << BITS;
+  const int T = parallel ? std::max(1, std::min<int>(Pool::get().size(), static_cast<int>(n / 65536))) : 1;
+  std::vector<int64_t> hist(static_cast<size_t>(T) * B);
+  const int64_t step = (n + T - 1) / T;
+  for (int pass = 0; pass < 7; ++pass) {
+    const int sh = pass * BITS;
+    auto body_hist = [&](int t) {
+      int64_t* h = &hist[static_cast<size_t>(t) * B];
+      std::fill(h, h + B, 0);
+      const int64_t lo = t * step, hi = std::min(n, lo + step);
+      for (int64_t i = lo; i < hi; ++i) ++h[(key[i] >> sh) & (B - 1)];
+    };
+    if (T > 1) Pool::get().run(T, body_hist); else body_hist(0);
+    int64_t off = 0;
+    for (int d = 0; d < B; ++d)
+      for (int t = 0; t < T; ++t) {
+        int64_t c = hist[static_cast<size_t>(t) * B + d];
+        hist[static_cast<size_t>(t) * B + d] = off;
+        off += c;
+      }
+    auto body_scatter = [&](int t) {
+      int64_t* h = &hist[static_cast<size_t>(t) * B];
+      const int64_t lo = t * step, hi = std::min(n, lo + step);
+      for (int64_t i = lo; i < hi; ++i) {
+        int64_t dst = h[(key[i] >> sh) & (B - 1)]++;
+        k2[dst] = key[i];
+        v2[dst] = val[i];
+      }
+    };
+    if (T > 1) Pool::get().run(T, body_scatter); else body_scatter(0);
+    key.swap(k2);
+    val.swap(v2);
+  }
+}
+
+// ---------------------------------------------------------------- one system
+
+struct SysTree {
+  int64_t n = 0;
+  std::vector<uint32_t> perm;  // tree position -> index within the system
+  std::vector<uint64_t> code;  // Morton code per tree position
+  std::vector<double> x;       // 3 per tree position
+  std::vector<double> m;
+  // cells in breadth-first order (children of a node are contiguous)
+  std::vector<uint64_t> key;
+  std::vector<int32_t> depth, parent, first_child, n_child;
+  std::vector<int64_t> pfirst, pcount;
+  std::vector<double> bmin, bmax, cube, M, com, S;  // 3, 3, 4, 1, 3, 6 per cell
+  std::vector<int32_t> groups;                      // cell index, tree (Morton) order
+  int depth_reached = 0;
+  int64_t max_group = 0;
+  int64_t n_leaves = 0;
+};
+
+inline int octant_at(uint64_t code, int child_depth) {
+  return static_cast<int>((code >> (3 * (kMaxDepth - child_depth))) & 7);
+}
+
+int build_system(const double* pos, const double* mass, int64_t n, int n_leaf, int n_group,
+                 bool parallel, SysTree& T) {
+  T.n = n;
+  const int64_t grain = parallel ? 16384 : (int64_t)1 << 62;
+  // ---- bounding box and root cube
+  double mn[3] = {pos[0], pos[1], pos[2]}, mx[3] = {pos[0], pos[1], pos[2]};
+  {
+    const int64_t chunks = parallel ? std::max<int64_t>(1, std::min<int64_t>(64, n / 65536)) : 1;
+    std::vector<double> part(chunks * 6);
+    const int64_t step = (n + chunks - 1) / chunks;
+    auto body = [&](int c) {
+      double a[3] = {pos[0], pos[1], pos[2]}, b[3] = {pos[0], pos[1], pos[2]};
+      for (int64_t i = c * step; i < std::min(n, (c + 1) * step); ++i)
+        for (int d = 0; d < 3; ++d) {
+          const double v = pos[3 * i + d];
+          if (v < a[d]) a[d] = v;
+          if (v > b[d]) b[d] = v;
+        }
+      for (int d = 0; d < 3; ++d) {
+        part[6 * c + d] = a[d];
+        part[6 * c + 3 + d] = b[d];
+      }
+    };
+    if (chunks > 1) Pool::get().run(static_cast<int>(chunks), body); else body(0);
+    for (int64_t c = 0; c < chunks; ++c)
+      for (int d = 0; d < 3; ++d) {
+        mn[d] = std::min(mn[d], part[6 * c + d]);
+        mx[d] = std::max(mx[d], part[6 * c + 3 + d]);
+      }
+  }
+  double ext = mx[0] - mn[0];
+  if (mx[1] - mn[1] > ext) ext = mx[1] - mn[1];
+  if (mx[2] - mn[2] > ext) ext = mx[2] - mn[2];
+  if (!(ext > 0)) ext = 1.0;
+  const double side = ext * (1.0 + 1.0 / 1048576.0);
+  double lo[3];
+  for (int d = 0; d < 3; ++d) lo[d] = (mn[d] + mx[d]) * 0.5 - side * 0.5;
+  const double scale = std::ldexp(1.0, kMaxDepth);
+  const uint64_t qmax = (1ull << kMaxDepth) - 1;
+
+  // ---- Morton codes and sort
+  std::vector<uint64_t> code(n);
+  std::vector<uint32_t> idx(n);
+  parallel_for(n, grain, [&](int64_t a, int64_t b) {
+    for (int64_t i = a; i < b; ++i) {
+      uint64_t q[3];
+      for (int d = 0; d < 3; ++d) {
+        const double u = (pos[3 * i + d] - lo[d]) / side;
+        const double v = std::floor(u * scale);
+        q[d] = v <= 0 ? 0 : (v >= static_cast<double>(qmax) ? qmax : static_cast<uint64_t>(v));
+      }
+      code[i] = spread21(q[0]) | (spread21(q[1]) << 1) | (spread21(q[2]) << 2);
+      idx[i] = static_cast<uint32_t>(i);
+    }
+  });
+  radix_sort(code, idx, parallel);
+  T.perm = std::move(idx);
+  T.code = std::move(code);
+  T.x.resize(3 * n);
+  T.m.resize(n);
+  parallel_for(n, grain, [&](int64_t a, int64_t b) {
+    for (int64_t t = a; t < b; ++t) {
+      const int64_t i = T.perm[t];
+      T.x[3 * t] = pos[3 * i];
+      T.x[3 * t + 1] = pos[3 * i + 1];
+      T.x[3 * t + 2] = pos[3 * i + 2];
+      T.m[t] = mass[i];
+    }
+  });
+
+  // ---- cells, level by level
+  auto push_cell = [&](uint64_t key, int depth, int32_t parent, int64_t pf, int64_t pc) {
+    T.key.push_back(key);
+    T.depth.push_back(depth);
+    T.parent.push_back(parent);
+    T.first_child.push_back(-1);
+    T.n_child.push_back(0);
+    T.pfirst.push_back(pf);
+    T.pcount.push_back(pc);
+  };
+  push_cell(1, 0, -1, 0, n);
+  std::vector<int64_t> level_begin = {0};
+  std::vector<int64_t> splits;  // 9 per cell of the level being split
+  for (int L = 0;; ++L) {
+    const int64_t lb = level_begin.back(), le = static_cast<int64_t>(T.key.size());
+    if (lb == le) break;
+    const int64_t nl = le - lb;
+    splits.assign(9 * nl, 0);
+    std::vector<int32_t> nch(nl, 0);
+    parallel_for(nl, parallel ? 512 : (int64_t)1 << 62, [&](int64_t a, int64_t b) {
+      for (int64_t k = a; k < b; ++k) {
+        const int64_t c = lb + k;
+        const int64_t f = T.pfirst[c], cnt = T.pcount[c];
+        int64_t* sp = &splits[9 * k];
+        if (cnt <= n_leaf || L >= kMaxDepth) continue;
+        sp[0] = f;
+        sp[8] = f + cnt;
+        const uint64_t* base = T.code.data();
+        for (int o = 1; o < 8; ++o) {
+          // first position whose child octant is >= o (octants ascend inside a cell)
+          const uint64_t* it = std::partition_point(base + sp[o - 1], base + f + cnt,
+                                                    [&](uint64_t cd) { return octant_at(cd, L + 1) < o; });
+          sp[o] = it - base;
+        }
+        int k8 = 0;
+        for (int o = 0; o < 8; ++o) k8 += sp[o + 1] > sp[o];
+        nch[k] = k8;
+      }
+    });
+    int64_t next = le;
+    std::vector<int64_t> child_base(nl);
+    for (int64_t k = 0; k < nl; ++k) {
+      child_base[k] = next;
+      next += nch[k];
+    }
+    if (next == le) break;
+    level_begin.push_back(le);
+    if (next >= (1ll << 28)) return fail(OCTGRAV_ERR_ARG, "tree too large (%lld cells)", (long long)next);
+    T.key.resize(next);
+    T.depth.resize(next);
+    T.parent.resize(next);
+    T.first_child.resize(next);
+    T.n_child.resize(next);
+    T.pfirst.resize(next);
+    T.pcount.resize(next);
+    parallel_for(nl, parallel ? 2048 : (int64_t)1 << 62, [&](int64_t a, int64_t b) {
+      for (int64_t k = a; k < b; ++k) {
+        if (!nch[k]) continue;
+        const int64_t c = lb + k;
+        int64_t w = child_base[k];
+        T.first_child[c] = static_cast<int32_t>(w);
+        T.n_child[c] = nch[k];
+        const int64_t* sp = &splits[9 * k];
+        for (int o = 0; o < 8; ++o) {
+          if (sp[o + 1] <= sp[o]) continue;
+          T.key[w] = (T.key[c] << 3) | static_cast<uint64_t>(o);
+          T.depth[w] = L + 1;
+          T.parent[w] = static_cast<int32_t>(c);
+          T.first_child[w] = -1;
+          T.n_child[w] = 0;
+          T.pfirst[w] = sp[o];
+          T.pcount[w] = sp[o + 1] - sp[o];
+          ++w;
+        }
+      }
+    });
+  }
+  const int64_t nc = static_cast<int64_t>(T.key.size());
+  T.depth_reached = static_cast<int>(level_begin.size()) - 1;
+
+  // ---- cell properties, deepest level first
+  T.bmin.resize(3 * nc);
+  T.bmax.resize(3 * nc);
+  T.cube.resize(4 * nc);
+  T.M.resize(nc);
+  T.com.resize(3 * nc);
+  T.S.resize(6 * nc);
+  level_begin.push_back(nc);
+  for (int L = static_cast<int>(level_begin.size()) - 2; L >= 0; --L) {
+    const int64_t lb = level_begin[L], le = level_begin[L + 1];
+    parallel_for(le - lb, parallel ? 1024 : (int64_t)1 << 62, [&](int64_t a, int64_t b) {
+      for (int64_t c = lb + a; c < lb + b; ++c) {
+        double* bn = &T.bmin[3 * c];
+        double* bx = &T.bmax[3 * c];
+        double* cm = &T.com[3 * c];
+        double* s6 = &T.S[6 * c];
+        double Mc = 0, sx = 0, sy = 0, sz = 0;
+        for (int d = 0; d < 3; ++d) {
+          bn[d] = INFINITY;
+          bx[d] = -INFINITY;
+        }
+        const int64_t f = T.pfirst[c], cnt = T.pcount[c];
+        if (T.n_child[c] == 0) {
+          for (int64_t t = f; t < f + cnt; ++t) {
+            const double* xp = &T.x[3 * t];
+            for (int d = 0; d < 3; ++d) {
+              bn[d] = std::min(bn[d], xp[d]);
+              bx[d] = std::max(bx[d], xp[d]);
+            }
+            Mc += T.m[t];
+            sx += T.m[t] * xp[0];
+            sy += T.m[t] * xp[1];
+            sz += T.m[t] * xp[2];
+          }
+        } else {
+          for (int j = T.first_child[c]; j < T.first_child[c] + T.n_child[c]; ++j) {
+            for (int d = 0; d < 3; ++d) {
+              bn[d] = std::min(bn[d], T.bmin[3 * j + d]);
+              bx[d] = std::max(bx[d], T.bmax[3 * j + d]);
+            }
+            Mc += T.M[j];
+            sx += T.M[j] * T.com[3 * j];
+            sy += T.M[j] * T.com[3 * j + 1];
+            sz += T.M[j] * T.com[3 * j + 2];
+          }
+        }
+        double* cu = &T.cube[4 * c];
+        for (int d = 0; d < 3; ++d) cu[d] = (bn[d] + bx[d]) * 0.5;
+        double e = bx[0] - bn[0];
+        if (bx[1] - bn[1] > e) e = bx[1] - bn[1];
+        if (bx[2] - bn[2] > e) e = bx[2] - bn[2];
+        cu[3] = 0.5 * e;
+        T.M[c] = Mc;
+        if (Mc > 0) {
+          cm[0] = sx / Mc;
+          cm[1] = sy / Mc;
+          cm[2] = sz / Mc;
+        } else {
+          cm[0] = cu[0];
+          cm[1] = cu[1];
+          cm[2] = cu[2];
+        }
+        for (int q = 0; q < 6; ++q) s6[q] = 0;
+        auto add_outer = [&](double w, double y0, double y1, double y2) {
+          s6[0] += w * y0 * y0;
+          s6[1] += w * y1 * y1;
+          s6[2] += w * y2 * y2;
+          s6[3] += w * y0 * y1;
+          s6[4] += w * y0 * y2;
+          s6[5] += w * y1 * y2;
+        };
+        if (T.n_child[c] == 0) {
+          for (int64_t t = f; t < f + cnt; ++t)
+            add_outer(T.m[t], T.x[3 * t] - cm[0], T.x[3 * t + 1] - cm[1], T.x[3 * t + 2] - cm[2]);
+        } else {
+          for (int j = T.first_child[c]; j < T.first_child[c] + T.n_child[c]; ++j) {
+            for (int q = 0; q < 6; ++q) s6[q] += T.S[6 * j + q];
+            add_outer(T.M[j], T.com[3 * j] - cm[0], T.com[3 * j + 1] - cm[1], T.com[3 * j + 2] - cm[2]);
+          }
+        }
+      }
+    });
+  }
+
+  // ---- groups: first cells from the root that are leaves or hold <= n_group
+  std::vector<uint8_t> covered(nc, 0);
+  T.n_leaves = 0;
+  for (int64_t c = 0; c < nc; ++c) {
+    const bool par = c > 0 && covered[T.parent[c]];
+    const bool leaf = T.n_child[c] == 0;
+    T.n_leaves += leaf;
+    const bool elig = leaf || T.pcount[c] <= n_group;
+    if (!par && elig) T.groups.push_back(static_cast<int32_t>(c));
+    covered[c] = par || elig;
+  }
+  std::sort(T.groups.begin(), T.groups.end(),
+            [&](int32_t a, int32_t b) { return T.pfirst[a] < T.pfirst[b]; });
+  for (int32_t g : T.groups) T.max_group = std::max(T.max_group, T.pcount[g]);
+  return OCTGRAV_OK;
+}
+
+// ---------------------------------------------------------------- device buffers
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  int reserve(size_t bytes) {
+    if (bytes <= cap && p) return OCTGRAV_OK;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    size_t want = std::max<size_t>(bytes, 256);
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return fail(e == cudaErrorMemoryAllocation ? OCTGRAV_ERR_OOM : OCTGRAV_ERR_CUDA,
+                  "cudaMalloc(%zu) failed: %s", want, cudaGetErrorString(e));
+    }
+    cap = want;
+    return OCTGRAV_OK;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+struct Device {
+  DevBuf parts, geo, link, mp, items, ibox, sysp, out, counts, ctl, dbg;
+  int device = -1;
+  void release() {
+    for (DevBuf* b : {&parts, &geo, &link, &mp, &items, &ibox, &sysp, &out, &counts, &ctl, &dbg}) b->release();
+  }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------- the tree object
+
+struct octgrav_tree {
+  int64_t n = 0;
+  int n_leaf = 0, n_group = 0, n_sys = 0;
+  int ppl = 2, ctas_per_sm = 0;
+  std::vector<int64_t> sys_off;   // particle offsets per system (n_sys + 1)
+  std::vector<int64_t> cell_off;  // cell offsets per system (n_sys + 1)
+  std::vector<int64_t> perm;      // tree position -> input index
+  std::vector<uint64_t> key;      // per global cell
+  std::vector<int32_t> group_cell;  // per group, global cell index
+  std::vector<int32_t> group_sys;
+  int64_t n_cells = 0, n_leaves = 0, max_group = 0;
+  int depth_reached = 0;
+  // host images of the device arrays
+  std::vector<float4> parts, geo, mp, ibox;
+  std::vector<int2> link;
+  std::vector<int4> items;
+  std::vector<uint64_t> item_key;
+  // host FP64 cell properties (tests / introspection)
+  std::vector<double> bmin, bmax, cube, M, com, S;
+  std::vector<int64_t> pcount;
+  // per-system parameters (optional)
+  std::vector<float4> sysp;
+  bool sysp_dirty = false;
+  // device state
+  Device own;
+  Device* dev = &own;
+  bool uploaded = false;
+  bool launched = false;
+  std::vector<SysTree> sys_scratch;
+};
+
+namespace {
+
+// Split every group into work items of at most 32 * ppl particles.
+void make_items(octgrav_tree* t) {
+  const int item_max = 32 * t->ppl;
+  t->items.clear();
+  t->ibox.clear();
+  t->item_key.clear();
+  for (size_t g = 0; g < t->group_cell.size(); ++g) {
+    const int64_t c = t->group_cell[g];
+    const int s = t->group_sys[g];
+    const int64_t root = t->cell_off[s];
+    const int64_t cnt = t->pcount[c];
+    // first particle of the group: from the link of a leaf or by walking down to a leaf
+    int64_t cc = c;
+    while (t->link[cc].y > 0) cc = t->link[cc].x;
+    const int64_t pf = t->link[cc].x;
+    float4 b[3];
+    double C[3];
+    float chi[3], clo[3];
+    for (int d = 0; d < 3; ++d) {
+      C[d] = t->cube[4 * c + d];
+      chi[d] = static_cast<float>(C[d]);
+      clo[d] = static_cast<float>(C[d] - static_cast<double>(chi[d]));
+    }
+    b[0] = make_float4(static_cast<float>(t->bmin[3 * c]), static_cast<float>(t->bmin[3 * c + 1]),
+                       static_cast<float>(t->bmin[3 * c + 2]), chi[0]);
+    b[1] = make_float4(static_cast<float>(t->bmax[3 * c]), static_cast<float>(t->bmax[3 * c + 1]),
+                       static_cast<float>(t->bmax[3 * c + 2]), chi[1]);
+    b[2] = make_float4(clo[0], clo[1], clo[2], chi[2]);
+    for (int64_t off = 0; off < cnt; off += item_max) {
+      const int k = static_cast<int>(std::min<int64_t>(item_max, cnt - off));
+      t->items.push_back(make_int4(static_cast<int>(root), static_cast<int>(pf + off), k, s));
+      t->ibox.push_back(b[0]);
+      t->ibox.push_back(b[1]);
+      t->ibox.push_back(b[2]);
+      t->item_key.push_back(t->key[c]);
+    }
+  }
+}
+
+// Concatenate the systems' trees into the device-array images.
+int assemble(octgrav_tree* t, std::vector<SysTree>& sys) {
+  const int ns = static_cast<int>(sys.size());
+  t->cell_off.assign(ns + 1, 0);
+  for (int s = 0; s < ns; ++s) t->cell_off[s + 1] = t->cell_off[s] + static_cast<int64_t>(sys[s].key.size());
+  const int64_t nc = t->cell_off[ns];
+  if (nc >= (1ll << 28)) return fail(OCTGRAV_ERR_ARG, "too many cells (%lld)", (long long)nc);
+  t->n_cells = nc;
+  t->perm.resize(t->n);
+  t->parts.resize(2 * t->n);
+  t->key.resize(nc);
+  t->geo.resize(nc);
+  t->link.resize(nc);
+  t->mp.resize(4 * nc);
+  t->bmin.resize(3 * nc);
+  t->bmax.resize(3 * nc);
+  t->cube.resize(4 * nc);
+  t->M.resize(nc);
+  t->com.resize(3 * nc);
+  t->S.resize(6 * nc);
+  t->pcount.resize(nc);
+  t->group_cell.clear();
+  t->group_sys.clear();
+  t->n_leaves = 0;
+  t->max_group = 0;
+  t->depth_reached = 0;
+  for (int s = 0; s < ns; ++s) {
+    SysTree& T = sys[s];
+    const int64_t p0 = t->sys_off[s], c0 = t->cell_off[s];
+    const int64_t n = T.n, ncs = static_cast<int64_t>(T.key.size());
+    parallel_for(n, 16384, [&](int64_t a, int64_t b) {
+      for (int64_t k = a; k < b; ++k) {
+        t->perm[p0 + k] = p0 + T.perm[k];
+        float hi[3], lo[3];
+        for (int d = 0; d < 3; ++d) {
+          const double v = T.x[3 * k + d];
+          hi[d] = static_cast<float>(v);
+          lo[d] = static_cast<float>(v - static_cast<double>(hi[d]));
+        }
+        t->parts[2 * (p0 + k)] = make_float4(hi[0], hi[1], hi[2], static_cast<float>(T.m[k]));
+        t->parts[2 * (p0 + k) + 1] = make_float4(lo[0], lo[1], lo[2], 0.f);
+      }
+    });
+    parallel_for(ncs, 8192, [&](int64_t a, int64_t b) {
+      for (int64_t c = a; c < b; ++c) {
+        const int64_t g = c0 + c;
+        t->key[g] = T.key[c];
+        const double* cu = &T.cube[4 * c];
+        t->geo[g] = make_float4(static_cast<float>(cu[0]), static_cast<float>(cu[1]),
+                                static_cast<float>(cu[2]), static_cast<float>(cu[3]));
+        if (T.n_child[c] > 0)
+          t->link[g] = make_int2(static_cast<int>(c0 + T.first_child[c]), T.n_child[c]);
+        else
+          t->link[g] = make_int2(static_cast<int>(p0 + T.pfirst[c]), -static_cast<int>(T.pcount[c]));
+        const double* cm = &T.com[3 * c];
+        const double* s6 = &T.S[6 * c];
+        float chi[3], clo[3];
+        for (int d = 0; d < 3; ++d) {
+          chi[d] = static_cast<float>(cm[d]);
+          clo[d] = static_cast<float>(cm[d] - static_cast<double>(chi[d]));
+        }
+        const double tr = s6[0] + s6[1] + s6[2];
+        t->mp[4 * g] = make_float4(chi[0], chi[1], chi[2], static_cast<float>(T.M[c]));
+        t->mp[4 * g + 1] = make_float4(clo[0], clo[1], clo[2], static_cast<float>(0.5 * tr));
+        t->mp[4 * g + 2] = make_float4(static_cast<float>(3.0 * s6[0]), static_cast<float>(3.0 * s6[1]),
+                                       static_cast<float>(3.0 * s6[2]), static_cast<float>(3.0 * s6[3]));
+        t->mp[4 * g + 3] = make_float4(static_cast<float>(3.0 * s6[4]), static_cast<float>(3.0 * s6[5]),
+                                       static_cast<float>(1.5 * tr), 0.f);
+        for (int d = 0; d < 3; ++d) {
+          t->bmin[3 * g + d] = T.bmin[3 * c + d];
+          t->bmax[3 * g + d] = T.bmax[3 * c + d];
+          t->com[3 * g + d] = cm[d];
+        }
+        for (int d = 0; d < 4; ++d) t->cube[4 * g + d] = cu[d];
+        for (int d = 0; d < 6; ++d) t->S[6 * g + d] = s6[d];
+        t->M[g] = T.M[c];
+        t->pcount[g] = T.pcount[c];
+      }
+    });
+    for (int32_t gc : T.groups) {
+      t->group_cell.push_back(static_cast<int32_t>(c0 + gc));
+      t->group_sys.push_back(s);
+    }
+    t->n_leaves += T.n_leaves;
+    t->max_group = std::max(t->max_group, T.max_group);
+    t->depth_reached = std::max(t->depth_reached, T.depth_reached);
+  }
+  make_items(t);
+  return OCTGRAV_OK;
+}
+
+int check_inputs(const double* pos, const double* mass, int64_t n) {
+  std::atomic<int> bad{0};
+  parallel_for(n, 65536, [&](int64_t a, int64_t b) {
+    for (int64_t i = a; i < b; ++i) {
+      if (!std::isfinite(pos[3 * i]) || !std::isfinite(pos[3 * i + 1]) || !std::isfinite(pos[3 * i + 2]) ||
+          !std::isfinite(mass[i]) || mass[i] < 0) {
+        bad.store(1);
+        return;
+      }
+    }
+  });
+  return bad.load() ? fail(OCTGRAV_ERR_NONFINITE, "non-finite position/mass or negative mass") : OCTGRAV_OK;
+}
+
+int build_common(int n_sys, const int64_t* offsets, const double* pos, const double* mass, int n_leaf,
+                 int n_group, octgrav_tree** out) {
+  if (!out) return fail(OCTGRAV_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!pos || !mass || !offsets || n_sys < 1) return fail(OCTGRAV_ERR_ARG, "NULL input or n_sys < 1");
+  if (n_leaf < 1 || n_group < n_leaf) return fail(OCTGRAV_ERR_ARG, "need 1 <= n_leaf <= n_group");
+  if (offsets[0] != 0) return fail(OCTGRAV_ERR_ARG, "offsets[0] must be 0");
+  for (int s = 0; s < n_sys; ++s)
+    if (offsets[s + 1] <= offsets[s]) return fail(OCTGRAV_ERR_ARG, "empty or decreasing system %d", s);
+  const int64_t n = offsets[n_sys];
+  if (n >= (1ll << 31) - 64) return fail(OCTGRAV_ERR_ARG, "too many particles");
+  int rc = check_inputs(pos, mass, n);
+  if (rc) return rc;
+  std::unique_ptr<octgrav_tree> t;
+  try {
+    t.reset(new octgrav_tree());
+    t->n = n;
+    t->n_leaf = n_leaf;
+    t->n_group = n_group;
+    t->n_sys = n_sys;
+    t->sys_off.assign(offsets, offsets + n_sys + 1);
+    std::vector<SysTree> sys(n_sys);
+    std::vector<int> rcs(n_sys, 0);
+    if (n_sys == 1) {
+      rcs[0] = build_system(pos, mass, n, n_leaf, n_group, true, sys[0]);
+    } else {
+      Pool::get().run(n_sys, [&](int s) {
+        const int64_t o = offsets[s];
+        rcs[s] = build_system(pos + 3 * o, mass + o, offsets[s + 1] - o, n_leaf, n_group, false, sys[s]);
+      });
+    }
+    for (int s = 0; s < n_sys; ++s)
+      if (rcs[s]) return rcs[s];
+    rc = assemble(t.get(), sys);
+    if (rc) return rc;
+  } catch (const std::bad_alloc&) {
+    return fail(OCTGRAV_ERR_OOM, "host allocation failed");
+  }
+  *out = t.release();
+  return OCTGRAV_OK;
+}
+
+template <class V>
+int upload_vec(DevBuf& b, const V& v, cudaStream_t st) {
+  const size_t bytes = v.size() * sizeof(typename V::value_type);
+  int rc = b.reserve(bytes);
+  if (rc) return rc;
+  if (bytes) CUDA_TRY(cudaMemcpyAsync(b.p, v.data(), bytes, cudaMemcpyHostToDevice, st));
+  return OCTGRAV_OK;
+}
+
+int upload(octgrav_tree* t, cudaStream_t st) {
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  Device& D = *t->dev;
+  if (D.device >= 0 && D.device != dev) {
+    D.release();
+  }
+  D.device = dev;
+  int rc;
+  if ((rc = upload_vec(D.parts, t->parts, st)) || (rc = upload_vec(D.geo, t->geo, st)) ||
+      (rc = upload_vec(D.link, t->link, st)) || (rc = upload_vec(D.mp, t->mp, st)) ||
+      (rc = upload_vec(D.items, t->items, st)) || (rc = upload_vec(D.ibox, t->ibox, st)))
+    return rc;
+  if ((rc = D.counts.reserve(t->items.size() * sizeof(int2)))) return rc;
+  if ((rc = D.ctl.reserve(64))) return rc;
+  if (!t->sysp.empty()) {
+    if ((rc = upload_vec(D.sysp, t->sysp, st))) return rc;
+  }
+  t->sysp_dirty = false;
+  t->uploaded = true;
+  return OCTGRAV_OK;
+}
+
+int check_params(double eps, double theta, double G) {
+  if (!(eps > 0) || !std::isfinite(eps)) return fail(OCTGRAV_ERR_ARG, "eps must be finite and > 0");
+  if (!(theta >= 0) || !std::isfinite(theta)) return fail(OCTGRAV_ERR_ARG, "theta must be finite and >= 0");
+  if (!std::isfinite(G)) return fail(OCTGRAV_ERR_ARG, "G must be finite");
+  return OCTGRAV_OK;
+}
+
+og::KParams make_params(octgrav_tree* t, float4* out) {
+  Device& D = *t->dev;
+  og::KParams p{};
+  p.parts = static_cast<const float4*>(D.parts.p);
+  p.geo = static_cast<const float4*>(D.geo.p);
+  p.link = static_cast<const int2*>(D.link.p);
+  p.mp = static_cast<const float4*>(D.mp.p);
+  p.items = static_cast<const int4*>(D.items.p);
+  p.ibox = static_cast<const float4*>(D.ibox.p);
+  p.sysp = t->sysp.empty() ? nullptr : static_cast<const float4*>(D.sysp.p);
+  p.out = out;
+  p.counts = static_cast<int2*>(D.counts.p);
+  p.status = static_cast<int*>(D.ctl.p);
+  p.work = reinterpret_cast<unsigned*>(static_cast<char*>(D.ctl.p) + 4);
+  p.n_items = static_cast<int>(t->items.size());
+  p.n_cells = static_cast<int>(t->n_cells);
+  return p;
+}
+
+int launch(octgrav_tree* t, double eps, double theta, double G, float4* out, cudaStream_t st,
+           bool capture, int* dbg_cell, int* dbg_leaf, int2* dbg_n, int dbg_cap) {
+  int rc = check_params(eps, theta, G);
+  if (rc) return rc;
+  if (!t->uploaded || t->sysp_dirty) {
+    if ((rc = upload(t, st))) return rc;
+  }
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != t->dev->device) return fail(OCTGRAV_ERR_STATE, "tree was uploaded to device %d, current is %d",
+                                         t->dev->device, dev);
+  og::KParams p = make_params(t, out);
+  p.sys0 = make_float4(static_cast<float>(theta * theta), static_cast<float>(eps * eps), static_cast<float>(G), 0.f);
+  if (capture) {
+    p.dbg_cell = dbg_cell;
+    p.dbg_leaf = dbg_leaf;
+    p.dbg_n = dbg_n;
+    p.dbg_cap = dbg_cap;
+  }
+  CUDA_TRY(cudaMemsetAsync(t->dev->ctl.p, 0, 8, st));
+  if (p.n_items > 0) {
+    cudaError_t e = og::launch_walk_eval(p, t->ppl, t->ctas_per_sm, capture, st, nullptr);
+    if (e != cudaSuccess) return fail(OCTGRAV_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+  }
+  t->launched = true;
+  return OCTGRAV_OK;
+}
+
+int read_status(octgrav_tree* t, cudaStream_t st) {
+  int h = 0;
+  CUDA_TRY(cudaMemcpyAsync(&h, t->dev->ctl.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  if (h & og::ST_TIMEOUT) return fail(OCTGRAV_ERR_TIMEOUT, "device wait timed out (status %d)", h);
+  if (h & og::ST_INDEX) return fail(OCTGRAV_ERR_INDEX, "walk met an out-of-range cell index");
+  if (h & og::ST_STACK) return fail(OCTGRAV_ERR_STACK, "walk overflowed its node stack");
+  return OCTGRAV_OK;
+}
+
+int forces_host(octgrav_tree* t, double eps, double theta, double G, double* acc, double* pot,
+                cudaStream_t st) {
+  if (!acc) return fail(OCTGRAV_ERR_ARG, "acc is NULL");
+  int rc = check_params(eps, theta, G);
+  if (rc) return rc;
+  if (!t->uploaded || t->sysp_dirty) {
+    if ((rc = upload(t, st))) return rc;
+  }
+  if ((rc = t->dev->out.reserve(sizeof(float4) * t->n))) return rc;
+  if ((rc = launch(t, eps, theta, G, static_cast<float4*>(t->dev->out.p), st, false, nullptr, nullptr, nullptr, 0)))
+    return rc;
+  std::vector<float4> h(t->n);
+  CUDA_TRY(cudaMemcpyAsync(h.data(), t->dev->out.p, sizeof(float4) * t->n, cudaMemcpyDeviceToHost, st));
+  if ((rc = read_status(t, st))) return rc;
+  parallel_for(t->n, 65536, [&](int64_t a, int64_t b) {
+    for (int64_t k = a; k < b; ++k) {
+      const int64_t i = t->perm[k];
+      acc[3 * i] = h[k].x;
+      acc[3 * i + 1] = h[k].y;
+      acc[3 * i + 2] = h[k].z;
+      if (pot) pot[i] = h[k].w;
+    }
+  });
+  return OCTGRAV_OK;
+}
+
+thread_local Device* tl_cache = nullptr;
+
+}  // namespace
+
+// ---------------------------------------------------------------- C ABI
+
+extern "C" {
+
+int octgrav_version(void) { return 10000; }
+
+const char* octgrav_last_error(void) { return g_err.c_str(); }
+
+int octgrav_build_tree(const double* pos, const double* mass, int64_t n, int n_leaf, int n_group,
+                       octgrav_tree** out) {
+  if (n < 1) return fail(OCTGRAV_ERR_ARG, "n must be >= 1");
+  const int64_t off[2] = {0, n};
+  return build_common(1, off, pos, mass, n_leaf, n_group, out);
+}
+
+int octgrav_build_batch(int n_sys, const int64_t* offsets, const double* pos, const double* mass, int n_leaf,
+                        int n_group, octgrav_tree** out) {
+  return build_common(n_sys, offsets, pos, mass, n_leaf, n_group, out);
+}
+
+int octgrav_tree_upload(octgrav_tree* t, void* stream) {
+  if (!t) return fail(OCTGRAV_ERR_ARG, "tree is NULL");
+  return upload(t, static_cast<cudaStream_t>(stream));
+}
+
+int octgrav_forces_device(octgrav_tree* t, double eps, double theta, double G, float* acc4_dev, void* stream) {
+  if (!t || !acc4_dev) return fail(OCTGRAV_ERR_ARG, "NULL tree or output");
+  int rc = check_params(eps, theta, G);
+  if (rc) return rc;
+  return launch(t, eps, theta, G, reinterpret_cast<float4*>(acc4_dev), static_cast<cudaStream_t>(stream), false,
+                nullptr, nullptr, nullptr, 0);
+}
+
+int octgrav_set_system_params(octgrav_tree* t, const double* eps, const double* theta) {
+  if (!t) return fail(OCTGRAV_ERR_ARG, "tree is NULL");
+  if (!eps && !theta) {
+    t->sysp.clear();
+    return OCTGRAV_OK;
+  }
+  if (!eps || !theta) return fail(OCTGRAV_ERR_ARG, "give both eps and theta, or neither");
+  std::vector<float4> sp(t->n_sys);
+  for (int s = 0; s < t->n_sys; ++s) {
+    int rc = check_params(eps[s], theta[s], 1.0);
+    if (rc) return rc;
+    sp[s] = make_float4(static_cast<float>(theta[s] * theta[s]), static_cast<float>(eps[s] * eps[s]), 1.f, 0.f);
+  }
+  t->sysp = std::move(sp);
+  t->sysp_dirty = true;
+  return OCTGRAV_OK;
+}
+
+int octgrav_forces_tree(octgrav_tree* t, double eps, double theta, double G, double* acc, double* pot,
+                        void* stream) {
+  if (!t) return fail(OCTGRAV_ERR_ARG, "tree is NULL");
+  return forces_host(t, eps, theta, G, acc, pot, static_cast<cudaStream_t>(stream));
+}
+
+int octgrav_forces_ex(const double* pos, const double* mass, int64_t n, double eps, double theta, double G,
+                      int n_leaf, int n_group, double* acc, double* pot, void* stream) {
+  int rc = check_params(eps, theta, G);
+  if (rc) return rc;
+  octgrav_tree* t = nullptr;
+  if ((rc = octgrav_build_tree(pos, mass, n, n_leaf, n_group, &t))) return rc;
+  if (!tl_cache) tl_cache = new Device();
+  t->dev = tl_cache;
+  rc = forces_host(t, eps, theta, G, acc, pot, static_cast<cudaStream_t>(stream));
+  octgrav_free_tree(t);
+  return rc;
+}
+
+int octgrav_forces(const double* pos, const double* mass, int64_t n, double eps, double theta, int n_leaf,
+                   double* acc, double* pot) {
+  return octgrav_forces_ex(pos, mass, n, eps, theta, 1.0, n_leaf, n_leaf, acc, pot, nullptr);
+}
+
+int octgrav_status(octgrav_tree* t, void* stream) {
+  if (!t) return fail(OCTGRAV_ERR_ARG, "tree is NULL");
+  if (!t->launched) return fail(OCTGRAV_ERR_STATE, "no launch on this tree yet");
+  return read_status(t, static_cast<cudaStream_t>(stream));
+}
+
+int octgrav_tree_stats(const octgrav_tree* t, int64_t* out, int n_out) {
+  if (!t || !out) return fail(OCTGRAV_ERR_ARG, "NULL argument");
+  const int64_t v[8] = {t->n, t->n_cells, t->n_leaves, static_cast<int64_t>(t->group_cell.size()),
+                        static_cast<int64_t>(t->items.size()), t->depth_reached, t->n_sys, t->max_group};
+  for (int k = 0; k < n_out && k < 8; ++k) out[k] = v[k];
+  return OCTGRAV_OK;
+}
+
+int octgrav_tree_perm(const octgrav_tree* t, int64_t* perm) {
+  if (!t || !perm) return fail(OCTGRAV_ERR_ARG, "NULL argument");
+  std::memcpy(perm, t->perm.data(), sizeof(int64_t) * t->n);
+  return OCTGRAV_OK;
+}
+
+int octgrav_tree_cell_keys(const octgrav_tree* t, uint64_t* keys) {
+  if (!t || !keys) return fail(OCTGRAV_ERR_ARG, "NULL argument");
+  std::memcpy(keys, t->key.data(), sizeof(uint64_t) * t->n_cells);
+  return OCTGRAV_OK;
+}
+
+int octgrav_tree_cell_props(const octgrav_tree* t, double* bmin, double* bmax, double* cube, double* mass,
+                            double* com, double* S, int64_t* count) {
+  if (!t) return fail(OCTGRAV_ERR_ARG, "NULL argument");
+  const size_t nc = static_cast<size_t>(t->n_cells);
+  if (bmin) std::memcpy(bmin, t->bmin.data(), 24 * nc);
+  if (bmax) std::memcpy(bmax, t->bmax.data(), 24 * nc);
+  if (cube) std::memcpy(cube, t->cube.data(), 32 * nc);
+  if (mass) std::memcpy(mass, t->M.data(), 8 * nc);
+  if (com) std::memcpy(com, t->com.data(), 24 * nc);
+  if (S) std::memcpy(S, t->S.data(), 48 * nc);
+  if (count) std::memcpy(count, t->pcount.data(), 8 * nc);
+  return OCTGRAV_OK;
+}
+
+int octgrav_item_info(const octgrav_tree* t, uint64_t* group_key, int64_t* first, int32_t* count, int32_t* sys) {
+  if (!t) return fail(OCTGRAV_ERR_ARG, "tree is NULL");
+  for (size_t k = 0; k < t->items.size(); ++k) {
+    if (group_key) group_key[k] = t->item_key[k];
+    if (first) first[k] = t->items[k].y;
+    if (count) count[k] = t->items[k].z;
+    if (sys) sys[k] = t->items[k].w;
+  }
+  return OCTGRAV_OK;
+}
+
+int octgrav_interaction_counts(octgrav_tree* t, int64_t* out, void* stream) {
+  if (!t || !out) return fail(OCTGRAV_ERR_ARG, "NULL argument");
+  if (!t->launched) return fail(OCTGRAV_ERR_STATE, "no launch on this tree yet");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<int2> c(t->items.size());
+  if (!c.empty())
+    CUDA_TRY(cudaMemcpyAsync(c.data(), t->dev->counts.p, sizeof(int2) * c.size(), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  int64_t npp = 0, npc = 0;
+  for (size_t k = 0; k < c.size(); ++k) {
+    const int64_t np = t->items[k].z;
+    npc += np * c[k].x;
+    npp += np * (c[k].y - 1);
+  }
+  out[0] = npp;
+  out[1] = npc;
+  out[2] = 38 * npp + 70 * npc;
+  return OCTGRAV_OK;
+}
+
+int octgrav_debug_lists(octgrav_tree* t, double theta, int cap, uint64_t* cell_keys, int32_t* n_cell,
+                        uint64_t* leaf_keys, int32_t* n_leaf, void* stream) {
+  if (!t || cap < 1 || !cell_keys || !n_cell || !leaf_keys || !n_leaf) return fail(OCTGRAV_ERR_ARG, "bad argument");
+  int rc = check_params(1.0, theta, 1.0);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t ni = t->items.size();
+  if (!t->uploaded || t->sysp_dirty) {
+    if ((rc = upload(t, st))) return rc;
+  }
+  if ((rc = t->dev->out.reserve(sizeof(float4) * t->n))) return rc;
+  const size_t bytes = ni * cap * 8 + ni * sizeof(int2);
+  if ((rc = t->dev->dbg.reserve(bytes))) return rc;
+  int* dcell = static_cast<int*>(t->dev->dbg.p);
+  int* dleaf = dcell + ni * cap;
+  int2* dn = reinterpret_cast<int2*>(dleaf + ni * cap);
+  if ((rc = launch(t, 1.0, theta, 1.0, static_cast<float4*>(t->dev->out.p), st, true, dcell, dleaf, dn, cap)))
+    return rc;
+  std::vector<int> hc(ni * cap), hl(ni * cap);
+  std::vector<int2> hn(ni);
+  CUDA_TRY(cudaMemcpyAsync(hc.data(), dcell, 4 * ni * cap, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(hl.data(), dleaf, 4 * ni * cap, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(hn.data(), dn, sizeof(int2) * ni, cudaMemcpyDeviceToHost, st));
+  if ((rc = read_status(t, st))) return rc;
+  bool trunc = false;
+  for (size_t k = 0; k < ni; ++k) {
+    n_cell[k] = hn[k].x;
+    n_leaf[k] = hn[k].y;
+    trunc |= hn[k].x > cap || hn[k].y > cap;
+    for (int e = 0; e < std::min(cap, hn[k].x); ++e) cell_keys[k * cap + e] = t->key[hc[k * cap + e]];
+    for (int e = 0; e < std::min(cap, hn[k].y); ++e) leaf_keys[k * cap + e] = t->key[hl[k * cap + e]];
+  }
+  if (trunc) return fail(OCTGRAV_ERR_LIST, "a list was longer than cap = %d", cap);
+  return OCTGRAV_OK;
+}
+
+int octgrav_set_launch(octgrav_tree* t, int particles_per_lane, int ctas_per_sm) {
+  if (!t) return fail(OCTGRAV_ERR_ARG, "tree is NULL");
+  if (particles_per_lane != 1 && particles_per_lane != 2) return fail(OCTGRAV_ERR_ARG, "particles_per_lane must be 1 or 2");
+  if (ctas_per_sm < 0) return fail(OCTGRAV_ERR_ARG, "ctas_per_sm must be >= 0");
+  t->ctas_per_sm = ctas_per_sm;
+  if (particles_per_lane != t->ppl) {
+    t->ppl = particles_per_lane;
+    make_items(t);
+    t->uploaded = false;
+  }
+  return OCTGRAV_OK;
+}
+
+void octgrav_free_tree(octgrav_tree* t) {
+  if (!t) return;
+  t->own.release();
+  delete t;
+}
+
+}  // extern "C"

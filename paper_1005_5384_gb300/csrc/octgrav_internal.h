@@ -1,0 +1,64 @@
+// octgrav_internal.h -- shared between the host library (octgrav_host.cpp) and
+// the CUDA kernels (octgrav_kernels.cu). Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace og {
+
+// Device status bits (OR-ed into the status word by the kernel).
+enum : int {
+  ST_STACK = 1,    // node stack overflow in a walk
+  ST_INDEX = 2,    // child index outside the cell array
+  ST_TIMEOUT = 4,  // bounded mbarrier wait expired
+};
+
+// Kernel arguments. Array layouts (all in tree order):
+//   parts [2*n]  float4: hi = (x_hi, y_hi, z_hi, m), lo = (x - x_hi, ..., 0)
+//   geo   [nc]   float4: boundary cube centre (FP32-rounded) and half side h
+//   link  [nc]   int2:   node -> (first child, number of children 1..8),
+//                        leaf -> (first particle, -count)
+//   mp    [4*nc] float4: q0 = (com_hi.xyz, M), q1 = (com_lo.xyz, T = trS/2),
+//                        q2 = (3Sxx, 3Syy, 3Szz, 3Sxy), q3 = (3Sxz, 3Syz, 3T, 0)
+//   items [ni]   int4:   (root cell of the system, first particle, count, system)
+//   ibox  [3*ni] float4: (gmin.xyz, C_hi.x), (gmax.xyz, C_hi.y), (C_lo.xyz, C_hi.z)
+//                        group tight box (FP32-rounded) and group centre C (hi/lo)
+//   sysp  [nsys] float4: (fl32(theta^2), fl32(eps^2), -, -) (optional; G is sys0.z)
+struct KParams {
+  const float4* parts;
+  const float4* geo;
+  const int2* link;
+  const float4* mp;
+  const int4* items;
+  const float4* ibox;
+  const float4* sysp;    // per-system parameters, or nullptr to use sys0
+  float4 sys0;           // (fl32(theta^2), fl32(eps^2), G, 0) for every system
+  float4* out;           // [n] (a_x, a_y, a_z, phi), tree order
+  int2* counts;          // [ni] (n_pc, n_pp sources incl. self)
+  int* status;           // device status word
+  unsigned* work;        // work-queue counter (zeroed before the launch)
+  int n_items;
+  int n_cells;
+  // capture mode (tests): per item up to dbg_cap cell indices
+  int* dbg_cell;
+  int* dbg_leaf;
+  int2* dbg_n;
+  int dbg_cap;
+};
+
+struct LaunchInfo {
+  int grid;
+  int block;
+  size_t smem;
+};
+
+// Launch the fused walk + evaluation kernel. ppl = particles per lane (1 or 2),
+// ctas_per_sm = 0 for the occupancy maximum. Returns a cudaError_t.
+cudaError_t launch_walk_eval(const KParams& p, int ppl, int ctas_per_sm, bool capture,
+                             cudaStream_t stream, LaunchInfo* info);
+
+// Shared memory per CTA of the fused kernel.
+size_t walk_eval_smem_bytes();
+
+}  // namespace og

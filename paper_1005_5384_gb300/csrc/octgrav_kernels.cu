@@ -1,0 +1,561 @@
+// octgrav_kernels.cu -- fused tree walk + interaction-list evaluation for sm_103a.
+//
+// One warp owns one work item (a group of at most 32*R particles, Sec. 2.2:
+// particles of a group share one interaction list). It walks the octree from
+// the root with a node stack in shared memory (Listing 1), applies the opening
+// test to the children of up to four popped nodes at once (one lane per child,
+// Listing 2), and compacts the three outcomes with warp ballots:
+//   accepted cell -> cell list: its 64-byte multipole record is fetched into a
+//                    shared-memory ring by a bulk async copy (cp.async.bulk,
+//                    completion on an mbarrier) the moment it is accepted;
+//   opened leaf   -> leaf queue (first particle, count);
+//   opened node   -> pushed on the stack as (first child, number of children).
+// Full tiles of 32 cell records are evaluated one walk step after their copies
+// were issued, by all particles of the group (Listing 3); the leaf queue is
+// evaluated in chunks of 64 source particles (Listing 4). The paper's two
+// walks (count, then write) and the host prefix sum between them (Sec. 2.2)
+// are gone: lists never leave the SM.
+//
+// Lane mapping: the n_g particles of the item are spread over w = ceil(n_g/R)
+// lanes (R particles per lane); the warp holds s = 32/w such slices, and slice
+// k evaluates list entries k, k+s, k+2s, ... . Partial sums of the slices are
+// combined with shuffles at the end, so small groups still fill the warp (the
+// paper lost ~70% of its threads to part-filled groups, Sec. 3.3).
+//
+// Precision: positions are group-relative FP32, x' = (x_hi - C_hi) + (x_lo - C_lo)
+// with C the group centre kept as a hi/lo float pair; sums are accumulated in
+// FP32 and folded into a compensated (TwoSum) accumulator every ~32 terms.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "octgrav_internal.h"
+
+namespace og {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int WARPS = 8;          // warps per CTA
+constexpr int TILE = 32;          // cell records per tile
+constexpr int NTILE = 3;          // tiles in the ring (copies run one step ahead)
+constexpr int REC = 5;            // float4 per ring slot: 64-byte record + 16-byte pad
+constexpr int STACK = 512;        // node-stack entries per warp
+constexpr int PCHUNK = 64;        // source particles per particle-particle chunk
+constexpr int LQ = 64;            // leaf-queue entries (flushed at >= 32)
+constexpr long long WAIT_LIMIT = 1ll << 31;  // cycles (~1 s) before a wait gives up
+
+struct __align__(16) WarpSmem {
+  float4 ring[NTILE * TILE * REC];  // 7680 B; stride 80 B keeps 8 slots on 8 bank quads
+  float4 src[PCHUNK];               // 1024 B: source (x', m)
+  int srcidx[PCHUNK];               // 256 B: source tree index (self exclusion)
+  int2 leafq[LQ];                   // 512 B: (first particle, count)
+  int lpref[LQ];                    // 256 B: inclusive prefix of counts
+  int stack[STACK];                 // 2048 B: packed (first child << 3 | n_child - 1)
+  unsigned long long bar[NTILE];    // one mbarrier per ring tile
+  unsigned long long pad_;
+};
+
+// ---------------------------------------------------------------- PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// Raise the barrier's expected transaction bytes (no arrival).
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\t"
+      "mbarrier.arrive.release.cta.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bulk asynchronous copy global -> shared; completion is signalled on bar.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+// Order this thread's generic-proxy shared-memory accesses before later
+// async-proxy (bulk copy) writes to the same locations.
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Bounded wait for the phase of parity `parity`; false after ~1 s.
+__device__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  bool ok = mbar_try_wait(bar, parity);
+  if (!ok) {
+    const long long t0 = clock64();
+    while (!(ok = mbar_try_wait(bar, parity))) {
+      if (clock64() - t0 > WAIT_LIMIT) break;
+    }
+  }
+  return __all_sync(FULL, ok);
+}
+
+// ---------------------------------------------------------------- arithmetic
+
+// Opening test (Sec. 2.2, Listing 2): open iff (2h)^2 >= theta^2 d^2, d the
+// distance from the group's tight box to the cell's boundary cube. Every
+// operation is an explicitly rounded FP32 op (no contraction), so the
+// decision is reproducible bit for bit by a CPU implementation.
+__device__ __forceinline__ bool must_open(float4 g, float3 gmin, float3 gmax, float theta2) {
+  const float h = g.w;
+  const float bx = __fsub_rn(gmin.x, __fadd_rn(g.x, h)), tx = __fsub_rn(__fsub_rn(g.x, h), gmax.x);
+  const float by = __fsub_rn(gmin.y, __fadd_rn(g.y, h)), ty = __fsub_rn(__fsub_rn(g.y, h), gmax.y);
+  const float bz = __fsub_rn(gmin.z, __fadd_rn(g.z, h)), tz = __fsub_rn(__fsub_rn(g.z, h), gmax.z);
+  const float dx = fmaxf(0.f, fmaxf(bx, tx));
+  const float dy = fmaxf(0.f, fmaxf(by, ty));
+  const float dz = fmaxf(0.f, fmaxf(bz, tz));
+  const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+  return __fmul_rn(4.0f, __fmul_rn(h, h)) >= __fmul_rn(theta2, d2);
+}
+
+struct Acc4 {
+  float x, y, z, p;
+};
+
+// Particle-cell interaction: second-order Taylor expansion of the Plummer
+// kernel about the cell's centre of mass (monopole + quadrupole). With
+// d = x_i - com, r^2 = |d|^2 + eps^2, S3 = 3S, q = d.S3.d, T = trS/2:
+//   a   += d (-M + (3T - 2.5 q/r^2)/r^2) / r^3 + S3 d / r^5
+//   phi -= (M + (q/(2 r^2) - T)/r^2) / r
+__device__ __forceinline__ void body_cell(float x, float y, float z, float eps2, float4 q0,
+                                          float T, float4 q2, float4 q3, Acc4& a) {
+  const float dx = x - q0.x, dy = y - q0.y, dz = z - q0.z;
+  const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+  const float rinv = rsqrtf(r2);
+  const float rinv2 = rinv * rinv;
+  const float rinv3 = rinv * rinv2;
+  const float rinv5 = rinv3 * rinv2;
+  const float sx = fmaf(q2.x, dx, fmaf(q2.w, dy, q3.x * dz));
+  const float sy = fmaf(q2.w, dx, fmaf(q2.y, dy, q3.y * dz));
+  const float sz = fmaf(q3.x, dx, fmaf(q3.y, dy, q2.z * dz));
+  const float q = fmaf(dx, sx, fmaf(dy, sy, dz * sz));
+  const float t1 = q * rinv2;
+  const float t2 = fmaf(-2.5f, t1, q3.z);
+  const float cd = fmaf(t2, rinv2, -q0.w) * rinv3;
+  a.x = fmaf(cd, dx, fmaf(rinv5, sx, a.x));
+  a.y = fmaf(cd, dy, fmaf(rinv5, sy, a.y));
+  a.z = fmaf(cd, dz, fmaf(rinv5, sz, a.z));
+  const float p2 = fmaf(fmaf(0.5f, t1, -T), rinv2, q0.w);
+  a.p = fmaf(-p2, rinv, a.p);
+}
+
+// Particle-particle interaction with Plummer softening; mj = 0 drops the self term.
+__device__ __forceinline__ void body_body(float x, float y, float z, float eps2, float4 s,
+                                          float mj, Acc4& a) {
+  const float dx = s.x - x, dy = s.y - y, dz = s.z - z;
+  const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+  const float rinv = rsqrtf(r2);
+  const float mr = mj * rinv;
+  const float mr3 = mr * rinv * rinv;
+  a.x = fmaf(mr3, dx, a.x);
+  a.y = fmaf(mr3, dy, a.y);
+  a.z = fmaf(mr3, dz, a.z);
+  a.p -= mr;
+}
+
+// Error-free transformation: hi + t = s + e exactly.
+__device__ __forceinline__ void two_sum_into(float& hi, float& lo, float t) {
+  const float s = hi + t;
+  const float bp = s - hi;
+  const float e = (hi - (s - bp)) + (t - bp);
+  hi = s;
+  lo += e;
+}
+
+template <int R>
+struct Particles {
+  float x[R], y[R], z[R];
+  int idx[R];
+  Acc4 part[R];  // plain FP32 partial sums since the last fold
+  Acc4 hi[R];    // compensated accumulator: value = hi + lo
+  Acc4 lo[R];
+
+  __device__ __forceinline__ void fold() {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      two_sum_into(hi[r].x, lo[r].x, part[r].x);
+      two_sum_into(hi[r].y, lo[r].y, part[r].y);
+      two_sum_into(hi[r].z, lo[r].z, part[r].z);
+      two_sum_into(hi[r].p, lo[r].p, part[r].p);
+      part[r] = Acc4{0.f, 0.f, 0.f, 0.f};
+    }
+  }
+};
+
+// ---------------------------------------------------------------- the kernel
+
+template <int R, bool CAPTURE>
+__global__ void __launch_bounds__(WARPS * 32, 2) walk_eval_kernel(const KParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  WarpSmem& S = reinterpret_cast<WarpSmem*>(smem_raw)[threadIdx.x >> 5];
+  const uint32_t bar0 = smem_u32(&S.bar[0]);
+  if (lane == 0) {
+    for (int t = 0; t < NTILE; ++t) mbar_init(bar0 + 8 * t, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  const unsigned lt = lanemask_lt();
+
+  // Ring counters, warp-uniform and persistent across items: `app` counts
+  // cell entries whose copies were issued, `done` those evaluated. Tile
+  // (e / TILE) % NTILE holds entry e; its k-th use completes phase k.
+  uint32_t app = 0, done = 0;
+  int status = 0;
+
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = static_cast<int>(atomicAdd(p.work, 1u));
+    item = __shfl_sync(FULL, item, 0);
+    if (item >= p.n_items) break;
+
+    const int4 it = __ldg(p.items + item);
+    const float4 b0 = __ldg(p.ibox + 3 * item);
+    const float4 b1 = __ldg(p.ibox + 3 * item + 1);
+    const float4 b2 = __ldg(p.ibox + 3 * item + 2);
+    const float4 sp = p.sysp ? __ldg(p.sysp + it.w) : p.sys0;
+    const float theta2 = sp.x, eps2 = sp.y, G = p.sys0.z;
+    const float3 gmin = make_float3(b0.x, b0.y, b0.z);
+    const float3 gmax = make_float3(b1.x, b1.y, b1.z);
+    const float3 chi = make_float3(b0.w, b1.w, b2.w);
+    const float3 clo = make_float3(b2.x, b2.y, b2.z);
+    const int pf = it.y, np = it.z;
+
+    // lane -> (slice, particles)
+    const int w = (np + R - 1) / R;
+    const int s = 32 / w;
+    const int sl = lane / w;
+    const int wl = lane - sl * w;
+    const bool act = sl < s;
+
+    Particles<R> P;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int k = wl + r * w;
+      const bool v = act && k < np;
+      P.idx[r] = v ? pf + k : -1;
+      P.x[r] = P.y[r] = P.z[r] = 0.f;
+      if (v) {
+        const float4 h4 = __ldg(p.parts + 2 * (pf + k));
+        const float4 l4 = __ldg(p.parts + 2 * (pf + k) + 1);
+        P.x[r] = (h4.x - chi.x) + (l4.x - clo.x);
+        P.y[r] = (h4.y - chi.y) + (l4.y - clo.y);
+        P.z[r] = (h4.z - chi.z) + (l4.z - clo.z);
+      }
+      P.part[r] = P.hi[r] = P.lo[r] = Acc4{0.f, 0.f, 0.f, 0.f};
+    }
+    int nsince = 0;  // tiles since the last fold
+
+    // ---- evaluation of one ring tile holding n records
+    auto eval_tile = [&](int n) -> bool {
+      const uint32_t tile = (done / TILE) % NTILE;
+      const uint32_t parity = (done / (TILE * NTILE)) & 1u;
+      if (!mbar_wait_bounded(bar0 + 8 * tile, parity)) return false;
+      float4* base = &S.ring[tile * TILE * REC];
+      if (lane < n) {  // centre of mass relative to the group centre
+        float4 q0 = base[lane * REC];
+        const float4 q1 = base[lane * REC + 1];
+        q0.x = (q0.x - chi.x) + (q1.x - clo.x);
+        q0.y = (q0.y - chi.y) + (q1.y - clo.y);
+        q0.z = (q0.z - chi.z) + (q1.z - clo.z);
+        base[lane * REC] = q0;
+      }
+      __syncwarp();
+      if (act) {
+        for (int e = sl; e < n; e += s) {
+          const float4 q0 = base[e * REC];
+          const float T = base[e * REC + 1].w;
+          const float4 q2 = base[e * REC + 2];
+          const float4 q3 = base[e * REC + 3];
+#pragma unroll
+          for (int r = 0; r < R; ++r) body_cell(P.x[r], P.y[r], P.z[r], eps2, q0, T, q2, q3, P.part[r]);
+        }
+      }
+      if (++nsince >= s) {
+        P.fold();
+        nsince = 0;
+      }
+      fence_proxy_async();
+      __syncwarp();
+      done += TILE;
+      return true;
+    };
+
+    // ---- evaluation of the queued leaves (Listing 4)
+    int n_pp = 0;
+    auto eval_leaves = [&](int nq) {
+      const int c0 = lane < nq ? S.leafq[lane].y : 0;
+      const int c1 = lane + 32 < nq ? S.leafq[lane + 32].y : 0;
+      int s0 = c0, s1 = c1;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u0 = __shfl_up_sync(FULL, s0, o);
+        const int u1 = __shfl_up_sync(FULL, s1, o);
+        if (lane >= o) {
+          s0 += u0;
+          s1 += u1;
+        }
+      }
+      const int tot0 = __shfl_sync(FULL, s0, 31);
+      const int total = tot0 + __shfl_sync(FULL, s1, 31);
+      S.lpref[lane] = s0;
+      S.lpref[lane + 32] = s1 + tot0;
+      __syncwarp();
+      n_pp += total;
+      for (int base = 0; base < total; base += PCHUNK) {
+        const int nloc = min(PCHUNK, total - base);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int rk = base + lane + 32 * h;
+          if (rk < total) {
+            int lo = 0, hi = nq - 1;  // first entry whose inclusive prefix exceeds rk
+            while (lo < hi) {
+              const int mid = (lo + hi) >> 1;
+              if (S.lpref[mid] > rk) hi = mid; else lo = mid + 1;
+            }
+            const int start = lo ? S.lpref[lo - 1] : 0;
+            const int j = S.leafq[lo].x + (rk - start);
+            const float4 h4 = __ldg(p.parts + 2 * j);
+            const float4 l4 = __ldg(p.parts + 2 * j + 1);
+            S.src[lane + 32 * h] = make_float4((h4.x - chi.x) + (l4.x - clo.x),
+                                               (h4.y - chi.y) + (l4.y - clo.y),
+                                               (h4.z - chi.z) + (l4.z - clo.z), h4.w);
+            S.srcidx[lane + 32 * h] = j;
+          }
+        }
+        __syncwarp();
+        if (act) {
+          for (int e = sl; e < nloc; e += s) {
+            const float4 q = S.src[e];
+            const int j = S.srcidx[e];
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+              body_body(P.x[r], P.y[r], P.z[r], eps2, q, j != P.idx[r] ? q.w : 0.f, P.part[r]);
+          }
+        }
+        if (++nsince >= s) {
+          P.fold();
+          nsince = 0;
+        }
+        __syncwarp();
+      }
+    };
+
+    // ---- walk (Listing 1): root opened; children of up to 4 nodes per step
+    int top = 0, nlq = 0, n_pc = 0, n_leafent = 0;
+    bool ok = true;
+    {
+      const int2 rl = __ldg(p.link + it.x);
+      if (rl.y < 0) {
+        if (lane == 0) S.leafq[0] = make_int2(rl.x, -rl.y);
+        if (CAPTURE && lane == 0 && p.dbg_cap > 0) p.dbg_leaf[(size_t)item * p.dbg_cap] = it.x;
+        nlq = 1;
+        n_leafent = 1;
+      } else {
+        if (lane == 0) S.stack[0] = (rl.x << 3) | (rl.y - 1);
+        top = 1;
+      }
+      __syncwarp();
+    }
+    while (top > 0) {
+      if (app - done >= 2 * TILE) {
+        if (!eval_tile(TILE)) { ok = false; break; }
+      }
+      const int npop = min(4, top);
+      const int k = lane >> 3, slot = lane & 7;
+      const int packed = k < npop ? S.stack[top - npop + k] : 0;
+      top -= npop;
+      __syncwarp();
+      const int nch = (packed & 7) + 1;
+      bool valid = (k < npop) && (slot < nch);
+      const int c = (packed >> 3) + slot;
+      if (valid && static_cast<unsigned>(c) >= static_cast<unsigned>(p.n_cells)) {
+        status |= ST_INDEX;
+        valid = false;
+      }
+      float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+      int2 lk = make_int2(0, 0);
+      if (valid) {
+        g = __ldg(p.geo + c);
+        lk = __ldg(p.link + c);
+      }
+      const bool open = valid && must_open(g, gmin, gmax, theta2);
+      const bool leaf = lk.y < 0;
+      const unsigned m_acc = __ballot_sync(FULL, valid && !open);
+      const unsigned m_leaf = __ballot_sync(FULL, open && leaf);
+      const unsigned m_node = __ballot_sync(FULL, open && !leaf);
+      const int nn = __popc(m_node);
+      if (top + nn > STACK) {
+        status |= ST_STACK;
+        break;
+      }
+      if (open && !leaf) S.stack[top + __popc(m_node & lt)] = (lk.x << 3) | (lk.y - 1);
+      top += nn;
+      if (open && leaf) {
+        const int q = nlq + __popc(m_leaf & lt);
+        S.leafq[q] = make_int2(lk.x, -lk.y);
+        if (CAPTURE && n_leafent + __popc(m_leaf & lt) < p.dbg_cap)
+          p.dbg_leaf[(size_t)item * p.dbg_cap + n_leafent + __popc(m_leaf & lt)] = c;
+      }
+      nlq += __popc(m_leaf);
+      n_leafent += __popc(m_leaf);
+      if (valid && !open) {
+        const uint32_t e = app + __popc(m_acc & lt);
+        const uint32_t se = e % (NTILE * TILE);
+        const uint32_t bar = bar0 + 8 * (se / TILE);
+        mbar_expect_tx(bar, 64);
+        bulk_g2s(smem_u32(&S.ring[se * REC]), p.mp + 4 * (size_t)c, 64, bar);
+        if (CAPTURE && n_pc + __popc(m_acc & lt) < p.dbg_cap)
+          p.dbg_cell[(size_t)item * p.dbg_cap + n_pc + __popc(m_acc & lt)] = c;
+      }
+      const int na = __popc(m_acc);
+      const uint32_t old = app;
+      app += na;
+      n_pc += na;
+      __syncwarp();  // all expect_tx of this step precede the tile's arrival
+      if (lane == 0) {
+        for (uint32_t b = (old / TILE + 1) * TILE; b <= app; b += TILE)
+          mbar_arrive(bar0 + 8 * (((b - 1) / TILE) % NTILE));
+      }
+      __syncwarp();
+      if (nlq >= TILE) {
+        eval_leaves(nlq);
+        nlq = 0;
+      }
+    }
+    // ---- drain: close the partial tile, evaluate what is pending
+    {
+      const uint32_t rem = app % TILE;
+      const uint32_t real_end = app;
+      if (rem) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar0 + 8 * ((app / TILE) % NTILE));
+        app += TILE - rem;
+      }
+      while (done < app) {
+        const int n = static_cast<int>(min(static_cast<uint32_t>(TILE), real_end - done));
+        if (!ok) {
+          // a wait already failed: give the rest one bounded wait each, then stop
+          const uint32_t tile = (done / TILE) % NTILE;
+          mbar_wait_bounded(bar0 + 8 * tile, (done / (TILE * NTILE)) & 1u);
+          done += TILE;
+          continue;
+        }
+        if (!eval_tile(n)) ok = false;
+      }
+    }
+    if (!ok) {
+      status |= ST_TIMEOUT;
+      break;  // barrier phases are no longer trustworthy in this warp
+    }
+    if (nlq > 0) eval_leaves(nlq);
+    P.fold();
+
+    // ---- combine the slices (lane wl of slice 0 gathers lanes wl + k*w)
+    for (int kk = 1; kk < s; ++kk) {
+      const int src = min(31, lane + kk * w);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const float hx = __shfl_sync(FULL, P.hi[r].x, src), lx = __shfl_sync(FULL, P.lo[r].x, src);
+        const float hy = __shfl_sync(FULL, P.hi[r].y, src), ly = __shfl_sync(FULL, P.lo[r].y, src);
+        const float hz = __shfl_sync(FULL, P.hi[r].z, src), lz = __shfl_sync(FULL, P.lo[r].z, src);
+        const float hp = __shfl_sync(FULL, P.hi[r].p, src), lp = __shfl_sync(FULL, P.lo[r].p, src);
+        if (sl == 0) {
+          two_sum_into(P.hi[r].x, P.lo[r].x, hx);
+          P.lo[r].x += lx;
+          two_sum_into(P.hi[r].y, P.lo[r].y, hy);
+          P.lo[r].y += ly;
+          two_sum_into(P.hi[r].z, P.lo[r].z, hz);
+          P.lo[r].z += lz;
+          two_sum_into(P.hi[r].p, P.lo[r].p, hp);
+          P.lo[r].p += lp;
+        }
+      }
+    }
+    if (sl == 0) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (P.idx[r] >= 0) {
+          p.out[P.idx[r]] = make_float4(G * (P.hi[r].x + P.lo[r].x), G * (P.hi[r].y + P.lo[r].y),
+                                        G * (P.hi[r].z + P.lo[r].z), G * (P.hi[r].p + P.lo[r].p));
+        }
+      }
+    }
+    if (lane == 0) {
+      p.counts[item] = make_int2(n_pc, n_pp);
+      if (CAPTURE) p.dbg_n[item] = make_int2(n_pc, n_leafent);
+    }
+    if (status & ST_STACK) break;
+  }
+  status = static_cast<int>(__reduce_or_sync(FULL, static_cast<unsigned>(status)));
+  if (status && lane == 0) atomicOr(p.status, status);
+}
+
+template <int R, bool CAPTURE>
+cudaError_t launch_t(const KParams& p, int ctas_per_sm, cudaStream_t stream, LaunchInfo* info) {
+  const size_t smem = sizeof(WarpSmem) * WARPS;
+  auto kern = walk_eval_kernel<R, CAPTURE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, occ = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, WARPS * 32, smem)) != cudaSuccess)
+    return e;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  const int per_sm = ctas_per_sm > 0 ? min(ctas_per_sm, occ) : occ;
+  const int grid = sms * per_sm;
+  if (info) {
+    info->grid = grid;
+    info->block = WARPS * 32;
+    info->smem = smem;
+  }
+  kern<<<grid, WARPS * 32, smem, stream>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t walk_eval_smem_bytes() { return sizeof(WarpSmem) * WARPS; }
+
+cudaError_t launch_walk_eval(const KParams& p, int ppl, int ctas_per_sm, bool capture,
+                             cudaStream_t stream, LaunchInfo* info) {
+  if (ppl == 1) {
+    return capture ? launch_t<1, true>(p, ctas_per_sm, stream, info)
+                   : launch_t<1, false>(p, ctas_per_sm, stream, info);
+  }
+  return capture ? launch_t<2, true>(p, ctas_per_sm, stream, info)
+                 : launch_t<2, false>(p, ctas_per_sm, stream, info);
+}
+
+}  // namespace og

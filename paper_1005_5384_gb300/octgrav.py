@@ -1,0 +1,257 @@
+"""Thin ctypes binding of liboctgrav.so (the C ABI in include/octgrav.h).
+
+Argument marshalling only: every step of the force calculation runs inside the
+library (host FP64 octree build, sm_103a walk + evaluation kernel). There is no
+Python or CPU fallback: if the library cannot be built or loaded, the calls
+raise.
+
+Device buffers and streams may come from PyTorch: ``Tree.forces_device``
+accepts a CUDA tensor of shape [n, 4] (float32) as its output and the handle of
+a torch stream (default: the current stream).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+OK = 0
+ERR_ARG, ERR_CUDA, ERR_OOM, ERR_STACK, ERR_LIST, ERR_TIMEOUT, ERR_NONFINITE, ERR_STATE, ERR_INDEX = \
+    -1, -2, -3, -4, -5, -6, -7, -8, -9
+MAX_DEPTH = 21
+MAX_ITEM = 64
+
+_lock = threading.Lock()
+_lib = None
+
+_f64 = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_i64 = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+_vp = C.c_void_p
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "octgrav_version": (C.c_int, []),
+    "octgrav_last_error": (C.c_char_p, []),
+    "octgrav_build_tree": (C.c_int, [_f64, _f64, C.c_int64, C.c_int, C.c_int, C.POINTER(_vp)]),
+    "octgrav_build_batch": (C.c_int, [C.c_int, _i64, _f64, _f64, C.c_int, C.c_int, C.POINTER(_vp)]),
+    "octgrav_tree_upload": (C.c_int, [_vp, _vp]),
+    "octgrav_forces_device": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double, _vp, _vp]),
+    "octgrav_set_system_params": (C.c_int, [_vp, _vp, _vp]),
+    "octgrav_forces_tree": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double, _vp, _vp, _vp]),
+    "octgrav_forces": (C.c_int, [_f64, _f64, C.c_int64, C.c_double, C.c_double, C.c_int, _vp, _vp]),
+    "octgrav_forces_ex": (C.c_int, [_f64, _f64, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_int,
+                                    C.c_int, _vp, _vp, _vp]),
+    "octgrav_status": (C.c_int, [_vp, _vp]),
+    "octgrav_tree_stats": (C.c_int, [_vp, _i64, C.c_int]),
+    "octgrav_tree_perm": (C.c_int, [_vp, _i64]),
+    "octgrav_tree_cell_keys": (C.c_int, [_vp, _vp]),
+    "octgrav_tree_cell_props": (C.c_int, [_vp] + [_vp] * 7),
+    "octgrav_item_info": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "octgrav_interaction_counts": (C.c_int, [_vp, _i64, _vp]),
+    "octgrav_debug_lists": (C.c_int, [_vp, C.c_double, C.c_int, _vp, _vp, _vp, _vp, _vp]),
+    "octgrav_set_launch": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "octgrav_free_tree": (None, [_vp]),
+}
+
+
+class OctgravError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("octgrav error %d: %s" % (code, msg))
+        self.code = code
+
+
+def load(path: str | None = None):
+    """Build (if stale) and load liboctgrav.so; raises if that is impossible."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = C.CDLL(path or _build.build())
+        for name, (res, args) in _SIGS.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def exported_symbols():
+    return sorted(_SIGS)
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise OctgravError(rc, load().octgrav_last_error().decode(errors="replace"))
+
+
+def _p(a):
+    return None if a is None else C.c_void_p(a.ctypes.data)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _pm(pos, mass):
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1)
+    mass = np.ascontiguousarray(mass, dtype=np.float64)
+    if pos.shape[0] != 3 * mass.shape[0]:
+        raise ValueError("pos must have shape [n, 3] matching mass [n]")
+    return pos, mass
+
+
+class Tree:
+    """An octgrav_tree handle (host FP64 tree + library-owned device arrays)."""
+
+    def __init__(self, handle, n: int):
+        self._h = C.c_void_p(handle)
+        self.n = n
+        self.stats = self._stats()
+
+    # ---- construction
+    @classmethod
+    def build(cls, pos, mass, n_leaf: int = 16, n_group: int | None = None) -> "Tree":
+        lib = load()
+        pos, mass = _pm(pos, mass)
+        h = C.c_void_p()
+        _check(lib.octgrav_build_tree(pos, mass, mass.shape[0], int(n_leaf),
+                                      int(n_group if n_group is not None else n_leaf), C.byref(h)))
+        return cls(h.value, mass.shape[0])
+
+    @classmethod
+    def build_batch(cls, systems, n_leaf: int = 16, n_group: int | None = None) -> "Tree":
+        """systems: list of (pos [n_s,3], mass [n_s]) pairs."""
+        lib = load()
+        pos = np.ascontiguousarray(np.concatenate([np.asarray(p, np.float64).reshape(-1, 3) for p, _ in systems]))
+        mass = np.ascontiguousarray(np.concatenate([np.asarray(m, np.float64) for _, m in systems]))
+        off = np.zeros(len(systems) + 1, np.int64)
+        off[1:] = np.cumsum([len(m) for _, m in systems])
+        h = C.c_void_p()
+        _check(lib.octgrav_build_batch(len(systems), off, pos.reshape(-1), mass, int(n_leaf),
+                                       int(n_group if n_group is not None else n_leaf), C.byref(h)))
+        t = cls(h.value, int(off[-1]))
+        t.offsets = off
+        return t
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.octgrav_free_tree(h)
+            self._h = None
+
+    def free(self):
+        self.__del__()
+
+    # ---- introspection
+    def _stats(self):
+        out = np.zeros(8, np.int64)
+        _check(load().octgrav_tree_stats(self._h, out, 8))
+        keys = ("n", "n_cells", "n_leaves", "n_groups", "n_items", "depth", "n_sys", "max_group")
+        return dict(zip(keys, (int(v) for v in out)))
+
+    def perm(self) -> np.ndarray:
+        out = np.zeros(self.n, np.int64)
+        _check(load().octgrav_tree_perm(self._h, out))
+        return out
+
+    def cell_keys(self) -> np.ndarray:
+        out = np.zeros(self.stats["n_cells"], np.uint64)
+        _check(load().octgrav_tree_cell_keys(self._h, _p(out)))
+        return out
+
+    def cell_props(self) -> dict:
+        nc = self.stats["n_cells"]
+        d = dict(bmin=np.zeros((nc, 3)), bmax=np.zeros((nc, 3)), cube=np.zeros((nc, 4)), mass=np.zeros(nc),
+                 com=np.zeros((nc, 3)), S=np.zeros((nc, 6)), count=np.zeros(nc, np.int64))
+        _check(load().octgrav_tree_cell_props(self._h, *[_p(d[k]) for k in
+                                                         ("bmin", "bmax", "cube", "mass", "com", "S", "count")]))
+        return d
+
+    def item_info(self) -> dict:
+        ni = self.stats["n_items"]
+        d = dict(group_key=np.zeros(ni, np.uint64), first=np.zeros(ni, np.int64), count=np.zeros(ni, np.int32),
+                 sys=np.zeros(ni, np.int32))
+        _check(load().octgrav_item_info(self._h, _p(d["group_key"]), _p(d["first"]), _p(d["count"]), _p(d["sys"])))
+        return d
+
+    # ---- configuration
+    def set_launch(self, particles_per_lane: int = 2, ctas_per_sm: int = 0):
+        _check(load().octgrav_set_launch(self._h, int(particles_per_lane), int(ctas_per_sm)))
+        self.stats = self._stats()
+
+    def set_system_params(self, eps=None, theta=None):
+        if eps is None and theta is None:
+            _check(load().octgrav_set_system_params(self._h, None, None))
+            return
+        e = np.ascontiguousarray(eps, dtype=np.float64)
+        t = np.ascontiguousarray(theta, dtype=np.float64)
+        self._sysp_keep = (e, t)
+        _check(load().octgrav_set_system_params(self._h, _p(e), _p(t)))
+
+    # ---- device work
+    def upload(self, stream=None):
+        _check(load().octgrav_tree_upload(self._h, _stream_handle(stream)))
+
+    def forces_device(self, eps: float, theta: float, out, G: float = 1.0, stream=None):
+        """Launch on the GPU; ``out`` is a CUDA float32 tensor [n, 4] (tree order) or a raw pointer."""
+        ptr = out if isinstance(out, int) else out.data_ptr()
+        _check(load().octgrav_forces_device(self._h, float(eps), float(theta), float(G), C.c_void_p(ptr),
+                                            _stream_handle(stream)))
+
+    def forces(self, eps: float, theta: float, G: float = 1.0, stream=None):
+        """Host outputs in input order: (acc [n,3], pot [n]) as float64 arrays."""
+        acc = np.zeros((self.n, 3))
+        pot = np.zeros(self.n)
+        _check(load().octgrav_forces_tree(self._h, float(eps), float(theta), float(G), _p(acc), _p(pot),
+                                          _stream_handle(stream)))
+        return acc, pot
+
+    def status(self, stream=None) -> int:
+        return int(load().octgrav_status(self._h, _stream_handle(stream)))
+
+    def interaction_counts(self, stream=None) -> dict:
+        out = np.zeros(3, np.int64)
+        _check(load().octgrav_interaction_counts(self._h, out, _stream_handle(stream)))
+        return dict(n_pp=int(out[0]), n_pc=int(out[1]), flops=int(out[2]))
+
+    def debug_lists(self, theta: float, cap: int = 8192, stream=None):
+        """Per work item: (sorted cell-list keys, sorted leaf-list keys)."""
+        ni = self.stats["n_items"]
+        ck = np.zeros((ni, cap), np.uint64)
+        lk = np.zeros((ni, cap), np.uint64)
+        nc = np.zeros(ni, np.int32)
+        nl = np.zeros(ni, np.int32)
+        _check(load().octgrav_debug_lists(self._h, float(theta), int(cap), _p(ck), _p(nc), _p(lk), _p(nl),
+                                          _stream_handle(stream)))
+        return [(np.sort(ck[k, :nc[k]]), np.sort(lk[k, :nl[k]])) for k in range(ni)]
+
+
+def forces(pos, mass, eps: float, theta: float, n_leaf: int = 16, n_group: int | None = None, G: float = 1.0,
+           stream=None):
+    """One-shot C-ABI call with host buffers: (acc [n,3], pot [n]) in input order."""
+    lib = load()
+    pos, mass = _pm(pos, mass)
+    n = mass.shape[0]
+    acc = np.zeros((n, 3))
+    pot = np.zeros(n)
+    _check(lib.octgrav_forces_ex(pos, mass, n, float(eps), float(theta), float(G), int(n_leaf),
+                                 int(n_group if n_group is not None else n_leaf), _p(acc), _p(pot),
+                                 _stream_handle(stream)))
+    return acc, pot
+
+
+def version() -> int:
+    return int(load().octgrav_version())

@@ -1,0 +1,118 @@
+"""CPU-only checks of the C-ABI library: it loads, exports every symbol the
+header declares, validates its arguments without touching a GPU, and its host
+FP64 octree equals the oracle's tree cell for cell."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1005_5384_gb300 import octgrav as G
+from paper_1005_5384_gb300 import workloads as W
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "octgrav.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(octgrav_\w+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = G.load()
+    names = _declared()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(G.exported_symbols())
+    assert G.version() >= 10000
+
+
+@pytest.mark.parametrize("n,n_leaf,n_group", [(1, 1, 1), (2, 1, 1), (37, 4, 8), (3000, 8, 24), (20000, 16, 64)])
+def test_host_tree_equals_oracle_tree(n, n_leaf, n_group):
+    pos, m = W.plummer(n, seed=n + 3) if n > 2 else (np.array([[0.0, 0, 0], [1, 2, 3]])[:n], np.ones(n))
+    T = G.Tree.build(pos, m, n_leaf, n_group)
+    R = O.Tree(pos, m, n_leaf, n_group)
+    k = T.cell_keys()
+    assert T.stats["n_cells"] == R.n_cells and T.stats["n_leaves"] == R.n_leaves
+    assert T.stats["n_groups"] == R.n_groups
+    ol, oo = np.argsort(k), np.argsort(R.key)
+    assert np.array_equal(k[ol], R.key[oo])
+    p = T.cell_props()
+    # boxes and cubes are exact min/max and x0.5 results: bit-identical
+    assert np.array_equal(p["bmin"][ol], R.bmin[oo]) and np.array_equal(p["bmax"][ol], R.bmax[oo])
+    assert np.array_equal(p["cube"][ol], R.cube[oo])
+    assert np.array_equal(p["count"][ol], R.count[oo])
+    # moments: parallel-axis combination vs direct sums, rounding only
+    np.testing.assert_allclose(p["mass"][ol], R.M[oo], rtol=1e-11)
+    np.testing.assert_allclose(p["com"][ol], R.com[oo], rtol=1e-11, atol=1e-12)
+    np.testing.assert_allclose(p["S"][ol], R.S[oo], rtol=1e-9, atol=1e-13 * max(1e-300, abs(R.S).max()))
+    info = T.item_info()
+    assert np.array_equal(np.unique(info["group_key"]), np.sort(R.key[R.groups]))
+    assert info["count"].sum() == n and info["count"].max() <= G.MAX_ITEM
+    perm = T.perm()
+    assert np.array_equal(np.sort(perm), np.arange(n))
+
+
+def test_batch_tree_is_concatenation_of_systems():
+    systems = [W.plummer(n, seed=s) for s, n in ((1, 300), (2, 1000), (3, 17))]
+    T = G.Tree.build_batch(systems, 8, 16)
+    assert T.stats["n_sys"] == 3
+    info = T.item_info()
+    perm = T.perm()
+    off = np.cumsum([0] + [len(m) for _, m in systems])
+    for s, (pos, m) in enumerate(systems):
+        R = O.Tree(pos, m, 8, 16)
+        sel = info["sys"] == s
+        assert np.array_equal(np.unique(info["group_key"][sel]), np.sort(R.key[R.groups]))
+        assert info["count"][sel].sum() == len(m)
+        seg = perm[off[s]:off[s + 1]]
+        assert np.array_equal(np.sort(seg), np.arange(off[s], off[s + 1]))
+
+
+def test_invalid_arguments_are_rejected_without_a_gpu():
+    pos, m = W.plummer(100, seed=1)
+    with pytest.raises(G.OctgravError) as e:
+        G.Tree.build(pos, m, 0, 0)
+    assert e.value.code == G.ERR_ARG
+    with pytest.raises(G.OctgravError) as e:
+        G.Tree.build(pos, m, 16, 8)
+    assert e.value.code == G.ERR_ARG
+    bad = pos.copy()
+    bad[7, 1] = np.nan
+    with pytest.raises(G.OctgravError) as e:
+        G.Tree.build(bad, m, 16)
+    assert e.value.code == G.ERR_NONFINITE
+    neg = m.copy()
+    neg[3] = -1.0
+    with pytest.raises(G.OctgravError) as e:
+        G.Tree.build(pos, neg, 16)
+    assert e.value.code == G.ERR_NONFINITE
+    for eps, theta in ((0.0, 0.5), (-1.0, 0.5), (0.01, -0.1), (float("nan"), 0.5), (0.01, float("inf"))):
+        with pytest.raises(G.OctgravError) as e:
+            G.forces(pos, m, eps, theta)
+        assert e.value.code == G.ERR_ARG
+        T = G.Tree.build(pos, m, 16)
+        with pytest.raises(G.OctgravError) as e:
+            T.forces(eps, theta)
+        assert e.value.code == G.ERR_ARG
+    T = G.Tree.build(pos, m, 16)
+    with pytest.raises(G.OctgravError) as e:
+        T.set_launch(3)
+    assert e.value.code == G.ERR_ARG
+    assert T.status() == G.ERR_STATE          # no launch yet
+
+
+def test_item_split_for_large_groups():
+    pos = np.zeros((150, 3))
+    pos[:140] = [0.5, 0.5, 0.5]          # 140 coincident particles: one max-depth leaf
+    pos[140:] = np.random.default_rng(3).random((10, 3))
+    m = np.full(150, 1 / 150)
+    T = G.Tree.build(pos, m, 4, 4)
+    info = T.item_info()
+    assert info["count"].max() <= 64 and info["count"].sum() == 150
+    assert T.stats["max_group"] == 140
+    T.set_launch(1)
+    assert T.item_info()["count"].max() <= 32

@@ -1,0 +1,168 @@
+"""GPU parity: the sm_103a walk + evaluation kernel against the FP64 CPU oracle.
+
+Interaction lists must equal the oracle's bit for bit as multisets of cell
+keys; accelerations must agree within 1e-5 relative RMS (FP32 evaluation vs
+FP64 oracle on the same lists). Every call goes through the C ABI.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1005_5384_gb300 import octgrav as G
+from paper_1005_5384_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL_RMS = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    G.load()
+    return torch
+
+
+def _list_parity(pos, m, n_leaf, n_group, theta, ppl=2):
+    T = G.Tree.build(pos, m, n_leaf, n_group)
+    T.set_launch(ppl)
+    R = O.Tree(pos, m, n_leaf, n_group)
+    gl = T.debug_lists(theta, cap=max(4096, R.n_cells))
+    info = T.item_info()
+    okey = {int(R.key[c]): g for g, c in enumerate(R.groups)}
+    checked = 0
+    for k, (ck, lk) in enumerate(gl):
+        g = okey[int(info["group_key"][k])]
+        rc, rl = R.list_keys(g, theta)
+        assert np.array_equal(ck, rc), (k, len(ck), len(rc))
+        assert np.array_equal(lk, rl), (k, len(lk), len(rl))
+        checked += 1
+    assert checked == T.stats["n_items"]
+    return T, R
+
+
+@pytest.mark.parametrize("theta", [0.0, 0.5, 0.75, 1.2])
+@pytest.mark.parametrize("n_group", [16, 64])
+def test_lists_bit_exact_plummer(theta, n_group):
+    pos, m = W.plummer(16384, seed=1)
+    _list_parity(pos, m, 16, n_group, theta)
+
+
+@pytest.mark.parametrize("ppl", [1, 2])
+def test_lists_bit_exact_clustered(ppl):
+    pos, m = W.clustered(20000, 8, seed=3)
+    _list_parity(pos, m, 16, 48, 0.5, ppl)
+
+
+def _force_parity(pos, m, n_leaf, n_group, eps, theta, ppl=2, G_=1.0):
+    T = G.Tree.build(pos, m, n_leaf, n_group)
+    T.set_launch(ppl)
+    acc, pot = T.forces(eps, theta, G=G_)
+    R = O.Tree(pos, m, n_leaf, n_group)
+    ra, rp, _, _, _ = R.forces(eps, theta, G=G_)
+    err = O.rel_rms(acc, ra)
+    perr = float(np.linalg.norm(pot - rp) / np.linalg.norm(rp))
+    assert err <= TOL_RMS, err
+    assert perr <= TOL_RMS, perr
+    return T, acc, pot
+
+
+def test_forces_plummer_16k_matches_oracle_and_direct():
+    pos, m = W.plummer(16384, seed=1)
+    T, acc, pot = _force_parity(pos, m, 16, 16, 0.01, 0.5)
+    ad, pd = O.direct(pos, m, 0.01)
+    e = O.rel_err(acc, ad)
+    assert np.median(e) < 1e-3
+    c = T.interaction_counts()
+    R = O.Tree(pos, m, 16, 16)
+    _, _, npp, npc, _ = R.forces(0.01, 0.5)
+    assert c["n_pp"] == int(npp.sum()) and c["n_pc"] == int(npc.sum())
+
+
+@pytest.mark.parametrize("ppl,n_group", [(1, 16), (1, 32), (2, 64), (2, 48)])
+def test_forces_lane_mappings(ppl, n_group):
+    pos, m = W.plummer(12000, seed=7)
+    _force_parity(pos, m, 16, n_group, 0.01, 0.6, ppl=ppl)
+
+
+def test_forces_clustered_fp32_hard_case():
+    """64 tight clusters, eps = 1e-3: separations ~1e-4 at |x| ~ 1."""
+    pos, m = W.clustered(65536, 64, seed=3)
+    _force_parity(pos, m, 16, 64, 0.001, 0.5)
+
+
+def test_theta_zero_equals_direct_sum():
+    pos, m = W.plummer(4096, seed=13)
+    T = G.Tree.build(pos, m, 16, 16)
+    acc, pot = T.forces(0.01, 0.0)
+    ad, pd = O.direct(pos, m, 0.01)
+    assert O.rel_rms(acc, ad) <= TOL_RMS
+    assert float(np.linalg.norm(pot - pd) / np.linalg.norm(pd)) <= TOL_RMS
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 17, 65, 129, 1000])
+def test_ragged_and_tiny_inputs(n):
+    pos, m = W.uniform_cube(n, seed=n)
+    eps = 0.05
+    acc, pot = G.forces(pos, m, eps, 0.7, n_leaf=1 if n < 20 else 4, n_group=4 if n < 20 else 8)
+    if n == 1:
+        assert np.all(acc == 0) and np.all(pot == 0)
+        return
+    ad, pd = O.direct(pos, m, eps)
+    R = O.Tree(pos, m, 1 if n < 20 else 4, 4 if n < 20 else 8)
+    ra, rp, _, _, _ = R.forces(eps, 0.7)
+    assert O.rel_rms(acc, ra) <= TOL_RMS
+    assert float(np.linalg.norm(pot - rp) / np.linalg.norm(rp)) <= TOL_RMS
+
+
+def test_coincident_particles_and_split_items():
+    """A max-depth leaf with 140 coincident particles is split over 3 warps."""
+    rng = np.random.default_rng(5)
+    pos = np.zeros((300, 3))
+    pos[:140] = [0.3, 0.3, 0.3]
+    pos[140:] = rng.random((160, 3))
+    m = np.full(300, 1 / 300)
+    T = G.Tree.build(pos, m, 4, 8)
+    assert T.stats["max_group"] == 140
+    acc, pot = T.forces(0.02, 0.5)
+    R = O.Tree(pos, m, 4, 8)
+    ra, rp, _, _, _ = R.forces(0.02, 0.5)
+    assert O.rel_rms(acc, ra) <= TOL_RMS
+    assert float(np.linalg.norm(pot - rp) / np.linalg.norm(rp)) <= TOL_RMS
+
+
+def test_device_output_order_and_determinism(_cuda):
+    torch = _cuda
+    pos, m = W.plummer(30000, seed=2)
+    T = G.Tree.build(pos, m, 16, 64)
+    out = torch.empty((T.n, 4), dtype=torch.float32, device="cuda")
+    T.forces_device(0.01, 0.5, out)
+    torch.cuda.synchronize()
+    assert T.status() == G.OK
+    a1 = out.cpu().numpy().copy()
+    T.forces_device(0.01, 0.5, out)
+    a2 = out.cpu().numpy()
+    assert np.array_equal(a1, a2)                     # bitwise reproducible
+    acc, pot = T.forces(0.01, 0.5)
+    perm = T.perm()
+    np.testing.assert_array_equal(acc[perm], a1[:, :3].astype(np.float64))
+    np.testing.assert_array_equal(pot[perm], a1[:, 3].astype(np.float64))
+
+
+def test_full_size_plummer_sampled_groups():
+    """1,048,576-particle Plummer sphere at theta = 0.5 in the benchmark's launch
+    configuration; the oracle evaluates a seeded sample of 400 groups."""
+    pos, m = W.plummer(1 << 20, seed=1)
+    T = G.Tree.build(pos, m, 16, 64)
+    acc, pot = T.forces(0.01, 0.5)
+    R = O.Tree(pos, m, 16, 64)
+    gsel = np.unique(W.sample_indices(R.n_groups, 400, seed=9))
+    ra, rp, _, _, _ = R.forces(0.01, 0.5, groups=gsel, counts=False)
+    idx = np.concatenate([R.cell_members(int(R.groups[g])) for g in gsel])
+    assert O.rel_rms(acc[idx], ra[idx]) <= TOL_RMS
+    assert float(np.linalg.norm(pot[idx] - rp[idx]) / np.linalg.norm(rp[idx])) <= TOL_RMS
+    samp = idx[:: max(1, len(idx) // 512)]
+    ad, _ = O.direct(pos, m, 0.01, targets=samp)
+    assert np.median(O.rel_err(acc[samp], ad)) < 1e-3
