@@ -163,6 +163,31 @@ int octgrav_set_launch(octgrav_tree *t, int particles_per_lane, int ctas_per_sm)
 
 void octgrav_free_tree(octgrav_tree *t);
 
+#define OCTGRAV_NOALLOC_MAX_ITEMS 262144 /* work items accepted by octgrav_forces_noalloc */
+
+/* Allocation-free variant of octgrav_forces_device. The paper has no
+ * counterpart; it exists for callers that cannot allocate device memory at
+ * this point: a code whose own allocator (for instance PyTorch's caching
+ * allocator) owns every device byte, or a time-step loop that must not suffer
+ * the device-wide synchronisation that cudaMalloc/cudaFree can cause. The
+ * call makes no cudaMalloc, cudaFree or other allocating call.
+ *   arena: caller-allocated device memory that receives the tree's device
+ *     arrays (copied from the tree's host images on stream). Call once with
+ *     arena = NULL to get the size needed in *arena_bytes; otherwise
+ *     *arena_bytes is the arena's size and must be at least that.
+ *   acc4_dev, eps, theta, G, stream: as octgrav_forces_device (tree order).
+ * The status word, work-queue counter and per-item counts live in a
+ * fixed-size array inside the library (2 MiB + 256 B per GPU, kept until the
+ * process exits), so the tree may have at most OCTGRAV_NOALLOC_MAX_ITEMS work
+ * items (octgrav_tree_stats out[4]); larger trees get ERR_ARG. The first call
+ * on a device looks up that array's address with the device current; make it
+ * before any stream capture. All calls share the array: calls that overlap on
+ * the GPU race and give wrong results. The call waits for the stream and
+ * returns OK, ERR_STACK, ERR_TIMEOUT or ERR_INDEX like octgrav_status.
+ * octgrav_interaction_counts does not see these launches. */
+int octgrav_forces_noalloc(octgrav_tree *t, void *arena, size_t *arena_bytes, double eps,
+                           double theta, double G, float *acc4_dev, void *stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *octgrav_last_error(void);
 

@@ -1070,6 +1070,59 @@ int octgrav_set_launch(octgrav_tree* t, int particles_per_lane, int ctas_per_sm)
   return OCTGRAV_OK;
 }
 
+int octgrav_forces_noalloc(octgrav_tree* t, void* arena, size_t* arena_bytes, double eps, double theta,
+                           double G, float* acc4_dev, void* stream) {
+  if (!t || !arena_bytes) return fail(OCTGRAV_ERR_ARG, "NULL tree or arena_bytes");
+  // arena layout: the device arrays, each starting on a 256-byte boundary
+  const size_t sizes[7] = {t->parts.size() * sizeof(float4), t->geo.size() * sizeof(float4),
+                           t->link.size() * sizeof(int2),    t->mp.size() * sizeof(float4),
+                           t->items.size() * sizeof(int4),   t->ibox.size() * sizeof(float4),
+                           t->sysp.size() * sizeof(float4)};
+  size_t offs[7], total = 0;
+  for (int k = 0; k < 7; ++k) {
+    offs[k] = total;
+    total += (sizes[k] + 255) & ~static_cast<size_t>(255);
+  }
+  if (!arena) {
+    *arena_bytes = total;
+    return OCTGRAV_OK;
+  }
+  if (*arena_bytes < total)
+    return fail(OCTGRAV_ERR_ARG, "arena of %zu bytes is smaller than the %zu bytes needed", *arena_bytes, total);
+  if (reinterpret_cast<uintptr_t>(arena) % 256) return fail(OCTGRAV_ERR_ARG, "arena must be 256-byte aligned");
+  if (t->items.size() > static_cast<size_t>(OCTGRAV_NOALLOC_MAX_ITEMS))
+    return fail(OCTGRAV_ERR_ARG, "tree has %zu work items; the allocation-free path takes at most %d",
+                t->items.size(), OCTGRAV_NOALLOC_MAX_ITEMS);
+  if (!acc4_dev) return fail(OCTGRAV_ERR_ARG, "NULL output");
+  int rc = check_params(eps, theta, G);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* a = static_cast<char*>(arena);
+  const void* src[7] = {t->parts.data(), t->geo.data(), t->link.data(), t->mp.data(),
+                        t->items.data(), t->ibox.data(), t->sysp.data()};
+  for (int k = 0; k < 7; ++k)
+    if (sizes[k]) CUDA_TRY(cudaMemcpyAsync(a + offs[k], src[k], sizes[k], cudaMemcpyHostToDevice, st));
+  og::KParams p{};
+  p.parts = reinterpret_cast<const float4*>(a + offs[0]);
+  p.geo = reinterpret_cast<const float4*>(a + offs[1]);
+  p.link = reinterpret_cast<const int2*>(a + offs[2]);
+  p.mp = reinterpret_cast<const float4*>(a + offs[3]);
+  p.items = reinterpret_cast<const int4*>(a + offs[4]);
+  p.ibox = reinterpret_cast<const float4*>(a + offs[5]);
+  p.sysp = t->sysp.empty() ? nullptr : reinterpret_cast<const float4*>(a + offs[6]);
+  p.sys0 = make_float4(static_cast<float>(theta * theta), static_cast<float>(eps * eps), static_cast<float>(G), 0.f);
+  p.out = reinterpret_cast<float4*>(acc4_dev);
+  p.n_items = static_cast<int>(t->items.size());
+  p.n_cells = static_cast<int>(t->n_cells);
+  int bits = 0;
+  cudaError_t e = og::launch_walk_eval_noalloc(p, t->ppl, t->ctas_per_sm, st, &bits);
+  if (e != cudaSuccess) return fail(OCTGRAV_ERR_CUDA, "allocation-free launch failed: %s", cudaGetErrorString(e));
+  if (bits & og::ST_TIMEOUT) return fail(OCTGRAV_ERR_TIMEOUT, "device wait timed out (status %d)", bits);
+  if (bits & og::ST_INDEX) return fail(OCTGRAV_ERR_INDEX, "walk met an out-of-range cell index");
+  if (bits & og::ST_STACK) return fail(OCTGRAV_ERR_STACK, "walk overflowed its node stack");
+  return OCTGRAV_OK;
+}
+
 void octgrav_free_tree(octgrav_tree* t) {
   if (!t) return;
   t->own.release();

@@ -61,4 +61,12 @@ cudaError_t launch_walk_eval(const KParams& p, int ppl, int ctas_per_sm, bool ca
 // Shared memory per CTA of the fused kernel.
 size_t walk_eval_smem_bytes();
 
+// Allocation-free launch: like launch_walk_eval, but the status word, the
+// work-queue counter and the per-item counts live in a file-scope device
+// array (no cudaMalloc). p.status, p.work and p.counts are ignored; p.n_items
+// must not exceed OCTGRAV_NOALLOC_MAX_ITEMS. Waits for the stream and returns
+// the device status bits in *status_bits.
+cudaError_t launch_walk_eval_noalloc(KParams p, int ppl, int ctas_per_sm, cudaStream_t stream,
+                                     int* status_bits);
+
 }  // namespace og

@@ -28,6 +28,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
+#include "../../include/octgrav.h"
 #include "octgrav_internal.h"
 
 namespace og {
@@ -556,6 +559,66 @@ cudaError_t launch_walk_eval(const KParams& p, int ppl, int ctas_per_sm, bool ca
   }
   return capture ? launch_t<2, true>(p, ctas_per_sm, stream, info)
                  : launch_t<2, false>(p, ctas_per_sm, stream, info);
+}
+
+// ---------------------------------------------------------------- allocation-free launch
+//
+// Scratch of octgrav_forces_noalloc, for callers that must not allocate device
+// memory themselves or have the library do it (see include/octgrav.h).
+// Layout: bytes 0..3 status word, 4..7 work-queue counter, 256.. per-item
+// interaction counts (int2) for at most OCTGRAV_NOALLOC_MAX_ITEMS items
+// (2 MiB + 256 B in total). Every GPU that loads the library keeps this array
+// until the process exits. All calls share it: calls that overlap on the GPU
+// (two streams, or two threads) race on it and give wrong results.
+namespace {
+constexpr size_t kNoAllocHeader = 256;
+constexpr size_t kNoAllocBytes = kNoAllocHeader + sizeof(int2) * OCTGRAV_NOALLOC_MAX_ITEMS;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device. The first call on
+// a device looks it up (cudaGetSymbolAddress) with that device current; later
+// calls reuse the cached address.
+cudaError_t noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t launch_walk_eval_noalloc(KParams p, int ppl, int ctas_per_sm, cudaStream_t stream,
+                                     int* status_bits) {
+  if (p.n_items < 0 || p.n_items > OCTGRAV_NOALLOC_MAX_ITEMS) return cudaErrorInvalidValue;
+  void* base = nullptr;
+  cudaError_t e = noalloc_scratch(&base);
+  if (e != cudaSuccess) return e;
+  char* b = static_cast<char*>(base);
+  p.status = reinterpret_cast<int*>(b);
+  p.work = reinterpret_cast<unsigned*>(b + 4);
+  p.counts = reinterpret_cast<int2*>(b + kNoAllocHeader);
+  // the array keeps the previous call's contents: the status word and the
+  // work counter must start at zero
+  if ((e = cudaMemsetAsync(b, 0, 8, stream)) != cudaSuccess) return e;
+  if (p.n_items > 0 && (e = launch_walk_eval(p, ppl, ctas_per_sm, false, stream, nullptr)) != cudaSuccess)
+    return e;
+  int h = 0;
+  if ((e = cudaMemcpyAsync(&h, b, sizeof(int), cudaMemcpyDeviceToHost, stream)) != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return e;
+  *status_bits = h;
+  return cudaSuccess;
 }
 
 }  // namespace og

@@ -23,6 +23,7 @@ ERR_ARG, ERR_CUDA, ERR_OOM, ERR_STACK, ERR_LIST, ERR_TIMEOUT, ERR_NONFINITE, ERR
     -1, -2, -3, -4, -5, -6, -7, -8, -9
 MAX_DEPTH = 21
 MAX_ITEM = 64
+NOALLOC_MAX_ITEMS = 262144
 
 _lock = threading.Lock()
 _lib = None
@@ -54,6 +55,8 @@ _SIGS = {
     "octgrav_debug_lists": (C.c_int, [_vp, C.c_double, C.c_int, _vp, _vp, _vp, _vp, _vp]),
     "octgrav_set_launch": (C.c_int, [_vp, C.c_int, C.c_int]),
     "octgrav_free_tree": (None, [_vp]),
+    "octgrav_forces_noalloc": (C.c_int, [_vp, _vp, C.POINTER(C.c_size_t), C.c_double, C.c_double, C.c_double,
+                                         _vp, _vp]),
 }
 
 
@@ -218,6 +221,25 @@ class Tree:
         _check(load().octgrav_forces_tree(self._h, float(eps), float(theta), float(G), _p(acc), _p(pot),
                                           _stream_handle(stream)))
         return acc, pot
+
+    def noalloc_arena_bytes(self) -> int:
+        """Device bytes the caller must provide to forces_noalloc for this tree."""
+        need = C.c_size_t(0)
+        _check(load().octgrav_forces_noalloc(self._h, None, C.byref(need), 1.0, 0.5, 1.0, None, None))
+        return int(need.value)
+
+    def forces_noalloc(self, eps: float, theta: float, out, arena, G: float = 1.0, stream=None):
+        """Allocation-free launch: ``arena`` is caller-owned device memory (a CUDA
+        uint8 tensor of at least noalloc_arena_bytes() bytes, or (pointer, size));
+        ``out`` as for forces_device. Waits for the stream."""
+        if isinstance(arena, tuple):
+            ptr, size = arena
+        else:
+            ptr, size = arena.data_ptr(), arena.numel() * arena.element_size()
+        optr = out if isinstance(out, int) else out.data_ptr()
+        sz = C.c_size_t(size)
+        _check(load().octgrav_forces_noalloc(self._h, C.c_void_p(ptr), C.byref(sz), float(eps), float(theta),
+                                             float(G), C.c_void_p(optr), _stream_handle(stream)))
 
     def status(self, stream=None) -> int:
         return int(load().octgrav_status(self._h, _stream_handle(stream)))
