@@ -161,6 +161,13 @@ int octgrav_debug_lists(octgrav_tree *t, double theta, int cap, uint64_t *cell_k
  * later launches on this tree; n_items may change. Errors: ERR_ARG. */
 int octgrav_set_launch(octgrav_tree *t, int particles_per_lane, int ctas_per_sm);
 
+/* How the fused kernel stages accepted cell records into shared memory:
+ *   0 = one cp.async.bulk (64 B) per record, issued by the accepting lane;
+ *   1 = four 16-byte cp.async per record, issued by the accepting lane (default);
+ *   2 = TMA tile::gather4, four records per instruction.
+ * All modes compute identical results. Errors: ERR_ARG. */
+int octgrav_set_staging(octgrav_tree *t, int mode);
+
 void octgrav_free_tree(octgrav_tree *t);
 
 #define OCTGRAV_NOALLOC_MAX_ITEMS 262144 /* work items accepted by octgrav_forces_noalloc */

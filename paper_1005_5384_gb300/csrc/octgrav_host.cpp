@@ -534,6 +534,8 @@ struct octgrav_tree {
   int64_t n = 0;
   int n_leaf = 0, n_group = 0, n_sys = 0;
   int ppl = 2, ctas_per_sm = 0;
+  int stage = og::STAGING_ASYNC;
+  CUtensorMap mp_map;
   std::vector<int64_t> sys_off;   // particle offsets per system (n_sys + 1)
   std::vector<int64_t> cell_off;  // cell offsets per system (n_sys + 1)
   std::vector<int64_t> perm;      // tree position -> input index
@@ -665,11 +667,11 @@ int assemble(octgrav_tree* t, std::vector<SysTree>& sys) {
         }
         const double tr = s6[0] + s6[1] + s6[2];
         t->mp[4 * g] = make_float4(chi[0], chi[1], chi[2], static_cast<float>(T.M[c]));
-        t->mp[4 * g + 1] = make_float4(clo[0], clo[1], clo[2], static_cast<float>(0.5 * tr));
+        t->mp[4 * g + 1] = make_float4(clo[0], clo[1], clo[2], 0.f);
         t->mp[4 * g + 2] = make_float4(static_cast<float>(3.0 * s6[0]), static_cast<float>(3.0 * s6[1]),
                                        static_cast<float>(3.0 * s6[2]), static_cast<float>(3.0 * s6[3]));
         t->mp[4 * g + 3] = make_float4(static_cast<float>(3.0 * s6[4]), static_cast<float>(3.0 * s6[5]),
-                                       static_cast<float>(1.5 * tr), 0.f);
+                                       static_cast<float>(1.5 * tr), static_cast<float>(0.5 * tr));
         for (int d = 0; d < 3; ++d) {
           t->bmin[3 * g + d] = T.bmin[3 * c + d];
           t->bmax[3 * g + d] = T.bmax[3 * c + d];
@@ -773,6 +775,10 @@ int upload(octgrav_tree* t, cudaStream_t st) {
     return rc;
   if ((rc = D.counts.reserve(t->items.size() * sizeof(int2)))) return rc;
   if ((rc = D.ctl.reserve(64))) return rc;
+  {
+    cudaError_t e = og::encode_mp_map(&t->mp_map, D.mp.p, static_cast<int>(t->n_cells));
+    if (e != cudaSuccess) return fail(OCTGRAV_ERR_CUDA, "tensor map encode failed: %s", cudaGetErrorString(e));
+  }
   if (!t->sysp.empty()) {
     if ((rc = upload_vec(D.sysp, t->sysp, st))) return rc;
   }
@@ -804,6 +810,8 @@ og::KParams make_params(octgrav_tree* t, float4* out) {
   p.work = reinterpret_cast<unsigned*>(static_cast<char*>(D.ctl.p) + 4);
   p.n_items = static_cast<int>(t->items.size());
   p.n_cells = static_cast<int>(t->n_cells);
+  p.stage = t->stage;
+  p.mp_map = t->mp_map;
   return p;
 }
 
@@ -1114,12 +1122,24 @@ int octgrav_forces_noalloc(octgrav_tree* t, void* arena, size_t* arena_bytes, do
   p.out = reinterpret_cast<float4*>(acc4_dev);
   p.n_items = static_cast<int>(t->items.size());
   p.n_cells = static_cast<int>(t->n_cells);
+  p.stage = t->stage;
+  {
+    cudaError_t e = og::encode_mp_map(&p.mp_map, a + offs[3], static_cast<int>(t->n_cells));
+    if (e != cudaSuccess) return fail(OCTGRAV_ERR_CUDA, "tensor map encode failed: %s", cudaGetErrorString(e));
+  }
   int bits = 0;
   cudaError_t e = og::launch_walk_eval_noalloc(p, t->ppl, t->ctas_per_sm, st, &bits);
   if (e != cudaSuccess) return fail(OCTGRAV_ERR_CUDA, "allocation-free launch failed: %s", cudaGetErrorString(e));
   if (bits & og::ST_TIMEOUT) return fail(OCTGRAV_ERR_TIMEOUT, "device wait timed out (status %d)", bits);
   if (bits & og::ST_INDEX) return fail(OCTGRAV_ERR_INDEX, "walk met an out-of-range cell index");
   if (bits & og::ST_STACK) return fail(OCTGRAV_ERR_STACK, "walk overflowed its node stack");
+  return OCTGRAV_OK;
+}
+
+int octgrav_set_staging(octgrav_tree* t, int mode) {
+  if (!t) return fail(OCTGRAV_ERR_ARG, "tree is NULL");
+  if (mode < og::STAGING_BULK || mode > og::STAGING_GATHER4) return fail(OCTGRAV_ERR_ARG, "staging mode must be 0, 1 or 2");
+  t->stage = mode;
   return OCTGRAV_OK;
 }
 

@@ -2,6 +2,7 @@
 // the CUDA kernels (octgrav_kernels.cu). Not part of the public ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -25,7 +26,15 @@ enum : int {
 //   ibox  [3*ni] float4: (gmin.xyz, C_hi.x), (gmax.xyz, C_hi.y), (C_lo.xyz, C_hi.z)
 //                        group tight box (FP32-rounded) and group centre C (hi/lo)
 //   sysp  [nsys] float4: (fl32(theta^2), fl32(eps^2), -, -) (optional; G is sys0.z)
+// Staging of accepted cell records (KParams::stage).
+enum : int {
+  STAGING_BULK = 0,     // cp.async.bulk per record
+  STAGING_ASYNC = 1,    // 4 x 16-byte cp.async per record
+  STAGING_GATHER4 = 2,  // TMA tile::gather4, 4 records per instruction (needs mp_map)
+};
+
 struct KParams {
+  CUtensorMap mp_map;    // 2-D map of mp: rows = cells, 16 floats per row (gather4 staging)
   const float4* parts;
   const float4* geo;
   const int2* link;
@@ -40,6 +49,7 @@ struct KParams {
   unsigned* work;        // work-queue counter (zeroed before the launch)
   int n_items;
   int n_cells;
+  int stage;             // STAGING_*
   // capture mode (tests): per item up to dbg_cap cell indices
   int* dbg_cell;
   int* dbg_leaf;
@@ -60,6 +70,10 @@ cudaError_t launch_walk_eval(const KParams& p, int ppl, int ctas_per_sm, bool ca
 
 // Shared memory per CTA of the fused kernel.
 size_t walk_eval_smem_bytes();
+
+// Encode the 2-D tensor map over a cell-record array (n_cells rows of 64 B)
+// used by the gather4 staging. Returns cudaSuccess or an error.
+cudaError_t encode_mp_map(CUtensorMap* map, const void* mp, int n_cells);
 
 // Allocation-free launch: like launch_walk_eval, but the status word, the
 // work-queue counter and the per-item counts live in a file-scope device

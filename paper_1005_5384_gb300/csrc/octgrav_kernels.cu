@@ -6,8 +6,11 @@
 // test to the children of up to four popped nodes at once (one lane per child,
 // Listing 2), and compacts the three outcomes with warp ballots:
 //   accepted cell -> cell list: its 64-byte multipole record is fetched into a
-//                    shared-memory ring by a bulk async copy (cp.async.bulk,
-//                    completion on an mbarrier) the moment it is accepted;
+//                    shared-memory ring by an asynchronous copy issued right
+//                    after the step that accepted it (STAGE selects the copy:
+//                    TMA tile::gather4 of 4 records per instruction with
+//                    mbarrier completion, per-lane 16-byte cp.async, or one
+//                    cp.async.bulk per record);
 //   opened leaf   -> leaf queue (first particle, count);
 //   opened node   -> pushed on the stack as (first child, number of children).
 // Full tiles of 32 cell records are evaluated one walk step after their copies
@@ -40,21 +43,28 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int WARPS = 8;          // warps per CTA
 constexpr int TILE = 32;          // cell records per tile
 constexpr int NTILE = 3;          // tiles in the ring (copies run one step ahead)
-constexpr int REC = 5;            // float4 per ring slot: 64-byte record + 16-byte pad
+// Staging of accepted cell records into the shared-memory ring.
+constexpr int STAGE_BULK = 0;     // one cp.async.bulk (64 B) per record, issued by its lane
+constexpr int STAGE_ASYNC = 1;    // four 16-byte cp.async per record, issued by its lane
+constexpr int STAGE_GATHER4 = 2;  // TMA tile::gather4: 4 records per instruction, lane 0 issues
+template <int STAGE>
+struct RingStride {               // float4 per ring slot
+  static constexpr int v = STAGE == STAGE_GATHER4 ? 4 : 5;  // 64 B rows / 64 B + 16 B pad
+};
 constexpr int STACK = 512;        // node-stack entries per warp
 constexpr int PCHUNK = 64;        // source particles per particle-particle chunk
 constexpr int LQ = 64;            // leaf-queue entries (flushed at >= 32)
 constexpr long long WAIT_LIMIT = 1ll << 31;  // cycles (~1 s) before a wait gives up
 
-struct __align__(16) WarpSmem {
-  float4 ring[NTILE * TILE * REC];  // 7680 B; stride 80 B keeps 8 slots on 8 bank quads
+struct __align__(128) WarpSmem {
+  float4 ring[NTILE * TILE * 5];    // 7680 B; stride 80 B keeps 8 slots on 8 bank quads
+  int cidx[NTILE * TILE];           // 384 B: cell index per ring slot (gather4 staging)
   float4 src[PCHUNK];               // 1024 B: source (x', m)
   int srcidx[PCHUNK];               // 256 B: source tree index (self exclusion)
   int2 leafq[LQ];                   // 512 B: (first particle, count)
   int lpref[LQ];                    // 256 B: inclusive prefix of counts
   int stack[STACK];                 // 2048 B: packed (first child << 3 | n_child - 1)
   unsigned long long bar[NTILE];    // one mbarrier per ring tile
-  unsigned long long pad_;
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -98,6 +108,30 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
           "r"(dst),
       "l"(src), "r"(bytes), "r"(bar)
       : "memory");
+}
+// TMA gather of 4 rows (64-byte cell records) of a 2-D tensor map into
+// 256 contiguous bytes of shared memory; completion on bar.
+__device__ __forceinline__ void gather4_g2s(uint32_t dst, const void* tmap, int r0, int r1, int r2, int r3,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+      "l"(tmap), "r"(0), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(bar)
+      : "memory");
+}
+// Per-thread 16-byte asynchronous copy global -> shared (L1-allocating).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// Hardware reciprocal square root (MUFU), denormal inputs flushed; every
+// argument here is >= eps^2 > 0.
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 // Order this thread's generic-proxy shared-memory accesses before later
 // async-proxy (bulk copy) writes to the same locations.
@@ -149,11 +183,12 @@ struct Acc4 {
 // d = x_i - com, r^2 = |d|^2 + eps^2, S3 = 3S, q = d.S3.d, T = trS/2:
 //   a   += d (-M + (3T - 2.5 q/r^2)/r^2) / r^3 + S3 d / r^5
 //   phi -= (M + (q/(2 r^2) - T)/r^2) / r
+// q0 = (com, M), q2 = (S3xx, S3yy, S3zz, S3xy), q3 = (S3xz, S3yz, 3T, T).
 __device__ __forceinline__ void body_cell(float x, float y, float z, float eps2, float4 q0,
-                                          float T, float4 q2, float4 q3, Acc4& a) {
+                                          float4 q2, float4 q3, Acc4& a) {
   const float dx = x - q0.x, dy = y - q0.y, dz = z - q0.z;
   const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-  const float rinv = rsqrtf(r2);
+  const float rinv = rsqrt_ftz(r2);
   const float rinv2 = rinv * rinv;
   const float rinv3 = rinv * rinv2;
   const float rinv5 = rinv3 * rinv2;
@@ -167,7 +202,7 @@ __device__ __forceinline__ void body_cell(float x, float y, float z, float eps2,
   a.x = fmaf(cd, dx, fmaf(rinv5, sx, a.x));
   a.y = fmaf(cd, dy, fmaf(rinv5, sy, a.y));
   a.z = fmaf(cd, dz, fmaf(rinv5, sz, a.z));
-  const float p2 = fmaf(fmaf(0.5f, t1, -T), rinv2, q0.w);
+  const float p2 = fmaf(fmaf(0.5f, t1, -q3.w), rinv2, q0.w);
   a.p = fmaf(-p2, rinv, a.p);
 }
 
@@ -176,7 +211,7 @@ __device__ __forceinline__ void body_body(float x, float y, float z, float eps2,
                                           float mj, Acc4& a) {
   const float dx = s.x - x, dy = s.y - y, dz = s.z - z;
   const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-  const float rinv = rsqrtf(r2);
+  const float rinv = rsqrt_ftz(r2);
   const float mr = mj * rinv;
   const float mr3 = mr * rinv * rinv;
   a.x = fmaf(mr3, dx, a.x);
@@ -216,11 +251,14 @@ struct Particles {
 
 // ---------------------------------------------------------------- the kernel
 
-template <int R, bool CAPTURE>
-__global__ void __launch_bounds__(WARPS * 32, 2) walk_eval_kernel(const KParams p) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+template <int R, int STAGE, bool CAPTURE>
+__global__ void __launch_bounds__(WARPS * 32, 2) walk_eval_kernel(const __grid_constant__ KParams p) {
+  constexpr int REC = RingStride<STAGE>::v;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
-  WarpSmem& S = reinterpret_cast<WarpSmem*>(smem_raw)[threadIdx.x >> 5];
+  unsigned char* smem_base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+  WarpSmem& S = reinterpret_cast<WarpSmem*>(smem_base)[threadIdx.x >> 5];
   const uint32_t bar0 = smem_u32(&S.bar[0]);
   if (lane == 0) {
     for (int t = 0; t < NTILE; ++t) mbar_init(bar0 + 8 * t, 1);
@@ -233,6 +271,7 @@ __global__ void __launch_bounds__(WARPS * 32, 2) walk_eval_kernel(const KParams 
   // cell entries whose copies were issued, `done` those evaluated. Tile
   // (e / TILE) % NTILE holds entry e; its k-th use completes phase k.
   uint32_t app = 0, done = 0;
+  uint32_t iss = 0;  // gather4 staging: entries whose copies were issued (multiple of 4)
   int status = 0;
 
   for (;;) {
@@ -282,7 +321,11 @@ __global__ void __launch_bounds__(WARPS * 32, 2) walk_eval_kernel(const KParams 
     auto eval_tile = [&](int n) -> bool {
       const uint32_t tile = (done / TILE) % NTILE;
       const uint32_t parity = (done / (TILE * NTILE)) & 1u;
-      if (!mbar_wait_bounded(bar0 + 8 * tile, parity)) return false;
+      if (STAGE == STAGE_ASYNC) {
+        __syncwarp();  // the lanes' completed copies (waited by the caller) are visible
+      } else if (!mbar_wait_bounded(bar0 + 8 * tile, parity)) {
+        return false;
+      }
       float4* base = &S.ring[tile * TILE * REC];
       if (lane < n) {  // centre of mass relative to the group centre
         float4 q0 = base[lane * REC];
@@ -294,20 +337,30 @@ __global__ void __launch_bounds__(WARPS * 32, 2) walk_eval_kernel(const KParams 
       }
       __syncwarp();
       if (act) {
-        for (int e = sl; e < n; e += s) {
-          const float4 q0 = base[e * REC];
-          const float T = base[e * REC + 1].w;
-          const float4 q2 = base[e * REC + 2];
-          const float4 q3 = base[e * REC + 3];
+        int e = sl;
+        for (; e + s < n; e += 2 * s) {  // two records per iteration: 2R independent chains
+          const float4* ra = base + e * REC;
+          const float4* rb = base + (e + s) * REC;
+          const float4 a0 = ra[0], a2 = ra[2], a3 = ra[3];
+          const float4 c0 = rb[0], c2 = rb[2], c3 = rb[3];
 #pragma unroll
-          for (int r = 0; r < R; ++r) body_cell(P.x[r], P.y[r], P.z[r], eps2, q0, T, q2, q3, P.part[r]);
+          for (int r = 0; r < R; ++r) {
+            body_cell(P.x[r], P.y[r], P.z[r], eps2, a0, a2, a3, P.part[r]);
+            body_cell(P.x[r], P.y[r], P.z[r], eps2, c0, c2, c3, P.part[r]);
+          }
+        }
+        if (e < n) {
+          const float4* ra = base + e * REC;
+          const float4 a0 = ra[0], a2 = ra[2], a3 = ra[3];
+#pragma unroll
+          for (int r = 0; r < R; ++r) body_cell(P.x[r], P.y[r], P.z[r], eps2, a0, a2, a3, P.part[r]);
         }
       }
       if (++nsince >= s) {
         P.fold();
         nsince = 0;
       }
-      fence_proxy_async();
+      if (STAGE != STAGE_ASYNC) fence_proxy_async();
       __syncwarp();
       done += TILE;
       return true;
@@ -391,6 +444,8 @@ __global__ void __launch_bounds__(WARPS * 32, 2) walk_eval_kernel(const KParams 
     }
     while (top > 0) {
       if (app - done >= 2 * TILE) {
+        // the oldest tile is complete and its copies were issued at least one step ago
+        if (STAGE == STAGE_ASYNC) cp_async_wait_1();
         if (!eval_tile(TILE)) { ok = false; break; }
       }
       const int npop = min(4, top);
@@ -434,9 +489,18 @@ __global__ void __launch_bounds__(WARPS * 32, 2) walk_eval_kernel(const KParams 
       if (valid && !open) {
         const uint32_t e = app + __popc(m_acc & lt);
         const uint32_t se = e % (NTILE * TILE);
-        const uint32_t bar = bar0 + 8 * (se / TILE);
-        mbar_expect_tx(bar, 64);
-        bulk_g2s(smem_u32(&S.ring[se * REC]), p.mp + 4 * (size_t)c, 64, bar);
+        if (STAGE == STAGE_BULK) {
+          const uint32_t bar = bar0 + 8 * (se / TILE);
+          mbar_expect_tx(bar, 64);
+          bulk_g2s(smem_u32(&S.ring[se * REC]), p.mp + 4 * (size_t)c, 64, bar);
+        } else if (STAGE == STAGE_ASYNC) {
+          const uint32_t dst = smem_u32(&S.ring[se * REC]);
+          const float4* src = p.mp + 4 * (size_t)c;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) cp_async16(dst + 16 * q, src + q);
+        } else {
+          S.cidx[se] = c;
+        }
         if (CAPTURE && n_pc + __popc(m_acc & lt) < p.dbg_cap)
           p.dbg_cell[(size_t)item * p.dbg_cap + n_pc + __popc(m_acc & lt)] = c;
       }
@@ -444,10 +508,25 @@ __global__ void __launch_bounds__(WARPS * 32, 2) walk_eval_kernel(const KParams 
       const uint32_t old = app;
       app += na;
       n_pc += na;
-      __syncwarp();  // all expect_tx of this step precede the tile's arrival
-      if (lane == 0) {
+      if (STAGE == STAGE_ASYNC) cp_async_commit();
+      __syncwarp();  // all expect_tx / index writes of this step are done
+      if (STAGE == STAGE_BULK && lane == 0) {
         for (uint32_t b = (old / TILE + 1) * TILE; b <= app; b += TILE)
           mbar_arrive(bar0 + 8 * (((b - 1) / TILE) % NTILE));
+      }
+      if (STAGE == STAGE_GATHER4) {
+        const uint32_t upto = app & ~3u;
+        if (lane == 0) {
+          for (uint32_t k = iss; k < upto; k += 4) {
+            const uint32_t sk = k % (NTILE * TILE);
+            const uint32_t bar = bar0 + 8 * (sk / TILE);
+            const int4 r4 = *reinterpret_cast<const int4*>(&S.cidx[sk]);
+            mbar_expect_tx(bar, 256);
+            gather4_g2s(smem_u32(&S.ring[sk * REC]), &p.mp_map, r4.x, r4.y, r4.z, r4.w, bar);
+            if ((k + 4) % TILE == 0) mbar_arrive(bar);
+          }
+        }
+        iss = upto;
       }
       __syncwarp();
       if (nlq >= TILE) {
@@ -459,17 +538,36 @@ __global__ void __launch_bounds__(WARPS * 32, 2) walk_eval_kernel(const KParams 
     {
       const uint32_t rem = app % TILE;
       const uint32_t real_end = app;
-      if (rem) {
+      if (STAGE == STAGE_ASYNC) {
+        cp_async_wait_all();
         __syncwarp();
-        if (lane == 0) mbar_arrive(bar0 + 8 * ((app / TILE) % NTILE));
+        if (rem) app += TILE - rem;
+      } else if (rem) {
+        __syncwarp();
+        if (lane == 0) {
+          const uint32_t bar = bar0 + 8 * ((app / TILE) % NTILE);
+          if (STAGE == STAGE_GATHER4 && iss < app) {
+            // last partial group of 4: pad with the first index; the padded
+            // slots lie beyond the item's last entry and are never read
+            const uint32_t sk = iss % (NTILE * TILE);
+            int4 r4 = *reinterpret_cast<const int4*>(&S.cidx[sk]);
+            if (app - iss < 2) r4.y = r4.x;
+            if (app - iss < 3) r4.z = r4.x;
+            r4.w = r4.x;
+            mbar_expect_tx(bar, 256);
+            gather4_g2s(smem_u32(&S.ring[sk * REC]), &p.mp_map, r4.x, r4.y, r4.z, r4.w, bar);
+          }
+          mbar_arrive(bar);
+        }
         app += TILE - rem;
+        iss = app;
       }
       while (done < app) {
         const int n = static_cast<int>(min(static_cast<uint32_t>(TILE), real_end - done));
         if (!ok) {
           // a wait already failed: give the rest one bounded wait each, then stop
           const uint32_t tile = (done / TILE) % NTILE;
-          mbar_wait_bounded(bar0 + 8 * tile, (done / (TILE * NTILE)) & 1u);
+          if (STAGE != STAGE_ASYNC) mbar_wait_bounded(bar0 + 8 * tile, (done / (TILE * NTILE)) & 1u);
           done += TILE;
           continue;
         }
@@ -523,10 +621,10 @@ __global__ void __launch_bounds__(WARPS * 32, 2) walk_eval_kernel(const KParams 
   if (status && lane == 0) atomicOr(p.status, status);
 }
 
-template <int R, bool CAPTURE>
+template <int R, int STAGE, bool CAPTURE>
 cudaError_t launch_t(const KParams& p, int ctas_per_sm, cudaStream_t stream, LaunchInfo* info) {
-  const size_t smem = sizeof(WarpSmem) * WARPS;
-  auto kern = walk_eval_kernel<R, CAPTURE>;
+  const size_t smem = sizeof(WarpSmem) * WARPS + 128;
+  auto kern = walk_eval_kernel<R, STAGE, CAPTURE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;
@@ -549,16 +647,49 @@ cudaError_t launch_t(const KParams& p, int ctas_per_sm, cudaStream_t stream, Lau
 
 }  // namespace
 
-size_t walk_eval_smem_bytes() { return sizeof(WarpSmem) * WARPS; }
+cudaError_t encode_mp_map(CUtensorMap* map, const void* mp, int n_cells) {
+  using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static EncodeFn fn = nullptr;
+  if (!fn) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !f) return cudaErrorNotSupported;
+    fn = reinterpret_cast<EncodeFn>(f);
+  }
+  const cuuint64_t dims[2] = {16, static_cast<cuuint64_t>(n_cells > 0 ? n_cells : 1)};
+  const cuuint64_t strides[1] = {64};
+  const cuuint32_t box[2] = {16, 1};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(mp), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+size_t walk_eval_smem_bytes() { return sizeof(WarpSmem) * WARPS + 128; }
+
+template <int STAGE>
+cudaError_t launch_s(const KParams& p, int ppl, int ctas_per_sm, bool capture, cudaStream_t stream,
+                     LaunchInfo* info) {
+  if (ppl == 1) {
+    return capture ? launch_t<1, STAGE, true>(p, ctas_per_sm, stream, info)
+                   : launch_t<1, STAGE, false>(p, ctas_per_sm, stream, info);
+  }
+  return capture ? launch_t<2, STAGE, true>(p, ctas_per_sm, stream, info)
+                 : launch_t<2, STAGE, false>(p, ctas_per_sm, stream, info);
+}
 
 cudaError_t launch_walk_eval(const KParams& p, int ppl, int ctas_per_sm, bool capture,
                              cudaStream_t stream, LaunchInfo* info) {
-  if (ppl == 1) {
-    return capture ? launch_t<1, true>(p, ctas_per_sm, stream, info)
-                   : launch_t<1, false>(p, ctas_per_sm, stream, info);
+  switch (p.stage) {
+    case STAGE_BULK: return launch_s<STAGE_BULK>(p, ppl, ctas_per_sm, capture, stream, info);
+    case STAGE_ASYNC: return launch_s<STAGE_ASYNC>(p, ppl, ctas_per_sm, capture, stream, info);
+    default: return launch_s<STAGE_GATHER4>(p, ppl, ctas_per_sm, capture, stream, info);
   }
-  return capture ? launch_t<2, true>(p, ctas_per_sm, stream, info)
-                 : launch_t<2, false>(p, ctas_per_sm, stream, info);
 }
 
 // ---------------------------------------------------------------- allocation-free launch

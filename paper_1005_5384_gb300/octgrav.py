@@ -54,6 +54,7 @@ _SIGS = {
     "octgrav_interaction_counts": (C.c_int, [_vp, _i64, _vp]),
     "octgrav_debug_lists": (C.c_int, [_vp, C.c_double, C.c_int, _vp, _vp, _vp, _vp, _vp]),
     "octgrav_set_launch": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "octgrav_set_staging": (C.c_int, [_vp, C.c_int]),
     "octgrav_free_tree": (None, [_vp]),
     "octgrav_forces_noalloc": (C.c_int, [_vp, _vp, C.POINTER(C.c_size_t), C.c_double, C.c_double, C.c_double,
                                          _vp, _vp]),
@@ -194,6 +195,10 @@ class Tree:
     def set_launch(self, particles_per_lane: int = 2, ctas_per_sm: int = 0):
         _check(load().octgrav_set_launch(self._h, int(particles_per_lane), int(ctas_per_sm)))
         self.stats = self._stats()
+
+    def set_staging(self, mode: int):
+        """0 = cp.async.bulk per record, 1 = 16-byte cp.async (default), 2 = TMA gather4."""
+        _check(load().octgrav_set_staging(self._h, int(mode)))
 
     def set_system_params(self, eps=None, theta=None):
         if eps is None and theta is None:

@@ -166,3 +166,27 @@ def test_full_size_plummer_sampled_groups():
     samp = idx[:: max(1, len(idx) // 512)]
     ad, _ = O.direct(pos, m, 0.01, targets=samp)
     assert np.median(O.rel_err(acc[samp], ad)) < 1e-3
+
+
+@pytest.mark.parametrize("stage", [0, 1, 2])
+def test_staging_modes_agree_bitwise(_cuda, stage):
+    """The three ways of staging cell records (per-record bulk copy, per-lane
+    16-byte cp.async, TMA gather4) feed the same slots in the same order."""
+    torch = _cuda
+    pos, m = W.clustered(30000, 16, seed=8)
+    T = G.Tree.build(pos, m, 16, 64)
+    T.set_staging(stage)
+    acc, pot = T.forces(0.005, 0.6)
+    R = O.Tree(pos, m, 16, 64)
+    ra, rp, _, _, _ = R.forces(0.005, 0.6)
+    assert O.rel_rms(acc, ra) <= TOL_RMS
+    T.set_staging(2)
+    acc2, pot2 = T.forces(0.005, 0.6)
+    assert np.array_equal(acc, acc2) and np.array_equal(pot, pot2)
+    T.set_staging(stage)
+    gl = T.debug_lists(0.6, cap=R.n_cells)
+    info = T.item_info()
+    okey = {int(R.key[c]): g for g, c in enumerate(R.groups)}
+    for k in range(0, len(gl), 5):
+        rc, rl = R.list_keys(okey[int(info["group_key"][k])], 0.6)
+        assert np.array_equal(gl[k][0], rc) and np.array_equal(gl[k][1], rl)
