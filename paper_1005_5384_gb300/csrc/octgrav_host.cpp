@@ -593,12 +593,18 @@ void make_items(octgrav_tree* t) {
     b[1] = make_float4(static_cast<float>(t->bmax[3 * c]), static_cast<float>(t->bmax[3 * c + 1]),
                        static_cast<float>(t->bmax[3 * c + 2]), chi[1]);
     b[2] = make_float4(clo[0], clo[1], clo[2], chi[2]);
+    float4 grange;  // (first particle, count) of the whole group, as int bits
+    const int32_t gr[2] = {static_cast<int32_t>(pf), static_cast<int32_t>(cnt)};
+    std::memcpy(&grange.x, &gr[0], 4);
+    std::memcpy(&grange.y, &gr[1], 4);
+    grange.z = grange.w = 0.f;
     for (int64_t off = 0; off < cnt; off += item_max) {
       const int k = static_cast<int>(std::min<int64_t>(item_max, cnt - off));
       t->items.push_back(make_int4(static_cast<int>(root), static_cast<int>(pf + off), k, s));
       t->ibox.push_back(b[0]);
       t->ibox.push_back(b[1]);
       t->ibox.push_back(b[2]);
+      t->ibox.push_back(grange);
       t->item_key.push_back(t->key[c]);
     }
   }

@@ -23,8 +23,9 @@ enum : int {
 //   mp    [4*nc] float4: q0 = (com_hi.xyz, M), q1 = (com_lo.xyz, T = trS/2),
 //                        q2 = (3Sxx, 3Syy, 3Szz, 3Sxy), q3 = (3Sxz, 3Syz, 3T, 0)
 //   items [ni]   int4:   (root cell of the system, first particle, count, system)
-//   ibox  [3*ni] float4: (gmin.xyz, C_hi.x), (gmax.xyz, C_hi.y), (C_lo.xyz, C_hi.z)
-//                        group tight box (FP32-rounded) and group centre C (hi/lo)
+//   ibox  [4*ni] float4: (gmin.xyz, C_hi.x), (gmax.xyz, C_hi.y), (C_lo.xyz, C_hi.z),
+//                        (first particle, count of the whole group as int bits, 0, 0):
+//                        group tight box (FP32-rounded), group centre C (hi/lo), group range
 //   sysp  [nsys] float4: (fl32(theta^2), fl32(eps^2), -, -) (optional; G is sys0.z)
 // Staging of accepted cell records (KParams::stage).
 enum : int {

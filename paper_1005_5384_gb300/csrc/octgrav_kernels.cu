@@ -15,7 +15,7 @@
 //   opened node   -> pushed on the stack as (first child, number of children).
 // Full tiles of 32 cell records are evaluated one walk step after their copies
 // were issued, by all particles of the group (Listing 3); the leaf queue is
-// evaluated in chunks of 64 source particles (Listing 4). The paper's two
+// evaluated in double-buffered chunks of 32 source particles (Listing 4). The paper's two
 // walks (count, then write) and the host prefix sum between them (Sec. 2.2)
 // are gone: lists never leave the SM.
 //
@@ -52,15 +52,15 @@ struct RingStride {               // float4 per ring slot
   static constexpr int v = STAGE == STAGE_GATHER4 ? 4 : 5;  // 64 B rows / 64 B + 16 B pad
 };
 constexpr int STACK = 512;        // node-stack entries per warp
-constexpr int PCHUNK = 64;        // source particles per particle-particle chunk
+constexpr int PCH = 32;           // source particles per particle-particle chunk
 constexpr int LQ = 64;            // leaf-queue entries (flushed at >= 32)
 constexpr long long WAIT_LIMIT = 1ll << 31;  // cycles (~1 s) before a wait gives up
 
 struct __align__(128) WarpSmem {
   float4 ring[NTILE * TILE * 5];    // 7680 B; stride 80 B keeps 8 slots on 8 bank quads
   int cidx[NTILE * TILE];           // 384 B: cell index per ring slot (gather4 staging)
-  float4 src[PCHUNK];               // 1024 B: source (x', m)
-  int srcidx[PCHUNK];               // 256 B: source tree index (self exclusion)
+  float4 pbuf[2][2 * PCH];          // 2048 B: two chunks of source particles (hi, lo records),
+                                    // rewritten in place to (x', m), (index, -, -, -)
   int2 leafq[LQ];                   // 512 B: (first particle, count)
   int lpref[LQ];                    // 256 B: inclusive prefix of counts
   int stack[STACK];                 // 2048 B: packed (first child << 3 | n_child - 1)
@@ -178,46 +178,70 @@ struct Acc4 {
   float x, y, z, p;
 };
 
+// ---- packed FP32x2 arithmetic (Blackwell FFMA2 / FMUL2 / FADD2): every op
+// below evaluates two interactions at once, halving the issued instructions.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 rsqrt2(float2 a) { return make_float2(rsqrt_ftz(a.x), rsqrt_ftz(a.y)); }
+
+struct Acc2 {  // partial sums of the two halves of a pair
+  float2 x, y, z, p;
+};
+
+// Two cell records side by side (each field holds record a in .x, record b
+// in .y): centre of mass relative to the group centre and negated (nc), -M,
+// S3 = 3 S, T3 = 3T and T = tr(S)/2. 96 bytes = six 16-byte loads.
+struct CellPair {
+  float2 ncx, ncy, ncz, nM, sxx, syy, szz, sxy, sxz, syz, t3, t;
+};
+
 // Particle-cell interaction: second-order Taylor expansion of the Plummer
 // kernel about the cell's centre of mass (monopole + quadrupole). With
 // d = x_i - com, r^2 = |d|^2 + eps^2, S3 = 3S, q = d.S3.d, T = trS/2:
 //   a   += d (-M + (3T - 2.5 q/r^2)/r^2) / r^3 + S3 d / r^5
 //   phi -= (M + (q/(2 r^2) - T)/r^2) / r
-// q0 = (com, M), q2 = (S3xx, S3yy, S3zz, S3xy), q3 = (S3xz, S3yz, 3T, T).
-__device__ __forceinline__ void body_cell(float x, float y, float z, float eps2, float4 q0,
-                                          float4 q2, float4 q3, Acc4& a) {
-  const float dx = x - q0.x, dy = y - q0.y, dz = z - q0.z;
-  const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-  const float rinv = rsqrt_ftz(r2);
-  const float rinv2 = rinv * rinv;
-  const float rinv3 = rinv * rinv2;
-  const float rinv5 = rinv3 * rinv2;
-  const float sx = fmaf(q2.x, dx, fmaf(q2.w, dy, q3.x * dz));
-  const float sy = fmaf(q2.w, dx, fmaf(q2.y, dy, q3.y * dz));
-  const float sz = fmaf(q3.x, dx, fmaf(q3.y, dy, q2.z * dz));
-  const float q = fmaf(dx, sx, fmaf(dy, sy, dz * sz));
-  const float t1 = q * rinv2;
-  const float t2 = fmaf(-2.5f, t1, q3.z);
-  const float cd = fmaf(t2, rinv2, -q0.w) * rinv3;
-  a.x = fmaf(cd, dx, fmaf(rinv5, sx, a.x));
-  a.y = fmaf(cd, dy, fmaf(rinv5, sy, a.y));
-  a.z = fmaf(cd, dz, fmaf(rinv5, sz, a.z));
-  const float p2 = fmaf(fmaf(0.5f, t1, -q3.w), rinv2, q0.w);
-  a.p = fmaf(-p2, rinv, a.p);
+__device__ __forceinline__ void body_cell2(float2 X, float2 Y, float2 Z, float2 eps2, const CellPair& c,
+                                           Acc2& a) {
+  const float2 dx = add2(X, c.ncx), dy = add2(Y, c.ncy), dz = add2(Z, c.ncz);
+  const float2 r2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, eps2)));
+  const float2 rinv = rsqrt2(r2);
+  const float2 rinv2 = mul2(rinv, rinv);
+  const float2 rinv3 = mul2(rinv, rinv2);
+  const float2 rinv5 = mul2(rinv3, rinv2);
+  const float2 sx = fma2(c.sxx, dx, fma2(c.sxy, dy, mul2(c.sxz, dz)));
+  const float2 sy = fma2(c.sxy, dx, fma2(c.syy, dy, mul2(c.syz, dz)));
+  const float2 sz = fma2(c.sxz, dx, fma2(c.syz, dy, mul2(c.szz, dz)));
+  const float2 q = fma2(dx, sx, fma2(dy, sy, mul2(dz, sz)));
+  const float2 t1 = mul2(q, rinv2);
+  const float2 t2 = fma2(f2(-2.5f), t1, c.t3);
+  const float2 cd = mul2(fma2(t2, rinv2, c.nM), rinv3);
+  a.x = fma2(cd, dx, fma2(rinv5, sx, a.x));
+  a.y = fma2(cd, dy, fma2(rinv5, sy, a.y));
+  a.z = fma2(cd, dz, fma2(rinv5, sz, a.z));
+  const float2 np2 = fma2(fma2(f2(-0.5f), t1, c.t), rinv2, c.nM);  // -(M + (q/(2r^2) - T)/r^2)
+  a.p = fma2(np2, rinv, a.p);
 }
 
-// Particle-particle interaction with Plummer softening; mj = 0 drops the self term.
-__device__ __forceinline__ void body_body(float x, float y, float z, float eps2, float4 s,
-                                          float mj, Acc4& a) {
-  const float dx = s.x - x, dy = s.y - y, dz = s.z - z;
-  const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-  const float rinv = rsqrt_ftz(r2);
-  const float mr = mj * rinv;
-  const float mr3 = mr * rinv * rinv;
-  a.x = fmaf(mr3, dx, a.x);
-  a.y = fmaf(mr3, dy, a.y);
-  a.z = fmaf(mr3, dz, a.z);
-  a.p -= mr;
+// Two source particles side by side: negated positions (relative to the group
+// centre) and negated masses. 32 bytes = two 16-byte loads.
+struct SrcPair {
+  float2 nx, ny, nz, nm;
+};
+
+// Particle-particle interaction with Plummer softening; nm = -m_j (0 drops a term).
+__device__ __forceinline__ void body_body2(float2 X, float2 Y, float2 Z, float2 eps2, const SrcPair& s,
+                                           float2 nm, Acc2& a) {
+  const float2 dx = add2(X, s.nx), dy = add2(Y, s.ny), dz = add2(Z, s.nz);  // x_i - x_j
+  const float2 r2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, eps2)));
+  const float2 rinv = rsqrt2(r2);
+  const float2 nmr = mul2(nm, rinv);
+  const float2 nmr3 = mul2(nmr, mul2(rinv, rinv));
+  a.x = fma2(nmr3, dx, a.x);  // += m_j (x_j - x_i) / r^3
+  a.y = fma2(nmr3, dy, a.y);
+  a.z = fma2(nmr3, dz, a.z);
+  a.p = add2(a.p, nmr);       // -= m_j / r
 }
 
 // Error-free transformation: hi + t = s + e exactly.
@@ -231,23 +255,34 @@ __device__ __forceinline__ void two_sum_into(float& hi, float& lo, float t) {
 
 template <int R>
 struct Particles {
-  float x[R], y[R], z[R];
-  int idx[R];
-  Acc4 part[R];  // plain FP32 partial sums since the last fold
-  Acc4 hi[R];    // compensated accumulator: value = hi + lo
+  float2 X[R], Y[R], Z[R];  // group-relative position, broadcast to both halves
+  int idx[R];               // tree position, -1 for an empty slot
+  Acc2 part[R];             // plain FP32 partial sums since the last fold
+  Acc4 hi[R];               // compensated accumulator: value = hi + lo
   Acc4 lo[R];
 
   __device__ __forceinline__ void fold() {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      two_sum_into(hi[r].x, lo[r].x, part[r].x);
-      two_sum_into(hi[r].y, lo[r].y, part[r].y);
-      two_sum_into(hi[r].z, lo[r].z, part[r].z);
-      two_sum_into(hi[r].p, lo[r].p, part[r].p);
-      part[r] = Acc4{0.f, 0.f, 0.f, 0.f};
+      two_sum_into(hi[r].x, lo[r].x, part[r].x.x + part[r].x.y);
+      two_sum_into(hi[r].y, lo[r].y, part[r].y.x + part[r].y.y);
+      two_sum_into(hi[r].z, lo[r].z, part[r].z.x + part[r].z.y);
+      two_sum_into(hi[r].p, lo[r].p, part[r].p.x + part[r].p.y);
+      part[r].x = part[r].y = part[r].z = part[r].p = f2(0.f);
     }
   }
 };
+
+__device__ __forceinline__ CellPair load_cell_pair(const float4* q) {
+  const float4 a = q[0], b = q[1], c = q[2], d = q[3], e = q[4], f = q[5];
+  return CellPair{make_float2(a.x, a.y), make_float2(a.z, a.w), make_float2(b.x, b.y), make_float2(b.z, b.w),
+                  make_float2(c.x, c.y), make_float2(c.z, c.w), make_float2(d.x, d.y), make_float2(d.z, d.w),
+                  make_float2(e.x, e.y), make_float2(e.z, e.w), make_float2(f.x, f.y), make_float2(f.z, f.w)};
+}
+__device__ __forceinline__ SrcPair load_src_pair(const float4* q) {
+  const float4 a = q[0], b = q[1];
+  return SrcPair{make_float2(a.x, a.y), make_float2(a.z, a.w), make_float2(b.x, b.y), make_float2(b.z, b.w)};
+}
 
 // ---------------------------------------------------------------- the kernel
 
@@ -256,8 +291,9 @@ __global__ void __launch_bounds__(WARPS * 32, 2) walk_eval_kernel(const __grid_c
   constexpr int REC = RingStride<STAGE>::v;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
-  unsigned char* smem_base = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+  // align to 128 B by offsetting the shared array itself (keeps the
+  // shared address space visible to the compiler: LDS, not generic LD)
+  unsigned char* smem_base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   WarpSmem& S = reinterpret_cast<WarpSmem*>(smem_base)[threadIdx.x >> 5];
   const uint32_t bar0 = smem_u32(&S.bar[0]);
   if (lane == 0) {
@@ -281,11 +317,14 @@ __global__ void __launch_bounds__(WARPS * 32, 2) walk_eval_kernel(const __grid_c
     if (item >= p.n_items) break;
 
     const int4 it = __ldg(p.items + item);
-    const float4 b0 = __ldg(p.ibox + 3 * item);
-    const float4 b1 = __ldg(p.ibox + 3 * item + 1);
-    const float4 b2 = __ldg(p.ibox + 3 * item + 2);
+    const float4 b0 = __ldg(p.ibox + 4 * item);
+    const float4 b1 = __ldg(p.ibox + 4 * item + 1);
+    const float4 b2 = __ldg(p.ibox + 4 * item + 2);
+    const float4 b3 = __ldg(p.ibox + 4 * item + 3);
+    const int gfirst = __float_as_int(b3.x), gcount = __float_as_int(b3.y);  // the whole group
     const float4 sp = p.sysp ? __ldg(p.sysp + it.w) : p.sys0;
-    const float theta2 = sp.x, eps2 = sp.y, G = p.sys0.z;
+    const float theta2 = sp.x, G = p.sys0.z;
+    const float2 E2 = f2(sp.y);
     const float3 gmin = make_float3(b0.x, b0.y, b0.z);
     const float3 gmax = make_float3(b1.x, b1.y, b1.z);
     const float3 chi = make_float3(b0.w, b1.w, b2.w);
@@ -305,15 +344,19 @@ __global__ void __launch_bounds__(WARPS * 32, 2) walk_eval_kernel(const __grid_c
       const int k = wl + r * w;
       const bool v = act && k < np;
       P.idx[r] = v ? pf + k : -1;
-      P.x[r] = P.y[r] = P.z[r] = 0.f;
+      float x = 0.f, y = 0.f, z = 0.f;
       if (v) {
         const float4 h4 = __ldg(p.parts + 2 * (pf + k));
         const float4 l4 = __ldg(p.parts + 2 * (pf + k) + 1);
-        P.x[r] = (h4.x - chi.x) + (l4.x - clo.x);
-        P.y[r] = (h4.y - chi.y) + (l4.y - clo.y);
-        P.z[r] = (h4.z - chi.z) + (l4.z - clo.z);
+        x = (h4.x - chi.x) + (l4.x - clo.x);
+        y = (h4.y - chi.y) + (l4.y - clo.y);
+        z = (h4.z - chi.z) + (l4.z - clo.z);
       }
-      P.part[r] = P.hi[r] = P.lo[r] = Acc4{0.f, 0.f, 0.f, 0.f};
+      P.X[r] = f2(x);
+      P.Y[r] = f2(y);
+      P.Z[r] = f2(z);
+      P.part[r].x = P.part[r].y = P.part[r].z = P.part[r].p = f2(0.f);
+      P.hi[r] = P.lo[r] = Acc4{0.f, 0.f, 0.f, 0.f};
     }
     int nsince = 0;  // tiles since the last fold
 
@@ -327,33 +370,35 @@ __global__ void __launch_bounds__(WARPS * 32, 2) walk_eval_kernel(const __grid_c
         return false;
       }
       float4* base = &S.ring[tile * TILE * REC];
-      if (lane < n) {  // centre of mass relative to the group centre
-        float4 q0 = base[lane * REC];
-        const float4 q1 = base[lane * REC + 1];
-        q0.x = (q0.x - chi.x) + (q1.x - clo.x);
-        q0.y = (q0.y - chi.y) + (q1.y - clo.y);
-        q0.z = (q0.z - chi.z) + (q1.z - clo.z);
-        base[lane * REC] = q0;
+      // Rewrite the tile in place into the pair layout: record e becomes half
+      // (e & 1) of pair e >> 1; an odd last record is paired with zeros.
+      float v[12];
+#pragma unroll
+      for (int f = 0; f < 12; ++f) v[f] = 0.f;
+      if (lane < n) {
+        const float4 q0 = base[lane * REC], q1 = base[lane * REC + 1];
+        const float4 q2 = base[lane * REC + 2], q3 = base[lane * REC + 3];
+        v[0] = -((q0.x - chi.x) + (q1.x - clo.x));
+        v[1] = -((q0.y - chi.y) + (q1.y - clo.y));
+        v[2] = -((q0.z - chi.z) + (q1.z - clo.z));
+        v[3] = -q0.w;
+        v[4] = q2.x; v[5] = q2.y; v[6] = q2.z; v[7] = q2.w;
+        v[8] = q3.x; v[9] = q3.y; v[10] = q3.z; v[11] = q3.w;
+      }
+      __syncwarp();
+      const int npad = (n + 1) & ~1;
+      if (lane < npad) {
+        float* dst = reinterpret_cast<float*>(base) + 24 * (lane >> 1) + (lane & 1);
+#pragma unroll
+        for (int f = 0; f < 12; ++f) dst[2 * f] = v[f];
       }
       __syncwarp();
       if (act) {
-        int e = sl;
-        for (; e + s < n; e += 2 * s) {  // two records per iteration: 2R independent chains
-          const float4* ra = base + e * REC;
-          const float4* rb = base + (e + s) * REC;
-          const float4 a0 = ra[0], a2 = ra[2], a3 = ra[3];
-          const float4 c0 = rb[0], c2 = rb[2], c3 = rb[3];
+        const float4* pb = base;
+        for (int k = sl; k < npad / 2; k += s) {
+          const CellPair c = load_cell_pair(pb + 6 * k);
 #pragma unroll
-          for (int r = 0; r < R; ++r) {
-            body_cell(P.x[r], P.y[r], P.z[r], eps2, a0, a2, a3, P.part[r]);
-            body_cell(P.x[r], P.y[r], P.z[r], eps2, c0, c2, c3, P.part[r]);
-          }
-        }
-        if (e < n) {
-          const float4* ra = base + e * REC;
-          const float4 a0 = ra[0], a2 = ra[2], a3 = ra[3];
-#pragma unroll
-          for (int r = 0; r < R; ++r) body_cell(P.x[r], P.y[r], P.z[r], eps2, a0, a2, a3, P.part[r]);
+          for (int r = 0; r < R; ++r) body_cell2(P.X[r], P.Y[r], P.Z[r], E2, c, P.part[r]);
         }
       }
       if (++nsince >= s) {
@@ -366,8 +411,96 @@ __global__ void __launch_bounds__(WARPS * 32, 2) walk_eval_kernel(const __grid_c
       return true;
     };
 
-    // ---- evaluation of the queued leaves (Listing 4)
+    // ---- particle-particle evaluation in chunks of PCH sources (Listing 4).
+    // Chunk k+1 is copied asynchronously while chunk k is evaluated. The
+    // sources are either the particles of the queued leaves (rank -> particle
+    // through the prefix of leaf counts) or, with `own`, the item's whole
+    // group, whose pass excludes the self term.
     int n_pp = 0;
+    auto pp_pass = [&](int total, int nq, bool own) {
+      const int nchunk = (total + PCH - 1) / PCH;
+      auto stage = [&](int k) -> int {
+        const int rk = k * PCH + lane;
+        int j = -1;
+        if (rk < total) {
+          if (own) {
+            j = gfirst + rk;
+          } else {
+            int lo = 0, hi = nq - 1;  // first entry whose inclusive prefix exceeds rk
+            while (lo < hi) {
+              const int mid = (lo + hi) >> 1;
+              if (S.lpref[mid] > rk) hi = mid; else lo = mid + 1;
+            }
+            const int start = lo ? S.lpref[lo - 1] : 0;
+            j = S.leafq[lo].x + (rk - start);
+          }
+          const uint32_t dst = smem_u32(&S.pbuf[k & 1][2 * lane]);
+          cp_async16(dst, p.parts + 2 * j);
+          cp_async16(dst + 16, p.parts + 2 * j + 1);
+        }
+        cp_async_commit();
+        return j;
+      };
+      int j_cur = nchunk > 0 ? stage(0) : -1;
+      for (int k = 0; k < nchunk; ++k) {
+        int j_next = -1;
+        if (k + 1 < nchunk) {
+          j_next = stage(k + 1);
+          cp_async_wait_1();
+        } else {
+          cp_async_wait_all();
+        }
+        float4* buf = S.pbuf[k & 1];
+        const int nloc = min(PCH, total - k * PCH);
+        const int npad = (nloc + 1) & ~1;
+        // this lane's own copy -> negated relative position and mass, pair layout
+        float nx = 0.f, ny = 0.f, nz = 0.f, nm = 0.f;
+        if (j_cur >= 0) {
+          const float4 h4 = buf[2 * lane];
+          const float4 l4 = buf[2 * lane + 1];
+          nx = -((h4.x - chi.x) + (l4.x - clo.x));
+          ny = -((h4.y - chi.y) + (l4.y - clo.y));
+          nz = -((h4.z - chi.z) + (l4.z - clo.z));
+          nm = -h4.w;
+        }
+        __syncwarp();
+        if (lane < npad) {
+          float* dst = reinterpret_cast<float*>(buf) + 8 * (lane >> 1) + (lane & 1);
+          dst[0] = nx;
+          dst[2] = ny;
+          dst[4] = nz;
+          dst[6] = nm;
+          if (own) reinterpret_cast<int*>(buf)[128 + lane] = j_cur;  // source index per half
+        }
+        __syncwarp();
+        if (act) {
+          if (own) {
+            const int* jj = reinterpret_cast<const int*>(buf) + 128;
+            for (int e = sl; e < npad / 2; e += s) {
+              const SrcPair q = load_src_pair(buf + 2 * e);
+              const int ja = jj[2 * e], jb = jj[2 * e + 1];
+#pragma unroll
+              for (int r = 0; r < R; ++r) {
+                const float2 nm2 = make_float2(ja == P.idx[r] ? 0.f : q.nm.x, jb == P.idx[r] ? 0.f : q.nm.y);
+                body_body2(P.X[r], P.Y[r], P.Z[r], E2, q, nm2, P.part[r]);
+              }
+            }
+          } else {
+            for (int e = sl; e < npad / 2; e += s) {
+              const SrcPair q = load_src_pair(buf + 2 * e);
+#pragma unroll
+              for (int r = 0; r < R; ++r) body_body2(P.X[r], P.Y[r], P.Z[r], E2, q, q.nm, P.part[r]);
+            }
+          }
+        }
+        if (++nsince >= s) {
+          P.fold();
+          nsince = 0;
+        }
+        __syncwarp();  // chunk k's buffer is free for chunk k+2
+        j_cur = j_next;
+      }
+    };
     auto eval_leaves = [&](int nq) {
       const int c0 = lane < nq ? S.leafq[lane].y : 0;
       const int c1 = lane + 32 < nq ? S.leafq[lane + 32].y : 0;
@@ -387,54 +520,22 @@ __global__ void __launch_bounds__(WARPS * 32, 2) walk_eval_kernel(const __grid_c
       S.lpref[lane + 32] = s1 + tot0;
       __syncwarp();
       n_pp += total;
-      for (int base = 0; base < total; base += PCHUNK) {
-        const int nloc = min(PCHUNK, total - base);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int rk = base + lane + 32 * h;
-          if (rk < total) {
-            int lo = 0, hi = nq - 1;  // first entry whose inclusive prefix exceeds rk
-            while (lo < hi) {
-              const int mid = (lo + hi) >> 1;
-              if (S.lpref[mid] > rk) hi = mid; else lo = mid + 1;
-            }
-            const int start = lo ? S.lpref[lo - 1] : 0;
-            const int j = S.leafq[lo].x + (rk - start);
-            const float4 h4 = __ldg(p.parts + 2 * j);
-            const float4 l4 = __ldg(p.parts + 2 * j + 1);
-            S.src[lane + 32 * h] = make_float4((h4.x - chi.x) + (l4.x - clo.x),
-                                               (h4.y - chi.y) + (l4.y - clo.y),
-                                               (h4.z - chi.z) + (l4.z - clo.z), h4.w);
-            S.srcidx[lane + 32 * h] = j;
-          }
-        }
-        __syncwarp();
-        if (act) {
-          for (int e = sl; e < nloc; e += s) {
-            const float4 q = S.src[e];
-            const int j = S.srcidx[e];
-#pragma unroll
-            for (int r = 0; r < R; ++r)
-              body_body(P.x[r], P.y[r], P.z[r], eps2, q, j != P.idx[r] ? q.w : 0.f, P.part[r]);
-          }
-        }
-        if (++nsince >= s) {
-          P.fold();
-          nsince = 0;
-        }
-        __syncwarp();
-      }
+      pp_pass(total, nq, false);
     };
+
+    // The group's own particles: they sit in the group's own leaves, which are
+    // always opened (distance 0) and are evaluated here, with the self term
+    // left out, instead of through the leaf queue.
+    n_pp += gcount;
+    pp_pass(gcount, 0, true);
 
     // ---- walk (Listing 1): root opened; children of up to 4 nodes per step
     int top = 0, nlq = 0, n_pc = 0, n_leafent = 0;
     bool ok = true;
     {
       const int2 rl = __ldg(p.link + it.x);
-      if (rl.y < 0) {
-        if (lane == 0) S.leafq[0] = make_int2(rl.x, -rl.y);
+      if (rl.y < 0) {  // the root is a leaf: it is the group itself (own pass above)
         if (CAPTURE && lane == 0 && p.dbg_cap > 0) p.dbg_leaf[(size_t)item * p.dbg_cap] = it.x;
-        nlq = 1;
         n_leafent = 1;
       } else {
         if (lane == 0) S.stack[0] = (rl.x << 3) | (rl.y - 1);
@@ -442,34 +543,52 @@ __global__ void __launch_bounds__(WARPS * 32, 2) walk_eval_kernel(const __grid_c
       }
       __syncwarp();
     }
+    // The children tested in the next step are known as soon as a step has
+    // pushed its nodes (the stack is LIFO and nothing else touches it), so
+    // their cube and link records are loaded one step ahead: the loads are in
+    // flight while this warp evaluates tiles and leaves.
+    bool nx_valid = false;
+    int nx_c = 0;
+    float4 nx_g = make_float4(0.f, 0.f, 0.f, 0.f);
+    int2 nx_lk = make_int2(0, 0);
+    auto prefetch = [&]() {
+      const int npop = min(4, top);
+      const int k = lane >> 3, slot = lane & 7;
+      const int packed = k < npop ? S.stack[top - npop + k] : 0;
+      const int nch = (packed & 7) + 1;
+      nx_valid = (k < npop) && (slot < nch);
+      nx_c = (packed >> 3) + slot;
+      if (nx_valid && static_cast<unsigned>(nx_c) >= static_cast<unsigned>(p.n_cells)) {
+        status |= ST_INDEX;
+        nx_valid = false;
+      }
+      nx_g = make_float4(0.f, 0.f, 0.f, 0.f);
+      nx_lk = make_int2(0, 0);
+      if (nx_valid) {
+        nx_g = __ldg(p.geo + nx_c);
+        nx_lk = __ldg(p.link + nx_c);
+      }
+      __syncwarp();  // stack reads precede the next step's pushes
+    };
+    if (top > 0) prefetch();
     while (top > 0) {
       if (app - done >= 2 * TILE) {
         // the oldest tile is complete and its copies were issued at least one step ago
         if (STAGE == STAGE_ASYNC) cp_async_wait_1();
         if (!eval_tile(TILE)) { ok = false; break; }
       }
-      const int npop = min(4, top);
-      const int k = lane >> 3, slot = lane & 7;
-      const int packed = k < npop ? S.stack[top - npop + k] : 0;
-      top -= npop;
-      __syncwarp();
-      const int nch = (packed & 7) + 1;
-      bool valid = (k < npop) && (slot < nch);
-      const int c = (packed >> 3) + slot;
-      if (valid && static_cast<unsigned>(c) >= static_cast<unsigned>(p.n_cells)) {
-        status |= ST_INDEX;
-        valid = false;
-      }
-      float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
-      int2 lk = make_int2(0, 0);
-      if (valid) {
-        g = __ldg(p.geo + c);
-        lk = __ldg(p.link + c);
-      }
+      top -= min(4, top);
+      const bool valid = nx_valid;
+      const int c = nx_c;
+      const float4 g = nx_g;
+      const int2 lk = nx_lk;
       const bool open = valid && must_open(g, gmin, gmax, theta2);
       const bool leaf = lk.y < 0;
+      // leaves of the own group are evaluated by the own pass, not queued
+      const bool own_leaf = open && leaf && lk.x >= gfirst && lk.x < gfirst + gcount;
       const unsigned m_acc = __ballot_sync(FULL, valid && !open);
       const unsigned m_leaf = __ballot_sync(FULL, open && leaf);
+      const unsigned m_lq = __ballot_sync(FULL, open && leaf && !own_leaf);
       const unsigned m_node = __ballot_sync(FULL, open && !leaf);
       const int nn = __popc(m_node);
       if (top + nn > STACK) {
@@ -478,13 +597,10 @@ __global__ void __launch_bounds__(WARPS * 32, 2) walk_eval_kernel(const __grid_c
       }
       if (open && !leaf) S.stack[top + __popc(m_node & lt)] = (lk.x << 3) | (lk.y - 1);
       top += nn;
-      if (open && leaf) {
-        const int q = nlq + __popc(m_leaf & lt);
-        S.leafq[q] = make_int2(lk.x, -lk.y);
-        if (CAPTURE && n_leafent + __popc(m_leaf & lt) < p.dbg_cap)
-          p.dbg_leaf[(size_t)item * p.dbg_cap + n_leafent + __popc(m_leaf & lt)] = c;
-      }
-      nlq += __popc(m_leaf);
+      if (open && leaf && !own_leaf) S.leafq[nlq + __popc(m_lq & lt)] = make_int2(lk.x, -lk.y);
+      if (CAPTURE && open && leaf && n_leafent + __popc(m_leaf & lt) < p.dbg_cap)
+        p.dbg_leaf[(size_t)item * p.dbg_cap + n_leafent + __popc(m_leaf & lt)] = c;
+      nlq += __popc(m_lq);
       n_leafent += __popc(m_leaf);
       if (valid && !open) {
         const uint32_t e = app + __popc(m_acc & lt);
@@ -529,6 +645,7 @@ __global__ void __launch_bounds__(WARPS * 32, 2) walk_eval_kernel(const __grid_c
         iss = upto;
       }
       __syncwarp();
+      if (top > 0) prefetch();
       if (nlq >= TILE) {
         eval_leaves(nlq);
         nlq = 0;
