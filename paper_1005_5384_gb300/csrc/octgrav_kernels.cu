@@ -52,6 +52,9 @@ struct RingStride {               // float4 per ring slot
   static constexpr int v = STAGE == STAGE_GATHER4 ? 4 : 5;  // 64 B rows / 64 B + 16 B pad
 };
 constexpr int STACK = 512;        // node-stack entries per warp
+constexpr int CPAIR = 7;          // float4 per cell pair in the evaluated tile (6 = 96 B, 7 = 112 B)
+constexpr int SPAIR = 3;          // float4 per source pair in a particle chunk (2 = 32 B, 3 = 48 B)
+constexpr int FOLD_EVERY = 4;     // fold partial sums every FOLD_EVERY * (slices) tiles/chunks
 constexpr int PCH = 32;           // source particles per particle-particle chunk
 constexpr int LQ = 64;            // leaf-queue entries (flushed at >= 32)
 constexpr long long WAIT_LIMIT = 1ll << 31;  // cycles (~1 s) before a wait gives up
@@ -66,6 +69,9 @@ struct __align__(128) WarpSmem {
   int stack[STACK];                 // 2048 B: packed (first child << 3 | n_child - 1)
   unsigned long long bar[NTILE];    // one mbarrier per ring tile
 };
+
+static_assert(16 * CPAIR * (TILE / 2) <= 64 * TILE, "cell pairs must fit the tile's ring slots");
+static_assert(16 * SPAIR * (PCH / 2) + 4 * PCH <= 32 * PCH, "source pairs and indices must fit a chunk");
 
 // ---------------------------------------------------------------- PTX helpers
 
@@ -388,7 +394,7 @@ __global__ void __launch_bounds__(WARPS * 32, 2) walk_eval_kernel(const __grid_c
       __syncwarp();
       const int npad = (n + 1) & ~1;
       if (lane < npad) {
-        float* dst = reinterpret_cast<float*>(base) + 24 * (lane >> 1) + (lane & 1);
+        float* dst = reinterpret_cast<float*>(base) + 4 * CPAIR * (lane >> 1) + (lane & 1);
 #pragma unroll
         for (int f = 0; f < 12; ++f) dst[2 * f] = v[f];
       }
@@ -396,12 +402,12 @@ __global__ void __launch_bounds__(WARPS * 32, 2) walk_eval_kernel(const __grid_c
       if (act) {
         const float4* pb = base;
         for (int k = sl; k < npad / 2; k += s) {
-          const CellPair c = load_cell_pair(pb + 6 * k);
+          const CellPair c = load_cell_pair(pb + CPAIR * k);
 #pragma unroll
           for (int r = 0; r < R; ++r) body_cell2(P.X[r], P.Y[r], P.Z[r], E2, c, P.part[r]);
         }
       }
-      if (++nsince >= s) {
+      if (++nsince >= FOLD_EVERY * s) {
         P.fold();
         nsince = 0;
       }
@@ -465,19 +471,19 @@ __global__ void __launch_bounds__(WARPS * 32, 2) walk_eval_kernel(const __grid_c
         }
         __syncwarp();
         if (lane < npad) {
-          float* dst = reinterpret_cast<float*>(buf) + 8 * (lane >> 1) + (lane & 1);
+          float* dst = reinterpret_cast<float*>(buf) + 4 * SPAIR * (lane >> 1) + (lane & 1);
           dst[0] = nx;
           dst[2] = ny;
           dst[4] = nz;
           dst[6] = nm;
-          if (own) reinterpret_cast<int*>(buf)[128 + lane] = j_cur;  // source index per half
+          if (own) reinterpret_cast<int*>(buf)[4 * SPAIR * 16 + lane] = j_cur;  // source index per half
         }
         __syncwarp();
         if (act) {
           if (own) {
-            const int* jj = reinterpret_cast<const int*>(buf) + 128;
+            const int* jj = reinterpret_cast<const int*>(buf) + 4 * SPAIR * 16;
             for (int e = sl; e < npad / 2; e += s) {
-              const SrcPair q = load_src_pair(buf + 2 * e);
+              const SrcPair q = load_src_pair(buf + SPAIR * e);
               const int ja = jj[2 * e], jb = jj[2 * e + 1];
 #pragma unroll
               for (int r = 0; r < R; ++r) {
@@ -487,13 +493,13 @@ __global__ void __launch_bounds__(WARPS * 32, 2) walk_eval_kernel(const __grid_c
             }
           } else {
             for (int e = sl; e < npad / 2; e += s) {
-              const SrcPair q = load_src_pair(buf + 2 * e);
+              const SrcPair q = load_src_pair(buf + SPAIR * e);
 #pragma unroll
               for (int r = 0; r < R; ++r) body_body2(P.X[r], P.Y[r], P.Z[r], E2, q, q.nm, P.part[r]);
             }
           }
         }
-        if (++nsince >= s) {
+        if (++nsince >= FOLD_EVERY * s) {
           P.fold();
           nsince = 0;
         }
