@@ -161,6 +161,31 @@ int octgrav_debug_lists(octgrav_tree *t, double theta, int cap, uint64_t *cell_k
  * later launches on this tree; n_items may change. Errors: ERR_ARG. */
 int octgrav_set_launch(octgrav_tree *t, int particles_per_lane, int ctas_per_sm);
 
+/* Capture one octgrav_forces_device call (status reset + the persistent
+ * walk/evaluation kernel) into a CUDA graph owned by the tree, for replay
+ * with octgrav_graph_launch. Uploads the tree first if needed. stream must
+ * be a non-default stream; acc4_dev is baked into the graph. The arguments
+ * follow octgrav_forces_device. Errors: ERR_ARG, ERR_CUDA. */
+int octgrav_graph_capture(octgrav_tree *t, double eps, double theta, double G, float *acc4_dev,
+                          void *stream);
+
+/* Replay the captured graph on stream (asynchronous). Status and interaction
+ * counts are read as after octgrav_forces_device. Errors: ERR_STATE if
+ * nothing was captured, ERR_CUDA. */
+int octgrav_graph_launch(octgrav_tree *t, void *stream);
+
+/* Autotuner: for the given systems (layout as octgrav_build_batch) times the
+ * fused kernel for every group size in n_group_cand[0..n_cand) (values below
+ * n_leaf are skipped) and particles-per-lane 1 and 2, and returns the fastest
+ * in best[0] = n_group, best[1] = particles per lane, best[2] = 0 (CTAs/SM:
+ * occupancy maximum), with its median time in *best_ms (may be NULL).
+ * Results are cached in-process per (n_sys, log2 N, theta, eps, n_leaf,
+ * candidates). Builds temporary trees and device buffers. Synchronous.
+ * Errors: as octgrav_build_batch and octgrav_forces_device. */
+int octgrav_autotune(int n_sys, const int64_t *offsets, const double *pos, const double *mass,
+                     int n_leaf, double eps, double theta, const int *n_group_cand, int n_cand,
+                     int *best, double *best_ms, void *stream);
+
 /* How the fused kernel stages accepted cell records into shared memory:
  *   0 = one cp.async.bulk (64 B) per record, issued by the accepting lane;
  *   1 = four 16-byte cp.async per record, issued by the accepting lane (default);

@@ -560,6 +560,7 @@ struct octgrav_tree {
   Device* dev = &own;
   bool uploaded = false;
   bool launched = false;
+  cudaGraphExec_t gexec = nullptr;  // captured memset + kernel (octgrav_graph_capture)
   std::vector<SysTree> sys_scratch;
 };
 
@@ -1142,6 +1143,120 @@ int octgrav_forces_noalloc(octgrav_tree* t, void* arena, size_t* arena_bytes, do
   return OCTGRAV_OK;
 }
 
+int octgrav_graph_capture(octgrav_tree* t, double eps, double theta, double G, float* acc4_dev, void* stream) {
+  if (!t || !acc4_dev) return fail(OCTGRAV_ERR_ARG, "NULL tree or output");
+  if (!stream) return fail(OCTGRAV_ERR_ARG, "graph capture needs a non-default stream");
+  int rc = check_params(eps, theta, G);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!t->uploaded || t->sysp_dirty) {
+    if ((rc = upload(t, st))) return rc;
+  }
+  CUDA_TRY(cudaStreamSynchronize(st));  // uploads from pageable memory cannot be captured
+  og::LaunchInfo li;
+  cudaError_t e = og::prepare_walk_eval(t->ppl, t->stage, t->ctas_per_sm, &li);
+  if (e != cudaSuccess) return fail(OCTGRAV_ERR_CUDA, "kernel preparation failed: %s", cudaGetErrorString(e));
+  CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  rc = launch(t, eps, theta, G, reinterpret_cast<float4*>(acc4_dev), st, false, nullptr, nullptr, nullptr, 0);
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(st, &graph);
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(OCTGRAV_ERR_CUDA, "cudaStreamEndCapture failed: %s", cudaGetErrorString(e));
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(OCTGRAV_ERR_CUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(e));
+  if (t->gexec) cudaGraphExecDestroy(t->gexec);
+  t->gexec = exec;
+  return OCTGRAV_OK;
+}
+
+int octgrav_graph_launch(octgrav_tree* t, void* stream) {
+  if (!t) return fail(OCTGRAV_ERR_ARG, "tree is NULL");
+  if (!t->gexec) return fail(OCTGRAV_ERR_STATE, "no captured graph on this tree");
+  CUDA_TRY(cudaGraphLaunch(t->gexec, static_cast<cudaStream_t>(stream)));
+  t->launched = true;
+  return OCTGRAV_OK;
+}
+
+int octgrav_autotune(int n_sys, const int64_t* offsets, const double* pos, const double* mass, int n_leaf,
+                     double eps, double theta, const int* n_group_cand, int n_cand, int* best, double* best_ms,
+                     void* stream) {
+  if (!offsets || !pos || !mass || !n_group_cand || n_cand < 1 || !best || n_sys < 1)
+    return fail(OCTGRAV_ERR_ARG, "bad argument");
+  int rc = check_params(eps, theta, 1.0);
+  if (rc) return rc;
+  // results are cached per (systems, log2 N, theta, eps, n_leaf, candidate set)
+  static std::mutex mu;
+  static std::vector<std::pair<std::vector<double>, std::vector<double>>> cache;
+  std::vector<double> key = {static_cast<double>(n_sys), std::floor(std::log2(static_cast<double>(offsets[n_sys]))),
+                             theta, eps, static_cast<double>(n_leaf)};
+  for (int c = 0; c < n_cand; ++c) key.push_back(n_group_cand[c]);
+  {
+    std::lock_guard<std::mutex> g(mu);
+    for (auto& kv : cache)
+      if (kv.first == key) {
+        best[0] = static_cast<int>(kv.second[0]);
+        best[1] = static_cast<int>(kv.second[1]);
+        best[2] = 0;
+        if (best_ms) *best_ms = kv.second[2];
+        return OCTGRAV_OK;
+      }
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  DevBuf outb;
+  if ((rc = outb.reserve(sizeof(float4) * offsets[n_sys]))) return rc;
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  double bms = 1e300;
+  int bng = -1, bppl = 2;
+  for (int c = 0; c < n_cand && rc == OCTGRAV_OK; ++c) {
+    if (n_group_cand[c] < n_leaf) continue;
+    octgrav_tree* t = nullptr;
+    if ((rc = build_common(n_sys, offsets, pos, mass, n_leaf, n_group_cand[c], &t))) break;
+    for (int ppl = 1; ppl <= 2 && rc == OCTGRAV_OK; ++ppl) {
+      if ((rc = octgrav_set_launch(t, ppl, 0))) break;
+      float4* out = static_cast<float4*>(outb.p);
+      if ((rc = launch(t, eps, theta, 1.0, out, st, false, nullptr, nullptr, nullptr, 0))) break;
+      std::vector<float> ms;
+      for (int k = 0; k < 3 && rc == OCTGRAV_OK; ++k) {
+        cudaEventRecord(e0, st);
+        rc = launch(t, eps, theta, 1.0, out, st, false, nullptr, nullptr, nullptr, 0);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(OCTGRAV_ERR_CUDA, "event sync failed");
+        float v = 0;
+        cudaEventElapsedTime(&v, e0, e1);
+        ms.push_back(v);
+      }
+      if (rc) break;
+      if ((rc = read_status(t, st))) break;
+      std::sort(ms.begin(), ms.end());
+      if (ms[1] < bms) {
+        bms = ms[1];
+        bng = n_group_cand[c];
+        bppl = ppl;
+      }
+    }
+    octgrav_free_tree(t);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  outb.release();
+  if (rc) return rc;
+  if (bng < 0) return fail(OCTGRAV_ERR_ARG, "no candidate n_group >= n_leaf");
+  best[0] = bng;
+  best[1] = bppl;
+  best[2] = 0;
+  if (best_ms) *best_ms = bms;
+  std::lock_guard<std::mutex> g(mu);
+  cache.push_back({key, {static_cast<double>(bng), static_cast<double>(bppl), bms}});
+  return OCTGRAV_OK;
+}
+
 int octgrav_set_staging(octgrav_tree* t, int mode) {
   if (!t) return fail(OCTGRAV_ERR_ARG, "tree is NULL");
   if (mode < og::STAGING_BULK || mode > og::STAGING_GATHER4) return fail(OCTGRAV_ERR_ARG, "staging mode must be 0, 1 or 2");
@@ -1151,6 +1266,7 @@ int octgrav_set_staging(octgrav_tree* t, int mode) {
 
 void octgrav_free_tree(octgrav_tree* t) {
   if (!t) return;
+  if (t->gexec) cudaGraphExecDestroy(t->gexec);
   t->own.release();
   delete t;
 }

@@ -69,6 +69,10 @@ struct LaunchInfo {
 cudaError_t launch_walk_eval(const KParams& p, int ppl, int ctas_per_sm, bool capture,
                              cudaStream_t stream, LaunchInfo* info);
 
+// Compute (and cache) the launch configuration of a kernel variant without
+// launching it; call before stream capture.
+cudaError_t prepare_walk_eval(int ppl, int stage, int ctas_per_sm, LaunchInfo* info);
+
 // Shared memory per CTA of the fused kernel.
 size_t walk_eval_smem_bytes();
 

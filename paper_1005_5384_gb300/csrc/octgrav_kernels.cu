@@ -744,19 +744,39 @@ __global__ void __launch_bounds__(WARPS * 32, 2) walk_eval_kernel(const __grid_c
   if (status && lane == 0) atomicOr(p.status, status);
 }
 
+// Launch configuration per kernel instance and device, computed once (so a
+// launch inside stream capture makes no attribute or occupancy calls).
+struct LaunchCache {
+  std::mutex mu;
+  int grid_per_sm[64] = {};
+  int sms[64] = {};
+};
+
 template <int R, int STAGE, bool CAPTURE>
-cudaError_t launch_t(const KParams& p, int ctas_per_sm, cudaStream_t stream, LaunchInfo* info) {
+cudaError_t launch_t(const KParams& p, int ctas_per_sm, cudaStream_t stream, LaunchInfo* info, bool dry) {
   const size_t smem = sizeof(WarpSmem) * WARPS + 128;
   auto kern = walk_eval_kernel<R, STAGE, CAPTURE>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(smem));
+  static LaunchCache cache;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0, occ = 0;
-  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, WARPS * 32, smem)) != cudaSuccess)
-    return e;
-  if (occ < 1) return cudaErrorInvalidConfiguration;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  int occ = 0, sms = 0;
+  {
+    std::lock_guard<std::mutex> lock(cache.mu);
+    if (!cache.grid_per_sm[dev]) {
+      if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem))) !=
+          cudaSuccess)
+        return e;
+      if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, WARPS * 32, smem)) != cudaSuccess) return e;
+      if (occ < 1) return cudaErrorInvalidConfiguration;
+      cache.grid_per_sm[dev] = occ;
+      cache.sms[dev] = sms;
+    }
+    occ = cache.grid_per_sm[dev];
+    sms = cache.sms[dev];
+  }
   const int per_sm = ctas_per_sm > 0 ? min(ctas_per_sm, occ) : occ;
   const int grid = sms * per_sm;
   if (info) {
@@ -764,6 +784,7 @@ cudaError_t launch_t(const KParams& p, int ctas_per_sm, cudaStream_t stream, Lau
     info->block = WARPS * 32;
     info->smem = smem;
   }
+  if (dry) return cudaSuccess;
   kern<<<grid, WARPS * 32, smem, stream>>>(p);
   return cudaGetLastError();
 }
@@ -797,22 +818,33 @@ size_t walk_eval_smem_bytes() { return sizeof(WarpSmem) * WARPS + 128; }
 
 template <int STAGE>
 cudaError_t launch_s(const KParams& p, int ppl, int ctas_per_sm, bool capture, cudaStream_t stream,
-                     LaunchInfo* info) {
+                     LaunchInfo* info, bool dry) {
   if (ppl == 1) {
-    return capture ? launch_t<1, STAGE, true>(p, ctas_per_sm, stream, info)
-                   : launch_t<1, STAGE, false>(p, ctas_per_sm, stream, info);
+    return capture ? launch_t<1, STAGE, true>(p, ctas_per_sm, stream, info, dry)
+                   : launch_t<1, STAGE, false>(p, ctas_per_sm, stream, info, dry);
   }
-  return capture ? launch_t<2, STAGE, true>(p, ctas_per_sm, stream, info)
-                 : launch_t<2, STAGE, false>(p, ctas_per_sm, stream, info);
+  return capture ? launch_t<2, STAGE, true>(p, ctas_per_sm, stream, info, dry)
+                 : launch_t<2, STAGE, false>(p, ctas_per_sm, stream, info, dry);
+}
+
+cudaError_t launch_dispatch(const KParams& p, int ppl, int ctas_per_sm, bool capture, cudaStream_t stream,
+                            LaunchInfo* info, bool dry) {
+  switch (p.stage) {
+    case STAGE_BULK: return launch_s<STAGE_BULK>(p, ppl, ctas_per_sm, capture, stream, info, dry);
+    case STAGE_ASYNC: return launch_s<STAGE_ASYNC>(p, ppl, ctas_per_sm, capture, stream, info, dry);
+    default: return launch_s<STAGE_GATHER4>(p, ppl, ctas_per_sm, capture, stream, info, dry);
+  }
 }
 
 cudaError_t launch_walk_eval(const KParams& p, int ppl, int ctas_per_sm, bool capture,
                              cudaStream_t stream, LaunchInfo* info) {
-  switch (p.stage) {
-    case STAGE_BULK: return launch_s<STAGE_BULK>(p, ppl, ctas_per_sm, capture, stream, info);
-    case STAGE_ASYNC: return launch_s<STAGE_ASYNC>(p, ppl, ctas_per_sm, capture, stream, info);
-    default: return launch_s<STAGE_GATHER4>(p, ppl, ctas_per_sm, capture, stream, info);
-  }
+  return launch_dispatch(p, ppl, ctas_per_sm, capture, stream, info, false);
+}
+
+cudaError_t prepare_walk_eval(int ppl, int stage, int ctas_per_sm, LaunchInfo* info) {
+  KParams p{};
+  p.stage = stage;
+  return launch_dispatch(p, ppl, ctas_per_sm, false, nullptr, info, true);
 }
 
 // ---------------------------------------------------------------- allocation-free launch

@@ -55,6 +55,10 @@ _SIGS = {
     "octgrav_debug_lists": (C.c_int, [_vp, C.c_double, C.c_int, _vp, _vp, _vp, _vp, _vp]),
     "octgrav_set_launch": (C.c_int, [_vp, C.c_int, C.c_int]),
     "octgrav_set_staging": (C.c_int, [_vp, C.c_int]),
+    "octgrav_graph_capture": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double, _vp, _vp]),
+    "octgrav_graph_launch": (C.c_int, [_vp, _vp]),
+    "octgrav_autotune": (C.c_int, [C.c_int, _i64, _f64, _f64, C.c_int, C.c_double, C.c_double, _vp, C.c_int,
+                                   _vp, _vp, _vp]),
     "octgrav_free_tree": (None, [_vp]),
     "octgrav_forces_noalloc": (C.c_int, [_vp, _vp, C.POINTER(C.c_size_t), C.c_double, C.c_double, C.c_double,
                                          _vp, _vp]),
@@ -246,6 +250,15 @@ class Tree:
         _check(load().octgrav_forces_noalloc(self._h, C.c_void_p(ptr), C.byref(sz), float(eps), float(theta),
                                              float(G), C.c_void_p(optr), _stream_handle(stream)))
 
+    def capture_graph(self, eps: float, theta: float, out, G: float = 1.0, stream=None):
+        """Capture one forces_device call into a CUDA graph (needs a non-default stream)."""
+        ptr = out if isinstance(out, int) else out.data_ptr()
+        _check(load().octgrav_graph_capture(self._h, float(eps), float(theta), float(G), C.c_void_p(ptr),
+                                            _stream_handle(stream)))
+
+    def launch_graph(self, stream=None):
+        _check(load().octgrav_graph_launch(self._h, _stream_handle(stream)))
+
     def status(self, stream=None) -> int:
         return int(load().octgrav_status(self._h, _stream_handle(stream)))
 
@@ -278,6 +291,24 @@ def forces(pos, mass, eps: float, theta: float, n_leaf: int = 16, n_group: int |
                                  int(n_group if n_group is not None else n_leaf), _p(acc), _p(pot),
                                  _stream_handle(stream)))
     return acc, pot
+
+
+def autotune(systems, n_leaf: int = 16, eps: float = 0.01, theta: float = 0.5, candidates=(16, 32, 64, 128),
+             stream=None) -> dict:
+    """Pick n_group and particles-per-lane by timing the kernel on these systems.
+
+    systems: list of (pos [n_s,3], mass [n_s]) pairs (one pair for a single system)."""
+    lib = load()
+    pos = np.ascontiguousarray(np.concatenate([np.asarray(p, np.float64).reshape(-1, 3) for p, _ in systems]))
+    mass = np.ascontiguousarray(np.concatenate([np.asarray(m, np.float64) for _, m in systems]))
+    off = np.zeros(len(systems) + 1, np.int64)
+    off[1:] = np.cumsum([len(m) for _, m in systems])
+    cand = np.ascontiguousarray(candidates, dtype=np.int32)
+    best = np.zeros(3, np.int32)
+    ms = np.zeros(1)
+    _check(lib.octgrav_autotune(len(systems), off, pos.reshape(-1), mass, int(n_leaf), float(eps), float(theta),
+                                _p(cand), len(cand), _p(best), _p(ms), _stream_handle(stream)))
+    return dict(n_group=int(best[0]), particles_per_lane=int(best[1]), ms=float(ms[0]))
 
 
 def version() -> int:
