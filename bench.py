@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the theta scan, clustered and ensemble legs")
     return ap.parse_args()
 
 
@@ -169,6 +170,116 @@ def accuracy(acc, pos, m, a, R):
     return {"rel_rms_vs_fp64_oracle": rms, "oracle_particles": int(len(idx)),
             "median_rel_err_vs_direct": float(np.median(e)), "p99_rel_err_vs_direct": float(np.percentile(e, 99)),
             "direct_sample": int(len(samp))}
+
+
+def time_kernel(torch, launch, flush, steps, stream):
+    """Median CUDA-event time (ms) of `launch()` over `steps` runs, L2 flushed before each."""
+    ts = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        launch()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def device_acc(torch, T, out, n):
+    acc = np.empty((n, 3))
+    acc[T.perm()] = out.cpu().numpy()[:, :3]
+    return acc
+
+
+def theta_for_median(torch, T, out, eps, samp, ad, target=1e-3, lo=0.5, hi=2.5, iters=9):
+    """Bisect theta so that the median Delta a/a over the sampled particles hits target."""
+    import oracle as O
+
+    def med(th):
+        T.forces_device(eps, th, out)
+        torch.cuda.synchronize()
+        acc = device_acc(torch, T, out, T.n)
+        return float(np.median(O.rel_err(acc[samp], ad)))
+    m_lo, m_hi = med(lo), med(hi)
+    if not (m_lo < target < m_hi):
+        return None, None
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        mm = med(mid)
+        if mm < target:
+            lo, m_lo = mid, mm
+        else:
+            hi, m_hi = mid, mm
+    return lo, m_lo
+
+
+def extras(torch, G, a, pos, m, T, out, flush, stream, peak, steps):
+    import oracle as O
+    res = {}
+    # C2 at theta = 0.75
+    T.forces_device(a.eps, 0.75, out, stream=stream)
+    ms = time_kernel(torch, lambda: T.forces_device(a.eps, 0.75, out, stream=stream), flush, steps, stream)
+    c = T.interaction_counts()
+    res["plummer_theta0.75"] = {"forces_per_s": a.n / (ms * 1e-3), "ms": ms, "frac_fp32_peak": c["flops"] / ms / 1e9 / peak,
+                                "flops_per_particle": c["flops"] / a.n}
+    # C2 at the theta whose median Delta a/a vs direct summation is 1e-3
+    samp = W.sample_indices(a.n, 1024, seed=17)
+    ad, _ = O.direct(pos, m, a.eps, targets=samp)
+    th, md = theta_for_median(torch, T, out, a.eps, samp, ad)
+    if th is not None:
+        ms = time_kernel(torch, lambda: T.forces_device(a.eps, th, out, stream=stream), flush, steps, stream)
+        c = T.interaction_counts()
+        res["plummer_median_1e-3"] = {"theta": th, "median_rel_err": md, "forces_per_s": a.n / (ms * 1e-3),
+                                      "ms": ms, "frac_fp32_peak": c["flops"] / ms / 1e9 / peak,
+                                      "flops_per_particle": c["flops"] / a.n}
+    # C3: clustered, 4,194,304 particles, theta 0.5, eps 0.001
+    cpos, cm = W.clustered(4_194_304, 64, seed=3)
+    CT = G.Tree.build(cpos, cm, a.n_leaf, a.n_group)
+    cout = torch.empty((CT.n, 4), dtype=torch.float32, device="cuda")
+    CT.forces_device(0.001, 0.5, cout, stream=stream)
+    ms = time_kernel(torch, lambda: CT.forces_device(0.001, 0.5, cout, stream=stream), flush, steps, stream)
+    c = CT.interaction_counts()
+    cacc = device_acc(torch, CT, cout, CT.n)
+    R = O.Tree(cpos, cm, a.n_leaf, a.n_group)
+    gsel = np.unique(W.sample_indices(R.n_groups, 100, seed=9))
+    ra, _, _, _, _ = R.forces(0.001, 0.5, groups=gsel, counts=False)
+    idx = np.concatenate([R.cell_members(int(R.groups[g])) for g in gsel])
+    csamp = W.sample_indices(CT.n, 512, seed=19)
+    cad, _ = O.direct(cpos, cm, 0.001, targets=csamp)
+    res["clustered_4M"] = {"workload": "64 Plummer spheres N=4194304 theta=0.5 eps=0.001 N_leaf=%d N_group=%d"
+                                       % (a.n_leaf, a.n_group),
+                           "forces_per_s": CT.n / (ms * 1e-3), "ms": ms,
+                           "frac_fp32_peak": c["flops"] / ms / 1e9 / peak,
+                           "rel_rms_vs_fp64_oracle": O.rel_rms(cacc[idx], ra[idx]),
+                           "median_rel_err_vs_direct": float(np.median(O.rel_err(cacc[csamp], cad)))}
+    del CT, cout, R
+    # C4: 256-system ensemble, one graph-captured persistent launch, autotuned
+    systems = W.ensemble(256, seed=4)
+    best = G.autotune(systems, n_leaf=a.n_leaf, eps=0.01, theta=0.6, candidates=(16, 32, 64, 128), stream=stream)
+    ET = G.Tree.build_batch(systems, a.n_leaf, best["n_group"])
+    ET.set_launch(best["particles_per_lane"])
+    eout = torch.empty((ET.n, 4), dtype=torch.float32, device="cuda")
+    gstream = torch.cuda.Stream()
+    with torch.cuda.stream(gstream):
+        ET.capture_graph(0.01, 0.6, eout, stream=gstream)
+        ET.launch_graph(stream=gstream)
+        gstream.synchronize()
+        ms = time_kernel(torch, lambda: ET.launch_graph(stream=gstream), flush, steps, gstream)
+    c = ET.interaction_counts(stream=gstream)
+    eacc = device_acc(torch, ET, eout, ET.n)
+    errs = []
+    for s in range(0, 256, 37):
+        pos_s, m_s = systems[s]
+        ra, _, _, _, _ = O.Tree(pos_s, m_s, a.n_leaf, best["n_group"]).forces(0.01, 0.6, counts=False)
+        errs.append(O.rel_rms(eacc[ET.offsets[s]:ET.offsets[s + 1]], ra))
+    res["ensemble_256"] = {"workload": "256 Plummer systems, N log-uniform in [1024, 65536], total N=%d, theta=0.6 "
+                                       "eps=0.01 N_leaf=%d" % (ET.n, a.n_leaf),
+                           "autotuned": best, "launch": "CUDA graph replay of one persistent launch",
+                           "forces_per_s": ET.n / (ms * 1e-3), "ms": ms,
+                           "frac_fp32_peak": c["flops"] / ms / 1e9 / peak,
+                           "max_rel_rms_vs_fp64_oracle_7_systems": max(errs)}
+    return res
 
 
 def run_reference(a, rank, world):
@@ -324,6 +435,8 @@ def main():
             import oracle as O
             R = O.Tree(pos, m, a.n_leaf, a.n_group)
         line["accuracy"] = accuracy(acc, pos, m, a, R)
+    if not a.no_extras:
+        line["extras"] = extras(torch, G, a, pos, m, T, out, flush, stream, peak, min(a.steps, 10))
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
