@@ -52,8 +52,8 @@ def parse():
     ap.add_argument("--theta", type=float, default=0.5)
     ap.add_argument("--eps", type=float, default=0.01)
     ap.add_argument("--n-leaf", type=int, default=16)
-    ap.add_argument("--n-group", type=int, default=64)
-    ap.add_argument("--ppl", type=int, default=2)
+    ap.add_argument("--n-group", type=int, default=0, help="0 = chosen by the autotuner")
+    ap.add_argument("--ppl", type=int, default=0, help="0 = chosen by the autotuner")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget")
@@ -130,6 +130,25 @@ def fp32_peak_tflops(torch):
     except (OSError, ValueError):
         pass
     return sms * 128 * 2 * mhz * 1e6 / 1e12, sms, mhz
+
+
+def measured_traffic(a):
+    """DRAM bytes per launch from the committed ncu summary, if it matches this kernel and workload."""
+    import hashlib
+    try:
+        fields = {}
+        for line in open(os.path.join(ROOT, "profiles", "walk_eval_traffic.txt")):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                fields[k.strip()] = v.strip()
+        src = open(os.path.join(ROOT, "paper_1005_5384_gb300", "csrc", "octgrav_kernels.cu"), "rb").read()
+        if hashlib.sha256(src).hexdigest()[:16] != fields["kernel_source_sha256_prefix"]:
+            return None
+        if fields["workload"] != workload_name(a):
+            return None
+        return int(fields["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def cpu_baseline(pos, m, a, budget_s):
@@ -256,7 +275,8 @@ def extras(torch, G, a, pos, m, T, out, flush, stream, peak, steps):
     del CT, cout, R
     # C4: 256-system ensemble, one graph-captured persistent launch, autotuned
     systems = W.ensemble(256, seed=4)
-    best = G.autotune(systems, n_leaf=a.n_leaf, eps=0.01, theta=0.6, candidates=(16, 32, 64, 128), stream=stream)
+    best = G.autotune(systems, n_leaf=a.n_leaf, eps=0.01, theta=0.6, candidates=(16, 32, 64, 128, 256, 512),
+                      stream=stream)
     ET = G.Tree.build_batch(systems, a.n_leaf, best["n_group"])
     ET.set_launch(best["particles_per_lane"])
     eout = torch.empty((ET.n, 4), dtype=torch.float32, device="cuda")
@@ -288,6 +308,8 @@ def run_reference(a, rank, world):
     import oracle as O
     pos, m = W.plummer(a.n, seed=a.seed)
     threads = O.default_threads()
+    if a.n_group <= 0:
+        a.n_group = 256  # the group size the GPU autotuner selects for this workload
     R = O.Tree(pos, m, a.n_leaf, a.n_group)
     rng = np.random.default_rng(5)
     budget = max(1.0, 120.0 / max(1, a.steps + a.warmup))
@@ -339,6 +361,12 @@ def main():
 
     pos, m = W.plummer(a.n, seed=a.seed + rank)
     G.load()
+    tuned = None
+    if a.n_group <= 0 or a.ppl <= 0:
+        tuned = G.autotune([(pos, m)], n_leaf=a.n_leaf, eps=a.eps, theta=a.theta,
+                           candidates=(16, 32, 64, 128, 256, 512))
+        a.n_group = a.n_group if a.n_group > 0 else tuned["n_group"]
+        a.ppl = a.ppl if a.ppl > 0 else tuned["particles_per_lane"]
     T = G.Tree.build(pos, m, a.n_leaf, a.n_group)
     T.set_launch(a.ppl)
     T.upload()
@@ -406,6 +434,7 @@ def main():
         "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload_name(a), "seed": a.seed, "particles_per_lane": a.ppl,
+                   "autotuner": tuned,
                    "l2": "flushed (256 MiB write) before every timed step, outside the events",
                    "parallelism": "replica per GPU" if world > 1 else "1 GPU"},
         "gflops": achieved * 1e3, "frac_fp32_peak": achieved / peak,
@@ -416,7 +445,7 @@ def main():
                 "path": "octgrav_forces_ex: host FP64 build + upload + kernel + download + unpermute"},
         "gpu_launches": a.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": measured_traffic(a),
                      "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz" % (sms, mhz),
                      "kernel": "walk_eval_kernel (fused walk + evaluation)"},
         "clocks": clk,
