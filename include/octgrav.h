@@ -186,6 +186,52 @@ int octgrav_autotune(int n_sys, const int64_t *offsets, const double *pos, const
                      int n_leaf, double eps, double theta, const int *n_group_cand, int n_cand,
                      int *best, double *best_ms, void *stream);
 
+/* ---- Learned opening criterion (a small network consulted inside the walk).
+ * Record layout (OCTGRAV_MLP_RECORD floats): input mean[12], standard
+ * deviation[12], standardised-input range min[12] and max[12], then the
+ * network W1[64][12], b1[64], W2[64][64], b2[64], w3[64], b3. The network maps
+ * the 12 inputs of a (group, cell) pair -- log2 l, log2 d, log2 |com - C_g|,
+ * l/d, log2 M, |S|_F/(M l^2), log2 count, the group's half extents / l (3),
+ * group count / N_group, log2 |C_g - com_root| -- to a prediction of log10 of
+ * the relative force error of accepting the cell. */
+#define OCTGRAV_MLP_RECORD 5105
+#define OCTGRAV_MLP_NPARAM 5057
+
+/* Training samples for the criterion, computed on the GPU: for each listed
+ * group (index in tree order, 0 .. n_groups-1 of octgrav_tree_stats), every
+ * child tested by a walk with theta_walk whose cube has h > 0 and lies apart
+ * from the group box gives one sample: features[12] (FP32) and the label =
+ * max over the group's particles of |a_multipole - a_direct(members)| /
+ * |a_ref| (FP64 direct sums; a_ref from this tree at theta = 0.3), and
+ * pairs[2] = (group, cell index). *n_out = number of samples; at most cap
+ * are written (features == NULL: count only). Synchronous. */
+int octgrav_mlp_samples(octgrav_tree *t, const int64_t *groups, int64_t n_groups, double theta_walk,
+                        double eps, float *features, float *labels, int64_t *pairs, int64_t cap,
+                        int64_t *n_out, void *stream);
+
+/* Train the criterion's network on the GPU (FP32 forward/backward, Adam, mini-
+ * batches drawn by a counter-based generator from seed) on log10 of the
+ * labels, with inputs standardised over the samples. Writes the record
+ * (OCTGRAV_MLP_RECORD floats) and the last mini-batch loss. Synchronous. */
+int octgrav_mlp_train(const float *features, const float *labels, int64_t n, int steps, int batch,
+                      double lr, uint64_t seed, float *record, float *final_loss, void *stream);
+
+/* Gradient of L = sum (y - t)^2 / (2n) over n standardised inputs x[n][12]
+ * and targets t[n] at params (OCTGRAV_MLP_NPARAM floats) -> grad, *loss.
+ * Test hook for the training kernels. Synchronous. */
+int octgrav_mlp_grad(const float *params, const float *x, const float *t, int64_t n, float *grad,
+                     float *loss, void *stream);
+
+/* Use the learned criterion in later launches on this tree (record == NULL
+ * restores the plain test). A child is opened when the plain test with
+ * theta_hi opens it, accepted when the plain test with theta_lo accepts it,
+ * accepted when its cube has h = 0, and otherwise accepted iff the network's
+ * prediction is below tau; a child whose standardised inputs leave the
+ * training range falls back to the plain test with theta_fb. The launch's own
+ * theta argument is then unused. Errors: ERR_ARG, ERR_CUDA. */
+int octgrav_set_criterion(octgrav_tree *t, const float *record, double tau, double theta_lo,
+                          double theta_hi, double theta_fb);
+
 /* How the fused kernel stages accepted cell records into shared memory:
  *   0 = one cp.async.bulk (64 B) per record, issued by the accepting lane;
  *   1 = four 16-byte cp.async per record, issued by the accepting lane (default);

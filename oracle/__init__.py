@@ -14,6 +14,8 @@ Steps (Gaburov, Bedorf & Portegies Zwart 2010):
   Tree.lists()    O5  walk + list classification (Sec. 2.2, Listings 1-2)
   Tree.forces()   O6  particle-cell (monopole + quadrupole) and particle-leaf
                   evaluation (Sec. 2.3, Listings 3-4)
+  Tree.mlp_*      O8  learned opening criterion: features, error labels, the
+                  walk that consults the network (see oracle/mlp.py)
 """
 from __future__ import annotations
 
@@ -83,6 +85,21 @@ def _load():
         lib.ora_cell_field.argtypes = [_f64p, C.c_double, _f64p, _f64p, C.c_double, C.c_double,
                                        _f64p, _f64p]
         lib.ora_cell_field.restype = None
+        lib.ora_mlp_features.argtypes = [C.c_void_p, C.c_int64, C.c_int64, _f64p]
+        lib.ora_mlp_features.restype = None
+        lib.ora_mlp_samples.argtypes = [C.c_void_p, _i64p, C.c_int64, C.c_double, C.c_double, _f64p,
+                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int]
+        lib.ora_mlp_samples.restype = C.c_int64
+        lib.ora_mlp_forward.argtypes = [_f64p, _f64p]
+        lib.ora_mlp_forward.restype = C.c_double
+        lib.ora_forces_mlp.argtypes = [C.c_void_p, C.c_double, C.c_double, _f64p, _f64p, _f64p, _f64p, _f64p,
+                                       C.c_double, C.c_double, C.c_double, C.c_double, C.c_void_p, C.c_int64,
+                                       _f64p, _f64p, C.c_void_p, C.c_void_p, C.c_int]
+        lib.ora_forces_mlp.restype = C.c_int64
+        lib.ora_forces_on_lists.argtypes = [C.c_void_p, C.c_int64, _i64p, C.c_int64, _i64p, C.c_int64,
+                                            C.c_double, C.c_double, _f64p, _f64p]
+        lib.ora_forces_on_lists.restype = None
+        lib.ora_mlp_label_mode.argtypes = [C.c_int]
         _lib = lib
         return lib
 
@@ -232,12 +249,70 @@ class Tree:
             raise RuntimeError("oracle forces failed")
         return acc, pot, npp, npc, int(flips)
 
+    # ---- O8: learned opening criterion
+    def mlp_features(self, g: int, c: int) -> np.ndarray:
+        f = np.zeros(12)
+        _load().ora_mlp_features(self._h, int(g), int(c), f)
+        return f
+
+    def mlp_samples(self, groups, theta_walk: float, eps: float, aref, nthreads: int | None = None):
+        """Features [S,12], labels [S] (relative error of accepting), pairs [S,2] (group, cell)."""
+        lib = _load()
+        garr = np.ascontiguousarray(groups, dtype=np.int64)
+        aref = np.ascontiguousarray(aref, dtype=np.float64).reshape(-1)
+        nt = int(nthreads or default_threads())
+        tot = lib.ora_mlp_samples(self._h, garr, len(garr), float(theta_walk), float(eps), aref,
+                                  None, None, None, 0, nt)
+        feat = np.zeros((tot, 12))
+        lab = np.zeros(tot)
+        pair = np.zeros((tot, 2), np.int64)
+        lib.ora_mlp_samples(self._h, garr, len(garr), float(theta_walk), float(eps), aref,
+                            _ptr(feat), _ptr(lab), _ptr(pair), tot, nt)
+        return feat, lab, pair
+
+    def forces_mlp(self, eps: float, net: dict, tau: float, theta_lo: float, theta_hi: float, theta_fb: float,
+                   G: float = 1.0, groups=None, nthreads: int | None = None):
+        """O6 with the learned criterion: acc, pot, n_pp, n_pc, number of network evaluations."""
+        lib = _load()
+        acc = np.zeros((self.n, 3))
+        pot = np.zeros(self.n)
+        npp = np.zeros(self.n, np.int64)
+        npc = np.zeros(self.n, np.int64)
+        if groups is None:
+            gp, ng, garr = None, self.n_groups, None
+        else:
+            garr = np.ascontiguousarray(groups, dtype=np.int64)
+            gp, ng = garr.ctypes.data_as(C.c_void_p), garr.shape[0]
+        w = np.ascontiguousarray(net["w"], dtype=np.float64)
+        args = [np.ascontiguousarray(net[k], dtype=np.float64) for k in ("mu", "sigma", "fmin", "fmax")]
+        nm = lib.ora_forces_mlp(self._h, float(eps), float(G), w, *args, float(tau), float(theta_lo),
+                                float(theta_hi), float(theta_fb), gp, ng, acc.reshape(-1), pot, _ptr(npp),
+                                _ptr(npc), int(nthreads or default_threads()))
+        if nm < 0:
+            raise RuntimeError("oracle MLP forces failed")
+        return acc, pot, npp, npc, int(nm)
+
+    def forces_on_lists(self, g: int, cells, leaves, eps: float, G: float = 1.0):
+        """O6 for group g's particles (member order) from given cell and leaf lists (cell indices)."""
+        n = int(self.count[self.groups[g]])
+        acc = np.zeros((n, 3))
+        pot = np.zeros(n)
+        c = np.ascontiguousarray(cells, dtype=np.int64)
+        lv = np.ascontiguousarray(leaves, dtype=np.int64)
+        _load().ora_forces_on_lists(self._h, int(g), c, len(c), lv, len(lv), float(eps), float(G), acc.reshape(-1), pot)
+        return acc, pot
+
     def group_of_particle(self) -> np.ndarray:
         """Group index of every particle (input order)."""
         out = np.full(self.n, -1, np.int64)
         for g, c in enumerate(self.groups):
             out[self.cell_members(int(c))] = g
         return out
+
+
+def mlp_forward_c(w, x) -> float:
+    """O8 FP64 forward pass (C) of the packed 12-64-64-1 network on one input."""
+    return float(_load().ora_mlp_forward(np.ascontiguousarray(w, np.float64), np.ascontiguousarray(x, np.float64)))
 
 
 def rel_err(a, a_ref):

@@ -609,3 +609,315 @@ int64_t ora_forces(const ora_tree *T, double eps, double theta, double G, const 
     run_threads(forces_worker, &J, nthreads);
     return J.err ? -1 : J.flips;
 }
+
+/* ------------------------------------------------------------------------ */
+/* O8: learned opening criterion -- features, error labels, MLP walk        */
+/* ------------------------------------------------------------------------ */
+
+#define ORA_NF 12
+#define ORA_NH 64
+
+/* Box-to-cube distance in FP64 (the quantity the opening test compares). */
+static double box_cube_dist(const double *gmin, const double *gmax, const double *cube)
+{
+    double d2 = 0, h = cube[3];
+    for (int k = 0; k < 3; ++k) {
+        double below = gmin[k] - (cube[k] + h), above = (cube[k] - h) - gmax[k];
+        double t = below > above ? below : above;
+        if (t > 0) d2 += t * t;
+    }
+    return sqrt(d2);
+}
+
+static double lg2(double x) { return log2(x > 1e-30 ? x : 1e-30); }
+
+/* The 12 inputs of the learned criterion for group g and cell c (h > 0, d > 0):
+ *  0 log2 l, 1 log2 d, 2 log2 |com_c - C_g|, 3 l/d, 4 log2 M_c,
+ *  5 |S_c|_F / (M_c l^2), 6 log2 count_c, 7..9 group half extents / l,
+ *  10 count_g / N_group, 11 log2 |C_g - com_root|,
+ * with l = 2h the side of the cell's boundary cube, d the box-to-cube distance,
+ * C_g the centre of the group's boundary cube. */
+void ora_mlp_features(const ora_tree *T, int64_t g, int64_t c, double *f)
+{
+    const int64_t gc = T->group[g];
+    const double *cu = T->cube + 4 * c, *C = T->cube + 4 * gc, *cm = T->com + 3 * c, *S = T->S + 6 * c;
+    const double *rc = T->com; /* root centre of mass */
+    const double l = 2.0 * cu[3];
+    const double d = box_cube_dist(T->bmin + 3 * gc, T->bmax + 3 * gc, cu);
+    double r2 = 0, o2 = 0;
+    for (int k = 0; k < 3; ++k) { r2 += (cm[k] - C[k]) * (cm[k] - C[k]); o2 += (C[k] - rc[k]) * (C[k] - rc[k]); }
+    const double sf = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2] + 2.0 * (S[3] * S[3] + S[4] * S[4] + S[5] * S[5]));
+    const double M = T->M[c];
+    f[0] = lg2(l);
+    f[1] = lg2(d);
+    f[2] = lg2(sqrt(r2));
+    f[3] = l / d;
+    f[4] = lg2(M);
+    f[5] = M > 0 ? sf / (M * l * l) : 0.0;
+    f[6] = lg2((double)T->count[c]);
+    for (int k = 0; k < 3; ++k) f[7 + k] = 0.5 * (T->bmax[3 * gc + k] - T->bmin[3 * gc + k]) / l;
+    f[10] = (double)T->count[gc] / (double)T->n_group;
+    f[11] = lg2(sqrt(o2));
+}
+
+/* Error label of accepting cell c for group g: the largest, over the group's
+ * particles i, of |a_multipole(c, i) - a_direct(members of c, i)| / |a_ref(i)|,
+ * a_ref the particle's total acceleration (input order, 3 per particle). */
+static int g_label_mean = 0; /* prototype switch: 0 = max over the group, 1 = mean */
+void ora_mlp_label_mode(int mean) { g_label_mean = mean; }
+
+static double mlp_label(const ora_tree *T, int64_t g, int64_t c, double eps2, const double *aref)
+{
+    const int64_t gc = T->group[g];
+    double emax = 0, esum = 0;
+    for (int64_t a = T->first[gc]; a < T->first[gc] + T->count[gc]; ++a) {
+        const int64_t i = T->idx[a];
+        const double *xi = T->pos + 3 * i;
+        double am[3], pm;
+        ora_cell_field(T->com + 3 * c, T->M[c], T->S + 6 * c, xi, eps2, 1.0, am, &pm);
+        double ad[3] = {0, 0, 0};
+        for (int64_t b = T->first[c]; b < T->first[c] + T->count[c]; ++b) {
+            const int64_t j = T->idx[b];
+            if (j == i) continue;
+            const double *xj = T->pos + 3 * j;
+            double dx = xj[0] - xi[0], dy = xj[1] - xi[1], dz = xj[2] - xi[2];
+            double r2 = dx * dx + dy * dy + dz * dz + eps2;
+            double rinv = 1.0 / sqrt(r2);
+            double mr3 = T->mass[j] * rinv * rinv * rinv;
+            ad[0] += mr3 * dx; ad[1] += mr3 * dy; ad[2] += mr3 * dz;
+        }
+        const double *ar = aref + 3 * i;
+        double ea = sqrt((am[0] - ad[0]) * (am[0] - ad[0]) + (am[1] - ad[1]) * (am[1] - ad[1]) + (am[2] - ad[2]) * (am[2] - ad[2]));
+        double na = sqrt(ar[0] * ar[0] + ar[1] * ar[1] + ar[2] * ar[2]);
+        double e = na > 0 ? ea / na : 0;
+        if (e > emax) emax = e;
+        esum += e;
+    }
+    return g_label_mean ? esum / (double)T->count[gc] : emax;
+}
+
+/* Training samples: for each listed group, every child tested by a walk with
+ * opening parameter theta_walk whose cube has h > 0 and lies at d > 0 from the
+ * group box yields (features, label, group, cell). Returns the number of
+ * samples (at most cap are written). */
+typedef struct {
+    const ora_tree *T; const int64_t *groups; int64_t ng; double theta, eps2; const double *aref;
+    double *feat, *label; int64_t *pair; int64_t cap; int64_t *offs; int pass; int64_t next;
+} samp_job;
+
+static void *samp_worker(void *arg)
+{
+    samp_job *J = (samp_job *)arg;
+    const ora_tree *T = J->T;
+    const float theta2 = (float)(J->theta * J->theta);
+    vec stack = {0, 0, 0};
+    for (;;) {
+        int64_t k = __atomic_fetch_add(&J->next, 1, __ATOMIC_RELAXED);
+        if (k >= J->ng) break;
+        const int64_t g = J->groups[k], gc = T->group[g];
+        int64_t cnt = 0, base = J->pass ? J->offs[k] : 0;
+        stack.n = 0;
+        if (!T->leaf[0]) vpush(&stack, 0);
+        while (stack.n) {
+            int64_t node = stack.v[--stack.n];
+            for (int o = 0; o < 8; ++o) {
+                int64_t ch = T->child[8 * node + o];
+                if (ch < 0) continue;
+                int op = open_cell(T, g, ch, theta2);
+                double d = box_cube_dist(T->bmin + 3 * gc, T->bmax + 3 * gc, T->cube + 4 * ch);
+                if (T->cube[4 * ch + 3] > 0 && d > 0) {
+                    if (J->pass) {
+                        int64_t s = base + cnt;
+                        if (s < J->cap) {
+                            ora_mlp_features(T, g, ch, J->feat + ORA_NF * s);
+                            J->label[s] = mlp_label(T, g, ch, J->eps2, J->aref);
+                            J->pair[2 * s] = g; J->pair[2 * s + 1] = ch;
+                        }
+                    }
+                    ++cnt;
+                }
+                if (op && !T->leaf[ch]) vpush(&stack, ch);
+            }
+        }
+        if (!J->pass) J->offs[k] = cnt;
+    }
+    free(stack.v);
+    return NULL;
+}
+
+int64_t ora_mlp_samples(const ora_tree *T, const int64_t *groups, int64_t ng, double theta_walk, double eps,
+                        const double *aref, double *feat, double *label, int64_t *pair, int64_t cap, int nthreads)
+{
+    int64_t *offs = (int64_t *)calloc((size_t)ng + 1, sizeof(int64_t));
+    samp_job J = {T, groups, ng, theta_walk, eps * eps, aref, feat, label, pair, cap, offs, 0, 0};
+    run_threads(samp_worker, &J, nthreads);
+    int64_t tot = 0;
+    for (int64_t k = 0; k < ng; ++k) { int64_t c = offs[k]; offs[k] = tot; tot += c; }
+    if (feat && label && pair && cap > 0) {
+        J.pass = 1; J.next = 0;
+        run_threads(samp_worker, &J, nthreads);
+    }
+    free(offs);
+    return tot;
+}
+
+/* FP64 forward pass of the 12 -> 64 -> 64 -> 1 ReLU network. Layout of w:
+ * W1[64][12], b1[64], W2[64][64], b2[64], w3[64], b3 (5057 values). */
+double ora_mlp_forward(const double *w, const double *x)
+{
+    const double *W1 = w, *b1 = w + ORA_NH * ORA_NF, *W2 = b1 + ORA_NH, *b2 = W2 + ORA_NH * ORA_NH;
+    const double *w3 = b2 + ORA_NH, *b3 = w3 + ORA_NH;
+    double h1[ORA_NH], y = *b3;
+    for (int j = 0; j < ORA_NH; ++j) {
+        double s = b1[j];
+        for (int i = 0; i < ORA_NF; ++i) s += W1[j * ORA_NF + i] * x[i];
+        h1[j] = s > 0 ? s : 0;
+    }
+    for (int j = 0; j < ORA_NH; ++j) {
+        double s = b2[j];
+        for (int i = 0; i < ORA_NH; ++i) s += W2[j * ORA_NH + i] * h1[i];
+        y += w3[j] * (s > 0 ? s : 0);
+    }
+    return y;
+}
+
+/* The learned criterion's decision for group g and child c (1 = open):
+ * the FP32 opening test with theta_hi opens -> open; with theta_lo accepts ->
+ * accept; otherwise (between the two) a cell with h = 0 is accepted (its
+ * monopole is exact), a cell whose standardised features leave [fmin, fmax]
+ * uses the FP32 test with theta_fb, and any other is accepted iff the network
+ * predicts log10 error < tau. Standardisation: x = (f - mu) / sigma. */
+typedef struct {
+    const double *w, *mu, *sigma, *fmin, *fmax; double tau, theta_lo, theta_hi, theta_fb;
+} mlp_rule;
+
+static int mlp_open(const ora_tree *T, int64_t g, int64_t c, const mlp_rule *R, int64_t *n_mlp)
+{
+    if (open_cell(T, g, c, (float)(R->theta_hi * R->theta_hi))) return 1;
+    if (!open_cell(T, g, c, (float)(R->theta_lo * R->theta_lo))) return 0;
+    if (T->cube[4 * c + 3] == 0) return 0;
+    double f[ORA_NF], x[ORA_NF];
+    ora_mlp_features(T, g, c, f);
+    for (int i = 0; i < ORA_NF; ++i) {
+        x[i] = (f[i] - R->mu[i]) / R->sigma[i];
+        if (!(x[i] >= R->fmin[i] && x[i] <= R->fmax[i])) return open_cell(T, g, c, (float)(R->theta_fb * R->theta_fb));
+    }
+    if (n_mlp) ++*n_mlp;
+    return !(ora_mlp_forward(R->w, x) < R->tau);
+}
+
+typedef struct {
+    const ora_tree *T; double eps2, G; const mlp_rule *R;
+    const int64_t *groups; int64_t ng; double *acc, *pot; int64_t *npp, *npc; int64_t next, n_mlp;
+} mlpf_job;
+
+static void *mlpf_worker(void *arg)
+{
+    mlpf_job *J = (mlpf_job *)arg;
+    const ora_tree *T = J->T;
+    vec cells = {0, 0, 0}, leaves = {0, 0, 0}, stack = {0, 0, 0};
+    int64_t nm = 0;
+    for (;;) {
+        int64_t k = __atomic_fetch_add(&J->next, 1, __ATOMIC_RELAXED);
+        if (k >= J->ng) break;
+        const int64_t g = J->groups ? J->groups[k] : k, gc = T->group[g];
+        cells.n = leaves.n = stack.n = 0;
+        if (T->leaf[0]) vpush(&leaves, 0); else vpush(&stack, 0);
+        while (stack.n) {
+            int64_t node = stack.v[--stack.n];
+            for (int o = 0; o < 8; ++o) {
+                int64_t ch = T->child[8 * node + o];
+                if (ch < 0) continue;
+                if (mlp_open(T, g, ch, J->R, &nm)) {
+                    if (T->leaf[ch]) vpush(&leaves, ch); else vpush(&stack, ch);
+                } else vpush(&cells, ch);
+            }
+        }
+        int64_t pp_src = 0;
+        for (int64_t l = 0; l < leaves.n; ++l) pp_src += T->count[leaves.v[l]];
+        for (int64_t a = T->first[gc]; a < T->first[gc] + T->count[gc]; ++a) {
+            const int64_t i = T->idx[a];
+            const double *xi = T->pos + 3 * i;
+            double ax = 0, ay = 0, az = 0, phi = 0;
+            for (int64_t e = 0; e < cells.n; ++e) {
+                double ac[3], pc;
+                ora_cell_field(T->com + 3 * cells.v[e], T->M[cells.v[e]], T->S + 6 * cells.v[e], xi, J->eps2, 1.0, ac, &pc);
+                ax += ac[0]; ay += ac[1]; az += ac[2]; phi += pc;
+            }
+            for (int64_t e = 0; e < leaves.n; ++e) {
+                const int64_t c = leaves.v[e];
+                for (int64_t b = T->first[c]; b < T->first[c] + T->count[c]; ++b) {
+                    const int64_t j = T->idx[b];
+                    if (j == i) continue;
+                    const double *xj = T->pos + 3 * j;
+                    double dx = xj[0] - xi[0], dy = xj[1] - xi[1], dz = xj[2] - xi[2];
+                    double rinv = 1.0 / sqrt(dx * dx + dy * dy + dz * dz + J->eps2);
+                    double mr3 = T->mass[j] * rinv * rinv * rinv;
+                    ax += mr3 * dx; ay += mr3 * dy; az += mr3 * dz;
+                    phi -= T->mass[j] * rinv;
+                }
+            }
+            J->acc[3 * i] = J->G * ax; J->acc[3 * i + 1] = J->G * ay; J->acc[3 * i + 2] = J->G * az;
+            J->pot[i] = J->G * phi;
+            if (J->npp) J->npp[i] = pp_src - 1;
+            if (J->npc) J->npc[i] = cells.n;
+        }
+    }
+    __atomic_fetch_add(&J->n_mlp, nm, __ATOMIC_RELAXED);
+    free(cells.v); free(leaves.v); free(stack.v);
+    return NULL;
+}
+
+/* Tree forces with the learned criterion (see mlp_open); arguments as
+ * ora_forces plus the network and its thresholds. Returns the number of
+ * network evaluations, or -1. */
+int64_t ora_forces_mlp(const ora_tree *T, double eps, double G, const double *w, const double *mu,
+                       const double *sigma, const double *fmin, const double *fmax, double tau, double theta_lo,
+                       double theta_hi, double theta_fb, const int64_t *groups, int64_t ng, double *acc,
+                       double *pot, int64_t *npp, int64_t *npc, int nthreads)
+{
+    mlp_rule R = {w, mu, sigma, fmin, fmax, tau, theta_lo, theta_hi, theta_fb};
+    mlpf_job J;
+    memset(&J, 0, sizeof J);
+    J.T = T; J.eps2 = eps * eps; J.G = G; J.R = &R;
+    J.groups = groups; J.ng = groups ? ng : T->n_groups;
+    J.acc = acc; J.pot = pot; J.npp = npp; J.npc = npc;
+    run_threads(mlpf_worker, &J, nthreads);
+    return J.n_mlp;
+}
+
+/* O6 on given lists: accelerations and potentials of group g's particles
+ * (in the group's member order) from the cells of `cells` (multipole) and the
+ * members of the leaves in `leaves` (direct, self excluded). Used to check a
+ * walk whose lists come from elsewhere. */
+void ora_forces_on_lists(const ora_tree *T, int64_t g, const int64_t *cells, int64_t nc, const int64_t *leaves,
+                         int64_t nl, double eps, double G, double *acc, double *pot)
+{
+    const int64_t gc = T->group[g];
+    const double eps2 = eps * eps;
+    for (int64_t a = 0; a < T->count[gc]; ++a) {
+        const int64_t i = T->idx[T->first[gc] + a];
+        const double *xi = T->pos + 3 * i;
+        double ax = 0, ay = 0, az = 0, phi = 0;
+        for (int64_t e = 0; e < nc; ++e) {
+            double ac[3], pc;
+            ora_cell_field(T->com + 3 * cells[e], T->M[cells[e]], T->S + 6 * cells[e], xi, eps2, 1.0, ac, &pc);
+            ax += ac[0]; ay += ac[1]; az += ac[2]; phi += pc;
+        }
+        for (int64_t e = 0; e < nl; ++e) {
+            const int64_t c = leaves[e];
+            for (int64_t b = T->first[c]; b < T->first[c] + T->count[c]; ++b) {
+                const int64_t j = T->idx[b];
+                if (j == i) continue;
+                const double *xj = T->pos + 3 * j;
+                double dx = xj[0] - xi[0], dy = xj[1] - xi[1], dz = xj[2] - xi[2];
+                double rinv = 1.0 / sqrt(dx * dx + dy * dy + dz * dz + eps2);
+                double mr3 = T->mass[j] * rinv * rinv * rinv;
+                ax += mr3 * dx; ay += mr3 * dy; az += mr3 * dz;
+                phi -= T->mass[j] * rinv;
+            }
+        }
+        acc[3 * a] = G * ax; acc[3 * a + 1] = G * ay; acc[3 * a + 2] = G * az;
+        pot[a] = G * phi;
+    }
+}

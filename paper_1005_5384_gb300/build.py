@@ -53,23 +53,28 @@ def build(force: bool = False, verbose: bool = False) -> str:
     cuda = _cuda_home()
     nvcc = os.path.join(cuda, "bin", "nvcc")
     ko = os.path.join(BUILD, "octgrav_kernels.o")
+    mo = os.path.join(BUILD, "octgrav_mlp.o")
     ho = os.path.join(BUILD, "octgrav_host.o")
-    k_cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xptxas", "-v" if verbose else "-O3",
-             "-Xcompiler", "-fPIC,-O2,-ffp-contract=off", "-I", INCLUDE,
-             "-c", os.path.join(CSRC, "octgrav_kernels.cu"), "-o", ko]
+
+    def nv(src, obj):
+        return [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xptxas", "-v" if verbose else "-O3",
+                "-Xcompiler", "-fPIC,-O2,-ffp-contract=off", "-I", INCLUDE,
+                "-c", os.path.join(CSRC, src), "-o", obj]
+    k_cmd = nv("octgrav_kernels.cu", ko)
+    m_cmd = nv("octgrav_mlp.cu", mo)
     h_cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-fno-fast-math", "-pthread",
              "-I", os.path.join(cuda, "include"), "-I", INCLUDE,
              "-c", os.path.join(CSRC, "octgrav_host.cpp"), "-o", ho]
-    procs = [subprocess.Popen(c, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
-             for c in (k_cmd, h_cmd)]
+    cmds = (k_cmd, m_cmd, h_cmd)
+    procs = [subprocess.Popen(c, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True) for c in cmds]
     outs = [p.communicate()[0] for p in procs]
-    for p, o, c in zip(procs, outs, (k_cmd, h_cmd)):
+    for p, o, c in zip(procs, outs, cmds):
         if p.returncode != 0:
             raise RuntimeError("build failed: %s\n%s" % (" ".join(c), o))
         if verbose and o:
             print(o)
     tmp = LIB + ".%d.tmp" % os.getpid()
-    link = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, ko, ho, "-lpthread"]
+    link = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, ko, mo, ho, "-lpthread"]
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed: %s\n%s" % (" ".join(link), r.stdout))

@@ -8,6 +8,8 @@
 
 namespace og {
 
+struct MlpDevice;
+
 // Device status bits (OR-ed into the status word by the kernel).
 enum : int {
   ST_STACK = 1,    // node stack overflow in a walk
@@ -51,6 +53,10 @@ struct KParams {
   int n_items;
   int n_cells;
   int stage;             // STAGING_*
+  // learned opening criterion (mlp != nullptr): network and band thresholds
+  const struct MlpDevice* mlp;
+  float theta_lo2, theta_hi2, theta_fb2;  // fl32(theta^2) of the band and the fallback
+  int n_group;
   // capture mode (tests): per item up to dbg_cap cell indices
   int* dbg_cell;
   int* dbg_leaf;
@@ -75,6 +81,35 @@ cudaError_t prepare_walk_eval(int ppl, int stage, int ctas_per_sm, LaunchInfo* i
 
 // Shared memory per CTA of the fused kernel.
 size_t walk_eval_smem_bytes();
+
+// Training samples of the learned criterion (octgrav_mlp.cu).
+struct MlpSampleArgs {
+  int n;                        // samples
+  int chunks;                   // ceil(largest group / 32)
+  const int* item;              // [n] work item of the sample's group (box, centre, range)
+  const int* cell;              // [n] candidate cell
+  const int4* items;
+  const float4* ibox;
+  const float4* geo;
+  const float4* mp;
+  const float4* parts;
+  const int2* link_first_count; // [nc] (first particle, count) of every cell
+  const double* com64;          // [3 nc] FP64 moments
+  const double* M64;
+  const double* S64;            // [6 nc]
+  const float4* aref;           // [n_particles] reference acceleration (tree order)
+  double eps2;
+  int n_group;
+  float* feat;                  // [n * 12]
+  double* label64;              // [n], zeroed before the label kernel
+};
+cudaError_t mlp_sample_features(const MlpSampleArgs& a, cudaStream_t st);
+cudaError_t mlp_sample_labels(const MlpSampleArgs& a, cudaStream_t st);
+// One training step's gradient (grad and loss accumulated, zero them first);
+// use_all: the B samples are X[0..B) instead of B counter-based draws.
+cudaError_t mlp_grad(const float* w, const float* X, const float* t, int n_total, int B, int step, uint64_t seed,
+                     bool use_all, float* grad, float* loss, cudaStream_t st);
+cudaError_t mlp_adam(float* w, float* m, float* v, const float* g, float lr, int step, cudaStream_t st);
 
 // Encode the 2-D tensor map over a cell-record array (n_cells rows of 64 B)
 // used by the gather4 staging. Returns cudaSuccess or an error.

@@ -28,6 +28,7 @@
 // Precision: positions are group-relative FP32, x' = (x_hi - C_hi) + (x_lo - C_lo)
 // with C the group centre kept as a hi/lo float pair; sums are accumulated in
 // FP32 and folded into a compensated (TwoSum) accumulator every ~32 terms.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -35,6 +36,7 @@
 
 #include "../../include/octgrav.h"
 #include "octgrav_internal.h"
+#include "octgrav_mlp.h"
 
 namespace og {
 namespace {
@@ -59,14 +61,20 @@ constexpr int PCH = 32;           // source particles per particle-particle chun
 constexpr int LQ = 64;            // leaf-queue entries (flushed at >= 32)
 constexpr long long WAIT_LIMIT = 1ll << 31;  // cycles (~1 s) before a wait gives up
 
-struct __align__(128) WarpSmem {
+constexpr int STACK_MLP = 384;    // node-stack entries per warp in the learned-criterion kernel
+constexpr int MQ = 64;            // deferred candidates awaiting the network (flushed at >= 32)
+
+template <bool GATHER, bool MLP>
+struct __align__(128) WarpSmemT {
   float4 ring[NTILE * TILE * 5];    // 7680 B; stride 80 B keeps 8 slots on 8 bank quads
-  int cidx[NTILE * TILE];           // 384 B: cell index per ring slot (gather4 staging)
   float4 pbuf[2][2 * PCH];          // 2048 B: two chunks of source particles (hi, lo records),
-                                    // rewritten in place to (x', m), (index, -, -, -)
+                                    // rewritten in place into pairs; also the network's input
+                                    // tile (32 rows x 16 bf16) during a network step
   int2 leafq[LQ];                   // 512 B: (first particle, count)
   int lpref[LQ];                    // 256 B: inclusive prefix of counts
-  int stack[STACK];                 // 2048 B: packed (first child << 3 | n_child - 1)
+  int stack[MLP ? STACK_MLP : STACK];  // packed (first child << 3 | n_child - 1)
+  int cidx[GATHER ? NTILE * TILE : 1]; // cell index per ring slot (gather4 staging)
+  int mq[MLP ? MQ : 1];             // deferred candidate cells
   unsigned long long bar[NTILE];    // one mbarrier per ring tile
 };
 
@@ -148,6 +156,79 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
   return m;
+}
+
+// Warp-level tensor-core MMA: D(16x8 f32) += A(16x16 bf16, row) * B(16x8 bf16, col).
+__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint2 b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
+}
+__device__ __forceinline__ void ldmatrix_x4(uint32_t* r, uint32_t addr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr));
+}
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// The learned criterion's network on the 32 rows of X (one candidate per lane;
+// 16 bf16 inputs per row, the last 4 zero): 12 -> 64 -> 64 -> 1 with ReLU,
+// bf16 weights and inputs, FP32 accumulation on the tensor cores. Returns the
+// prediction for row `lane`. Layer-1 accumulators become layer-2 A fragments
+// in registers (the C and A fragment layouts line up pairwise).
+__device__ float mlp_eval(const MlpDevice& W, uint32_t x_smem, int lane) {
+  float y00 = 0.f, y01 = 0.f, y10 = 0.f, y11 = 0.f;
+  const int q = 2 * (lane & 3);
+#pragma unroll 1
+  for (int t = 0; t < 2; ++t) {
+    uint32_t a[4];
+    ldmatrix_x4(a, x_smem + 2u * ((16 * t + (lane & 15)) * 16 + (lane >> 4) * 8));
+    uint32_t a2[4][4];
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
+      mma_bf16(c0, a, W.w1f[2 * kk][lane]);
+      mma_bf16(c1, a, W.w1f[2 * kk + 1][lane]);
+      const int u0 = 16 * kk + q, u1 = u0 + 8;
+      a2[kk][0] = pack_bf16(fmaxf(c0[0] + W.b1[u0], 0.f), fmaxf(c0[1] + W.b1[u0 + 1], 0.f));
+      a2[kk][1] = pack_bf16(fmaxf(c0[2] + W.b1[u0], 0.f), fmaxf(c0[3] + W.b1[u0 + 1], 0.f));
+      a2[kk][2] = pack_bf16(fmaxf(c1[0] + W.b1[u1], 0.f), fmaxf(c1[1] + W.b1[u1 + 1], 0.f));
+      a2[kk][3] = pack_bf16(fmaxf(c1[2] + W.b1[u1], 0.f), fmaxf(c1[3] + W.b1[u1 + 1], 0.f));
+    }
+    float r0 = 0.f, r1 = 0.f;
+#pragma unroll 1
+    for (int j = 0; j < 8; ++j) {
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) mma_bf16(acc, a2[kk], W.w2f[kk][j][lane]);
+      const int u = 8 * j + q;
+      r0 = fmaf(fmaxf(acc[0] + W.b2[u], 0.f), W.w3[u], r0);
+      r0 = fmaf(fmaxf(acc[1] + W.b2[u + 1], 0.f), W.w3[u + 1], r0);
+      r1 = fmaf(fmaxf(acc[2] + W.b2[u], 0.f), W.w3[u], r1);
+      r1 = fmaf(fmaxf(acc[3] + W.b2[u + 1], 0.f), W.w3[u + 1], r1);
+    }
+    r0 += __shfl_xor_sync(FULL, r0, 1);
+    r0 += __shfl_xor_sync(FULL, r0, 2);
+    r1 += __shfl_xor_sync(FULL, r1, 1);
+    r1 += __shfl_xor_sync(FULL, r1, 2);
+    if (t == 0) {
+      y00 = r0;  // row lane/4 of tile 0
+      y01 = r1;  // row lane/4 + 8
+    } else {
+      y10 = r0;
+      y11 = r1;
+    }
+  }
+  const int r = lane & 15, src = 4 * (r & 7);
+  const float v00 = __shfl_sync(FULL, y00, src), v01 = __shfl_sync(FULL, y01, src);
+  const float v10 = __shfl_sync(FULL, y10, src), v11 = __shfl_sync(FULL, y11, src);
+  const float v = lane < 16 ? (r < 8 ? v00 : v01) : (r < 8 ? v10 : v11);
+  return v + W.b3;
 }
 
 // Bounded wait for the phase of parity `parity`; false after ~1 s.
@@ -292,15 +373,33 @@ __device__ __forceinline__ SrcPair load_src_pair(const float4* q) {
 
 // ---------------------------------------------------------------- the kernel
 
-template <int R, int STAGE, bool CAPTURE>
-__global__ void __launch_bounds__(WARPS * 32, 2) walk_eval_kernel(const __grid_constant__ KParams p) {
+// The learned-criterion kernel runs one CTA of 12 warps per SM: the network
+// step needs registers beyond the 128 a two-CTA launch leaves per thread.
+constexpr int WARPS_MLP = 12;
+
+template <bool MLP>
+struct CtaWarps {
+  static constexpr int v = MLP ? WARPS_MLP : WARPS;
+};
+
+template <int R, int STAGE, bool CAPTURE, bool MLP>
+__global__ void __launch_bounds__(CtaWarps<MLP>::v * 32, MLP ? 1 : 2) walk_eval_kernel(const __grid_constant__ KParams p) {
   constexpr int REC = RingStride<STAGE>::v;
+  using WarpSmem = WarpSmemT<STAGE == STAGE_GATHER4, MLP>;
+  constexpr int STK = MLP ? STACK_MLP : STACK;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   // align to 128 B by offsetting the shared array itself (keeps the
   // shared address space visible to the compiler: LDS, not generic LD)
   unsigned char* smem_base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   WarpSmem& S = reinterpret_cast<WarpSmem*>(smem_base)[threadIdx.x >> 5];
+  MlpDevice& NW = *reinterpret_cast<MlpDevice*>(smem_base + sizeof(WarpSmem) * CtaWarps<MLP>::v);
+  if (MLP) {  // the network, shared by the CTA's warps
+    const uint4* src = reinterpret_cast<const uint4*>(p.mlp);
+    uint4* dst = reinterpret_cast<uint4*>(&NW);
+    for (int k = threadIdx.x; k < static_cast<int>(sizeof(MlpDevice) / 16); k += blockDim.x) dst[k] = src[k];
+    __syncthreads();
+  }
   const uint32_t bar0 = smem_u32(&S.bar[0]);
   if (lane == 0) {
     for (int t = 0; t < NTILE; ++t) mbar_init(bar0 + 8 * t, 1);
@@ -331,6 +430,14 @@ __global__ void __launch_bounds__(WARPS * 32, 2) walk_eval_kernel(const __grid_c
     const float4 sp = p.sysp ? __ldg(p.sysp + it.w) : p.sys0;
     const float theta2 = sp.x, G = p.sys0.z;
     const float2 E2 = f2(sp.y);
+    float f10 = 0.f, f11 = 0.f;  // learned criterion: group size and distance from the system's CoM
+    if (MLP) {
+      const float4 r0 = __ldg(p.mp + 4 * it.x), r1 = __ldg(p.mp + 4 * it.x + 1);
+      const float ox = (b0.w - r0.x) + (b2.x - r1.x), oy = (b1.w - r0.y) + (b2.y - r1.y),
+                  oz = (b2.w - r0.z) + (b2.z - r1.z);
+      f10 = static_cast<float>(gcount) / static_cast<float>(p.n_group);
+      f11 = mlp_lg2(sqrtf(ox * ox + oy * oy + oz * oz));
+    }
     const float3 gmin = make_float3(b0.x, b0.y, b0.z);
     const float3 gmax = make_float3(b1.x, b1.y, b1.z);
     const float3 chi = make_float3(b0.w, b1.w, b2.w);
@@ -576,19 +683,82 @@ __global__ void __launch_bounds__(WARPS * 32, 2) walk_eval_kernel(const __grid_c
       }
       __syncwarp();  // stack reads precede the next step's pushes
     };
-    if (top > 0) prefetch();
-    while (top > 0) {
+    // Learned criterion: the opening test with theta_hi opens, with theta_lo
+    // accepts; the candidates in between (with h > 0) are deferred to a queue
+    // that the network classifies 32 at a time. A network step takes the place
+    // of a stack step; its outcomes are handled like the test's.
+    int mq = 0;
+    auto network_step_next = [&]() { return MLP && (mq >= 32 || (top == 0 && mq > 0)); };
+    if (top > 0 && !network_step_next()) prefetch();
+    while (top > 0 || (MLP && mq > 0)) {
       if (app - done >= 2 * TILE) {
         // the oldest tile is complete and its copies were issued at least one step ago
         if (STAGE == STAGE_ASYNC) cp_async_wait_1();
         if (!eval_tile(TILE)) { ok = false; break; }
       }
-      top -= min(4, top);
-      const bool valid = nx_valid;
-      const int c = nx_c;
-      const float4 g = nx_g;
-      const int2 lk = nx_lk;
-      const bool open = valid && must_open(g, gmin, gmax, theta2);
+      bool valid, open, defer = false;
+      int c;
+      float4 g;
+      int2 lk;
+      if (network_step_next()) {
+        const int nb = min(32, mq);
+        valid = lane < nb;
+        c = valid ? S.mq[mq - nb + lane] : 0;
+        mq -= nb;
+        __syncwarp();
+        g = valid ? __ldg(p.geo + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+        lk = valid ? __ldg(p.link + c) : make_int2(0, 0);
+        float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0, q2 = q0, q3 = q0;
+        if (valid) {
+          q0 = __ldg(p.mp + 4 * c);
+          q1 = __ldg(p.mp + 4 * c + 1);
+          q2 = __ldg(p.mp + 4 * c + 2);
+          q3 = __ldg(p.mp + 4 * c + 3);
+        }
+        float f[MLP_NF];
+        mlp_features(g, q0, q1, q2, q3, gmin, gmax, chi, clo, f10, f11, f);
+        bool in_range = valid;
+        uint32_t xw[8];
+#pragma unroll
+        for (int i = 0; i < MLP_NF; i += 2) {
+          const float xa = (f[i] - NW.mu[i]) * NW.isig[i], xb = (f[i + 1] - NW.mu[i + 1]) * NW.isig[i + 1];
+          in_range = in_range && xa >= NW.xmin[i] && xa <= NW.xmax[i] && xb >= NW.xmin[i + 1] &&
+                     xb <= NW.xmax[i + 1];
+          xw[i / 2] = pack_bf16(xa, xb);
+        }
+        xw[6] = xw[7] = 0u;
+        if (!in_range) {
+#pragma unroll
+          for (int i = 0; i < 6; ++i) xw[i] = 0u;
+        }
+        uint4* xrow = reinterpret_cast<uint4*>(&S.pbuf[0][0]) + 2 * lane;
+        xrow[0] = make_uint4(xw[0], xw[1], xw[2], xw[3]);
+        xrow[1] = make_uint4(xw[4], xw[5], xw[6], xw[7]);
+        __syncwarp();
+        const float y = mlp_eval(NW, smem_u32(&S.pbuf[0][0]), lane);
+        __syncwarp();
+        open = valid && (in_range ? !(y < NW.tau) : must_open(g, gmin, gmax, p.theta_fb2));
+      } else {
+        top -= min(4, top);
+        valid = nx_valid;
+        c = nx_c;
+        g = nx_g;
+        lk = nx_lk;
+        if (MLP) {
+          const bool open_hi = valid && must_open(g, gmin, gmax, p.theta_hi2);
+          const bool open_lo = valid && must_open(g, gmin, gmax, p.theta_lo2);
+          defer = valid && !open_hi && open_lo && g.w > 0.f;
+          open = open_hi;
+        } else {
+          open = valid && must_open(g, gmin, gmax, theta2);
+        }
+      }
+      if (MLP) {
+        const unsigned m_def = __ballot_sync(FULL, defer);
+        if (defer) S.mq[mq + __popc(m_def & lt)] = c;
+        mq += __popc(m_def);
+        valid = valid && !defer;
+      }
       const bool leaf = lk.y < 0;
       // leaves of the own group are evaluated by the own pass, not queued
       const bool own_leaf = open && leaf && lk.x >= gfirst && lk.x < gfirst + gcount;
@@ -597,7 +767,7 @@ __global__ void __launch_bounds__(WARPS * 32, 2) walk_eval_kernel(const __grid_c
       const unsigned m_lq = __ballot_sync(FULL, open && leaf && !own_leaf);
       const unsigned m_node = __ballot_sync(FULL, open && !leaf);
       const int nn = __popc(m_node);
-      if (top + nn > STACK) {
+      if (top + nn > STK) {
         status |= ST_STACK;
         break;
       }
@@ -651,7 +821,7 @@ __global__ void __launch_bounds__(WARPS * 32, 2) walk_eval_kernel(const __grid_c
         iss = upto;
       }
       __syncwarp();
-      if (top > 0) prefetch();
+      if (top > 0 && !network_step_next()) prefetch();
       if (nlq >= TILE) {
         eval_leaves(nlq);
         nlq = 0;
@@ -752,10 +922,11 @@ struct LaunchCache {
   int sms[64] = {};
 };
 
-template <int R, int STAGE, bool CAPTURE>
+template <int R, int STAGE, bool CAPTURE, bool MLP = false>
 cudaError_t launch_t(const KParams& p, int ctas_per_sm, cudaStream_t stream, LaunchInfo* info, bool dry) {
-  const size_t smem = sizeof(WarpSmem) * WARPS + 128;
-  auto kern = walk_eval_kernel<R, STAGE, CAPTURE>;
+  constexpr int NW = CtaWarps<MLP>::v;
+  const size_t smem = sizeof(WarpSmemT<STAGE == STAGE_GATHER4, MLP>) * NW + (MLP ? sizeof(MlpDevice) : 0) + 128;
+  auto kern = walk_eval_kernel<R, STAGE, CAPTURE, MLP>;
   static LaunchCache cache;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -769,7 +940,7 @@ cudaError_t launch_t(const KParams& p, int ctas_per_sm, cudaStream_t stream, Lau
           cudaSuccess)
         return e;
       if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, WARPS * 32, smem)) != cudaSuccess) return e;
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NW * 32, smem)) != cudaSuccess) return e;
       if (occ < 1) return cudaErrorInvalidConfiguration;
       cache.grid_per_sm[dev] = occ;
       cache.sms[dev] = sms;
@@ -781,11 +952,11 @@ cudaError_t launch_t(const KParams& p, int ctas_per_sm, cudaStream_t stream, Lau
   const int grid = sms * per_sm;
   if (info) {
     info->grid = grid;
-    info->block = WARPS * 32;
+    info->block = NW * 32;
     info->smem = smem;
   }
   if (dry) return cudaSuccess;
-  kern<<<grid, WARPS * 32, smem, stream>>>(p);
+  kern<<<grid, NW * 32, smem, stream>>>(p);
   return cudaGetLastError();
 }
 
@@ -814,7 +985,7 @@ cudaError_t encode_mp_map(CUtensorMap* map, const void* mp, int n_cells) {
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-size_t walk_eval_smem_bytes() { return sizeof(WarpSmem) * WARPS + 128; }
+size_t walk_eval_smem_bytes() { return sizeof(WarpSmemT<false, false>) * WARPS + 128; }
 
 template <int STAGE>
 cudaError_t launch_s(const KParams& p, int ppl, int ctas_per_sm, bool capture, cudaStream_t stream,
@@ -829,6 +1000,10 @@ cudaError_t launch_s(const KParams& p, int ppl, int ctas_per_sm, bool capture, c
 
 cudaError_t launch_dispatch(const KParams& p, int ppl, int ctas_per_sm, bool capture, cudaStream_t stream,
                             LaunchInfo* info, bool dry) {
+  if (p.mlp) {  // learned criterion: one variant (2 particles per lane, cp.async staging)
+    return capture ? launch_t<2, STAGE_ASYNC, true, true>(p, ctas_per_sm, stream, info, dry)
+                   : launch_t<2, STAGE_ASYNC, false, true>(p, ctas_per_sm, stream, info, dry);
+  }
   switch (p.stage) {
     case STAGE_BULK: return launch_s<STAGE_BULK>(p, ppl, ctas_per_sm, capture, stream, info, dry);
     case STAGE_ASYNC: return launch_s<STAGE_ASYNC>(p, ppl, ctas_per_sm, capture, stream, info, dry);

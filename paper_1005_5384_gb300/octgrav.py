@@ -55,6 +55,12 @@ _SIGS = {
     "octgrav_debug_lists": (C.c_int, [_vp, C.c_double, C.c_int, _vp, _vp, _vp, _vp, _vp]),
     "octgrav_set_launch": (C.c_int, [_vp, C.c_int, C.c_int]),
     "octgrav_set_staging": (C.c_int, [_vp, C.c_int]),
+    "octgrav_mlp_samples": (C.c_int, [_vp, _i64, C.c_int64, C.c_double, C.c_double, _vp, _vp, _vp, C.c_int64,
+                                      C.POINTER(C.c_int64), _vp]),
+    "octgrav_mlp_train": (C.c_int, [_vp, _vp, C.c_int64, C.c_int, C.c_int, C.c_double, C.c_uint64, _vp, _vp,
+                                    _vp]),
+    "octgrav_mlp_grad": (C.c_int, [_vp, _vp, _vp, C.c_int64, _vp, _vp, _vp]),
+    "octgrav_set_criterion": (C.c_int, [_vp, _vp, C.c_double, C.c_double, C.c_double, C.c_double]),
     "octgrav_graph_capture": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double, _vp, _vp]),
     "octgrav_graph_launch": (C.c_int, [_vp, _vp]),
     "octgrav_autotune": (C.c_int, [C.c_int, _i64, _f64, _f64, C.c_int, C.c_double, C.c_double, _vp, C.c_int,
@@ -250,6 +256,31 @@ class Tree:
         _check(load().octgrav_forces_noalloc(self._h, C.c_void_p(ptr), C.byref(sz), float(eps), float(theta),
                                              float(G), C.c_void_p(optr), _stream_handle(stream)))
 
+    # ---- learned opening criterion
+    def mlp_samples(self, groups, theta_walk: float, eps: float, stream=None):
+        """(features [S,12] float32, labels [S] float32, pairs [S,2] (group, cell))."""
+        lib = load()
+        g = np.ascontiguousarray(groups, dtype=np.int64)
+        n = C.c_int64(0)
+        _check(lib.octgrav_mlp_samples(self._h, g, len(g), float(theta_walk), float(eps), None, None, None, 0,
+                                       C.byref(n), _stream_handle(stream)))
+        f = np.zeros((n.value, 12), np.float32)
+        lab = np.zeros(n.value, np.float32)
+        pr = np.zeros((n.value, 2), np.int64)
+        _check(lib.octgrav_mlp_samples(self._h, g, len(g), float(theta_walk), float(eps), _p(f), _p(lab), _p(pr),
+                                       n.value, C.byref(n), _stream_handle(stream)))
+        return f, lab, pr
+
+    def set_criterion(self, record=None, tau: float = -3.5, theta_lo: float = 0.5, theta_hi: float = 4.0,
+                      theta_fb: float = 1.0):
+        """Enable the learned criterion (record from mlp_train) or restore the plain test (None)."""
+        if record is None:
+            _check(load().octgrav_set_criterion(self._h, None, 0.0, 0.0, 0.0, 0.0))
+            return
+        r = np.ascontiguousarray(record, dtype=np.float32)
+        _check(load().octgrav_set_criterion(self._h, _p(r), float(tau), float(theta_lo), float(theta_hi),
+                                            float(theta_fb)))
+
     def capture_graph(self, eps: float, theta: float, out, G: float = 1.0, stream=None):
         """Capture one forces_device call into a CUDA graph (needs a non-default stream)."""
         ptr = out if isinstance(out, int) else out.data_ptr()
@@ -291,6 +322,33 @@ def forces(pos, mass, eps: float, theta: float, n_leaf: int = 16, n_group: int |
                                  int(n_group if n_group is not None else n_leaf), _p(acc), _p(pot),
                                  _stream_handle(stream)))
     return acc, pot
+
+
+MLP_RECORD = 5105
+MLP_NPARAM = 5057
+
+
+def mlp_train(features, labels, steps: int = 3000, batch: int = 4096, lr: float = 2e-3, seed: int = 1,
+              stream=None):
+    """Train the criterion's network on the GPU; returns (record [5105] float32, last loss)."""
+    f = np.ascontiguousarray(features, dtype=np.float32)
+    lab = np.ascontiguousarray(labels, dtype=np.float32)
+    rec = np.zeros(MLP_RECORD, np.float32)
+    loss = np.zeros(1, np.float32)
+    _check(load().octgrav_mlp_train(_p(f), _p(lab), len(lab), int(steps), int(batch), float(lr), int(seed),
+                                    _p(rec), _p(loss), _stream_handle(stream)))
+    return rec, float(loss[0])
+
+
+def mlp_grad(params, x, t, stream=None):
+    """GPU gradient of sum (y - t)^2 / (2n) at params over standardised inputs x [n,12]: (grad, loss)."""
+    w = np.ascontiguousarray(params, dtype=np.float32)
+    xx = np.ascontiguousarray(x, dtype=np.float32)
+    tt = np.ascontiguousarray(t, dtype=np.float32)
+    g = np.zeros(MLP_NPARAM, np.float32)
+    loss = np.zeros(1, np.float32)
+    _check(load().octgrav_mlp_grad(_p(w), _p(xx), _p(tt), len(tt), _p(g), _p(loss), _stream_handle(stream)))
+    return g, float(loss[0])
 
 
 def autotune(systems, n_leaf: int = 16, eps: float = 0.01, theta: float = 0.5, candidates=(16, 32, 64, 128),
