@@ -136,18 +136,21 @@ def measured_traffic(a):
     """DRAM bytes per launch from the committed ncu summary, if it matches this kernel and workload."""
     import hashlib
     try:
-        fields = {}
+        sha, table = None, {}
         for line in open(os.path.join(ROOT, "profiles", "walk_eval_traffic.txt")):
-            if ":" in line and not line.startswith("#"):
-                k, v = line.split(":", 1)
-                fields[k.strip()] = v.strip()
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            if line.startswith("kernel_source_sha256_prefix:"):
+                sha = line.split(":", 1)[1].strip()
+            elif " = " in line:
+                k, v = line.rsplit(" = ", 1)
+                table[k.strip()] = int(v)
         src = open(os.path.join(ROOT, "paper_1005_5384_gb300", "csrc", "octgrav_kernels.cu"), "rb").read()
-        if hashlib.sha256(src).hexdigest()[:16] != fields["kernel_source_sha256_prefix"]:
+        if hashlib.sha256(src).hexdigest()[:16] != sha:
             return None
-        if fields["workload"] != workload_name(a):
-            return None
-        return int(fields["dram_bytes_per_launch"])
-    except (OSError, KeyError, ValueError):
+        return table.get(workload_name(a))
+    except (OSError, ValueError):
         return None
 
 
@@ -299,7 +302,66 @@ def extras(torch, G, a, pos, m, T, out, flush, stream, peak, steps):
                            "forces_per_s": ET.n / (ms * 1e-3), "ms": ms,
                            "frac_fp32_peak": c["flops"] / ms / 1e9 / peak,
                            "max_rel_rms_vs_fp64_oracle_7_systems": max(errs)}
+    res["learned_criterion_sphere_disc_1M"] = learned_leg(torch, G, a, flush, stream, peak, steps)
     return res
+
+
+def learned_leg(torch, G, a, flush, stream, peak, steps):
+    """C5: sphere + disc, N = 1,048,576; the plain theta walk and the learned
+    criterion, each tuned to a median Delta a/a of 1e-3 against direct sums."""
+    import oracle as O
+    n = 1_048_576
+    band = dict(theta_lo=0.8, theta_hi=1.3, theta_fb=1.0)
+    t0 = time.perf_counter()
+    tpos, tm = W.sphere_disc(n, seed=6)                 # training system (another seed)
+    TT = G.Tree.build(tpos, tm, a.n_leaf, 64)
+    groups = np.sort(np.random.default_rng(0).choice(TT.stats["n_groups"], 128, replace=False))
+    f, lab, _ = TT.mlp_samples(groups, 0.35, 0.01, stream=stream)
+    rec, loss = G.mlp_train(f, lab, steps=3000, batch=4096, lr=2e-3, seed=3, stream=stream)
+    t_train = time.perf_counter() - t0
+    del TT
+    pos, m = W.sphere_disc(n, seed=5)
+    T = G.Tree.build(pos, m, a.n_leaf, 64)
+    out = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    samp = W.sample_indices(n, 1024, seed=23)
+    ad, _ = O.direct(pos, m, 0.01, targets=samp)
+
+    def med(theta):
+        T.forces_device(0.01, theta, out, stream=stream)
+        torch.cuda.synchronize()
+        return float(np.median(O.rel_err(device_acc(torch, T, out, n)[samp], ad)))
+
+    def bisect(fn, lo, hi, iters=10):
+        for _ in range(iters):
+            mid = 0.5 * (lo + hi)
+            if fn(mid) < 1e-3:
+                lo = mid
+            else:
+                hi = mid
+        return lo
+    th = bisect(med, 0.3, 2.0)
+    e_th = med(th)
+    c_th = T.interaction_counts()
+    ms_th = time_kernel(torch, lambda: T.forces_device(0.01, th, out, stream=stream), flush, steps, stream)
+
+    def med_tau(tau):
+        T.set_criterion(rec, tau=tau, **band)
+        return med(0.5)
+    tau = bisect(med_tau, -6.0, -1.0)
+    e_ml = med_tau(tau)
+    c_ml = T.interaction_counts()
+    ms_ml = time_kernel(torch, lambda: T.forces_device(0.01, 0.5, out, stream=stream), flush, steps, stream)
+    return {"workload": "sphere (r=1) + exponential disc (R_d=0.3, z_d=0.03), N=1048576, eps=0.01, "
+                        "N_leaf=%d N_group=64" % a.n_leaf,
+            "training": {"system": "same recipe, seed 6", "groups": 128, "samples": int(len(lab)),
+                         "steps": 3000, "final_loss": loss, "seconds": t_train},
+            "theta_walk": {"theta": th, "median_rel_err": e_th, "forces_per_s": n / (ms_th * 1e-3), "ms": ms_th,
+                           "flops_per_particle": c_th["flops"] / n,
+                           "frac_fp32_peak": c_th["flops"] / ms_th / 1e9 / peak},
+            "learned_walk": {"tau": tau, "band": band, "median_rel_err": e_ml, "forces_per_s": n / (ms_ml * 1e-3),
+                             "ms": ms_ml, "flops_per_particle": c_ml["flops"] / n,
+                             "frac_fp32_peak": c_ml["flops"] / ms_ml / 1e9 / peak},
+            "speedup_learned_over_theta": ms_th / ms_ml}
 
 
 def run_reference(a, rank, world):
