@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the theta scan, clustered and ensemble legs")
+    ap.add_argument("--leg", default="", choices=["", "learned"],
+                    help="learned: train the criterion on the 1M sphere+disc and launch the learned walk "
+                         "twice (a small driver for profilers; prints the interaction counts)")
     return ap.parse_args()
 
 
@@ -364,6 +367,27 @@ def learned_leg(torch, G, a, flush, stream, peak, steps):
             "speedup_learned_over_theta": ms_th / ms_ml}
 
 
+def run_learned_driver():
+    """Train on the sphere+disc (seed 6), launch the learned walk twice on seed 5."""
+    import torch
+    from paper_1005_5384_gb300 import octgrav as G
+    n = 1_048_576
+    pos, m = W.sphere_disc(n, seed=6)
+    TT = G.Tree.build(pos, m, 16, 64)
+    groups = np.sort(np.random.default_rng(0).choice(TT.stats["n_groups"], 128, replace=False))
+    f, lab, _ = TT.mlp_samples(groups, 0.35, 0.01)      # includes one plain-test launch
+    rec, _ = G.mlp_train(f, lab, steps=3000, batch=4096, lr=2e-3, seed=3)
+    del TT
+    pos, m = W.sphere_disc(n, seed=5)
+    T = G.Tree.build(pos, m, 16, 64)
+    T.set_criterion(rec, tau=-3.54, theta_lo=0.8, theta_hi=1.3, theta_fb=1.0)
+    out = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    for _ in range(2):
+        T.forces_device(0.01, 0.5, out)
+    torch.cuda.synchronize()
+    print(json.dumps({"status": T.status(), "counts": T.interaction_counts()}), flush=True)
+
+
 def run_reference(a, rank, world):
     if rank != 0:
         return
@@ -408,6 +432,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if a.impl == "reference":
         run_reference(a, rank, world)
+        return
+    if a.leg == "learned":
+        run_learned_driver()
         return
 
     import torch
