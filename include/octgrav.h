@@ -112,6 +112,51 @@ int octgrav_forces(const double *pos, const double *mass, int64_t n, double eps,
 int octgrav_forces_ex(const double *pos, const double *mass, int64_t n, double eps, double theta,
                       double G, int n_leaf, int n_group, double *acc, double *pot, void *stream);
 
+/* ---- Tree build on the GPU (Sec. 2.1 run as CUDA kernels).
+ *
+ * The same tree as octgrav_build_tree / octgrav_build_batch of the same data,
+ * byte for byte: Morton keys from the root cube, a stable radix sort, cells
+ * split level by level, FP64 tight boxes, boundary cubes, masses, centres of
+ * mass and second moments combined bottom-up in the host build's operation
+ * order, the same groups and work items. The arrays are written on the
+ * device in place; host copies of the tree (for the introspection calls
+ * below) are made only when one of those calls asks. The whole build is
+ * enqueued on `stream`; the call returns after reading one result block, so
+ * the inputs may be freed or overwritten afterwards. */
+
+/* One system from DEVICE arrays on the current device: pos_dev (n x 3 FP64,
+ * xyz interleaved), mass_dev (n FP64). Errors: ERR_ARG (NULL, n < 1,
+ * n_leaf < 1, n_group < n_leaf, too many particles or cells), ERR_NONFINITE
+ * (non-finite coordinate or mass, negative mass; found on the device),
+ * ERR_OOM, ERR_CUDA. */
+int octgrav_build_tree_gpu(const double *pos_dev, const double *mass_dev, int64_t n, int n_leaf,
+                           int n_group, void *stream, octgrav_tree **out);
+
+/* n_sys systems concatenated as for octgrav_build_batch: offsets is a HOST
+ * array (n_sys + 1, offsets[0] = 0, strictly increasing); pos_dev / mass_dev
+ * are device arrays. Errors as octgrav_build_tree_gpu. */
+int octgrav_build_batch_gpu(int n_sys, const int64_t *offsets, const double *pos_dev,
+                            const double *mass_dev, int n_leaf, int n_group, void *stream,
+                            octgrav_tree **out);
+
+/* Forces in INPUT order into DEVICE FP64 arrays: acc_dev (n x 3) and pot_dev
+ * (n, may be NULL), for any tree (host- or GPU-built). Enqueued on stream and
+ * not waited for: read the launch status with octgrav_status. Errors: ERR_ARG
+ * (NULL tree/acc_dev, bad eps/theta/G), ERR_OOM, ERR_CUDA. */
+int octgrav_forces_tree_device64(octgrav_tree *t, double eps, double theta, double G,
+                                 double *acc_dev, double *pot_dev, void *stream);
+
+/* One-shot call like octgrav_forces_ex with the tree built on the GPU: HOST
+ * arrays pos (n x 3), mass (n) in, acc (n x 3) and pot (n, may be NULL) out,
+ * both in input order. Copies the inputs to the device (at link speed when the
+ * host arrays are pinned), builds the tree, evaluates, unpermutes on the
+ * device and copies the FP64 results back; returns after the copies. Device
+ * buffers are cached between calls on the calling thread's current device.
+ * Errors as octgrav_build_tree_gpu plus the launch status (ERR_STACK,
+ * ERR_TIMEOUT, ERR_INDEX). */
+int octgrav_forces_gpu(const double *pos, const double *mass, int64_t n, double eps, double theta,
+                       double G, int n_leaf, int n_group, double *acc, double *pot, void *stream);
+
 /* Wait for stream and return the status of the last launch on this tree:
  * OK, ERR_STACK, ERR_TIMEOUT or ERR_INDEX. Clears nothing. */
 int octgrav_status(octgrav_tree *t, void *stream);

@@ -2,9 +2,10 @@
 
     python -m paper_1005_5384_gb300.build        # or build() from Python
 
-nvcc compiles the kernels for sm_103a only; g++ compiles the host library with
--ffp-contract=off (the octree definition relies on uncontracted FP64 ops).
-Both translation units compile in parallel; the result lands in
+nvcc compiles the kernels for sm_103a only (the GPU tree build with
+-fmad=false); g++ compiles the host library with -ffp-contract=off (the octree
+definition relies on uncontracted FP64 ops, and the two builds must agree to the
+bit). The translation units compile in parallel; the result lands in
 paper_1005_5384_gb300/_build/liboctgrav.so.
 """
 from __future__ import annotations
@@ -54,18 +55,20 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = os.path.join(cuda, "bin", "nvcc")
     ko = os.path.join(BUILD, "octgrav_kernels.o")
     mo = os.path.join(BUILD, "octgrav_mlp.o")
+    bo = os.path.join(BUILD, "octgrav_build.o")
     ho = os.path.join(BUILD, "octgrav_host.o")
 
-    def nv(src, obj):
+    def nv(src, obj, *extra):
         return [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xptxas", "-v" if verbose else "-O3",
-                "-Xcompiler", "-fPIC,-O2,-ffp-contract=off", "-I", INCLUDE,
+                "-Xcompiler", "-fPIC,-O2,-ffp-contract=off", *extra, "-I", INCLUDE,
                 "-c", os.path.join(CSRC, src), "-o", obj]
     k_cmd = nv("octgrav_kernels.cu", ko)
     m_cmd = nv("octgrav_mlp.cu", mo)
+    b_cmd = nv("octgrav_build.cu", bo, "-fmad=false")
     h_cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-fno-fast-math", "-pthread",
              "-I", os.path.join(cuda, "include"), "-I", INCLUDE,
              "-c", os.path.join(CSRC, "octgrav_host.cpp"), "-o", ho]
-    cmds = (k_cmd, m_cmd, h_cmd)
+    cmds = (k_cmd, m_cmd, b_cmd, h_cmd)
     procs = [subprocess.Popen(c, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True) for c in cmds]
     outs = [p.communicate()[0] for p in procs]
     for p, o, c in zip(procs, outs, cmds):
@@ -74,7 +77,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if verbose and o:
             print(o)
     tmp = LIB + ".%d.tmp" % os.getpid()
-    link = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, ko, mo, ho, "-lpthread"]
+    link = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, ko, mo, bo, ho, "-lpthread"]
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed: %s\n%s" % (" ".join(link), r.stdout))

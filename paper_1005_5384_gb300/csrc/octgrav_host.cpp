@@ -521,9 +521,16 @@ struct DevBuf {
 
 struct Device {
   DevBuf parts, geo, link, mp, items, ibox, sysp, out, counts, ctl, dbg, mlp;
+  // GPU build: tree arrays beyond the walk's, scratch, inputs and FP64 outputs
+  DevBuf perm, key, props, pcount, cfirst, groups, ikey, celloff, result, scratch, in_pos, in_mass, acc64, pot64;
   int device = -1;
+  int64_t cell_cap = 0;  // cell capacity that last sufficed for a GPU build
   void release() {
-    for (DevBuf* b : {&parts, &geo, &link, &mp, &items, &ibox, &sysp, &out, &counts, &ctl, &dbg, &mlp}) b->release();
+    for (DevBuf* b : {&parts, &geo, &link, &mp, &items, &ibox, &sysp, &out, &counts, &ctl, &dbg, &mlp, &perm, &key,
+                      &props, &pcount, &cfirst, &groups, &ikey, &celloff, &result, &scratch, &in_pos, &in_mass,
+                      &acc64, &pot64})
+      b->release();
+    cell_cap = 0;
   }
 };
 
@@ -565,6 +572,13 @@ struct octgrav_tree {
   Device* dev = &own;
   bool uploaded = false;
   bool launched = false;
+  // built on the GPU: the device arrays are the tree; the host images above
+  // are filled on demand (host_valid)
+  bool gpu = false;
+  bool host_valid = true;
+  bool perm_on_device = false;  // Device::perm holds the permutation (int32)
+  int64_t n_groups = 0, n_items = 0;
+  int64_t cell_cap = 0;  // cell capacity of the device arrays of a GPU-built tree
   cudaGraphExec_t gexec = nullptr;  // captured memset + kernel (octgrav_graph_capture)
   std::vector<SysTree> sys_scratch;
 };
@@ -616,6 +630,8 @@ void make_items(octgrav_tree* t) {
       t->item_key.push_back(t->key[c]);
     }
   }
+  t->n_groups = static_cast<int64_t>(t->group_cell.size());
+  t->n_items = static_cast<int64_t>(t->items.size());
 }
 
 // Concatenate the systems' trees into the device-array images.
@@ -785,11 +801,14 @@ int upload(octgrav_tree* t, cudaStream_t st) {
   }
   D.device = dev;
   int rc;
-  if ((rc = upload_vec(D.parts, t->parts, st)) || (rc = upload_vec(D.geo, t->geo, st)) ||
-      (rc = upload_vec(D.link, t->link, st)) || (rc = upload_vec(D.mp, t->mp, st)) ||
-      (rc = upload_vec(D.items, t->items, st)) || (rc = upload_vec(D.ibox, t->ibox, st)))
-    return rc;
-  if ((rc = D.counts.reserve(t->items.size() * sizeof(int2)))) return rc;
+  if (!t->gpu) {  // a GPU-built tree already lives in these arrays
+    if ((rc = upload_vec(D.parts, t->parts, st)) || (rc = upload_vec(D.geo, t->geo, st)) ||
+        (rc = upload_vec(D.link, t->link, st)) || (rc = upload_vec(D.mp, t->mp, st)) ||
+        (rc = upload_vec(D.items, t->items, st)) || (rc = upload_vec(D.ibox, t->ibox, st)))
+      return rc;
+    t->perm_on_device = false;
+  }
+  if ((rc = D.counts.reserve(t->n_items * sizeof(int2)))) return rc;
   if ((rc = D.ctl.reserve(64))) return rc;
   {
     cudaError_t e = og::encode_mp_map(&t->mp_map, D.mp.p, static_cast<int>(t->n_cells));
@@ -824,7 +843,7 @@ og::KParams make_params(octgrav_tree* t, float4* out) {
   p.counts = static_cast<int2*>(D.counts.p);
   p.status = static_cast<int*>(D.ctl.p);
   p.work = reinterpret_cast<unsigned*>(static_cast<char*>(D.ctl.p) + 4);
-  p.n_items = static_cast<int>(t->items.size());
+  p.n_items = static_cast<int>(t->n_items);
   p.n_cells = static_cast<int>(t->n_cells);
   p.stage = t->stage;
   p.mp_map = t->mp_map;
@@ -876,11 +895,50 @@ int read_status(octgrav_tree* t, cudaStream_t st) {
   return OCTGRAV_OK;
 }
 
+// The permutation on the device (int32); uploaded once for a host-built tree.
+int device_perm(octgrav_tree* t, cudaStream_t st) {
+  if (t->gpu || t->perm_on_device) return OCTGRAV_OK;
+  std::vector<int32_t> p32(t->n);
+  for (int64_t k = 0; k < t->n; ++k) p32[k] = static_cast<int32_t>(t->perm[k]);
+  int rc = t->dev->perm.reserve(4 * t->n);
+  if (rc) return rc;
+  CUDA_TRY(cudaMemcpyAsync(t->dev->perm.p, p32.data(), 4 * t->n, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  t->perm_on_device = true;
+  return OCTGRAV_OK;
+}
+
+// Forces into device FP64 arrays in input order (enqueued, not waited for).
+int forces_dev64(octgrav_tree* t, double eps, double theta, double G, double* acc, double* pot, cudaStream_t st) {
+  int rc = check_params(eps, theta, G);
+  if (rc) return rc;
+  if (!t->uploaded || t->sysp_dirty) {
+    if ((rc = upload(t, st))) return rc;
+  }
+  if ((rc = t->dev->out.reserve(sizeof(float4) * t->n))) return rc;
+  if ((rc = device_perm(t, st))) return rc;
+  if ((rc = launch(t, eps, theta, G, static_cast<float4*>(t->dev->out.p), st, false, nullptr, nullptr, nullptr, 0)))
+    return rc;
+  cudaError_t e = og::gpu_unpermute(static_cast<const float4*>(t->dev->out.p), static_cast<const int*>(t->dev->perm.p),
+                                    t->n, acc, pot, st);
+  if (e != cudaSuccess) return fail(OCTGRAV_ERR_CUDA, "unpermute launch failed: %s", cudaGetErrorString(e));
+  return OCTGRAV_OK;
+}
+
 int forces_host(octgrav_tree* t, double eps, double theta, double G, double* acc, double* pot,
                 cudaStream_t st) {
   if (!acc) return fail(OCTGRAV_ERR_ARG, "acc is NULL");
   int rc = check_params(eps, theta, G);
   if (rc) return rc;
+  if (t->gpu) {  // unpermute on the device, copy FP64 results straight into the caller's arrays
+    Device& D = *t->dev;
+    if ((rc = D.acc64.reserve(24 * t->n)) || (rc = D.pot64.reserve(8 * t->n))) return rc;
+    if ((rc = forces_dev64(t, eps, theta, G, static_cast<double*>(D.acc64.p), static_cast<double*>(D.pot64.p), st)))
+      return rc;
+    CUDA_TRY(cudaMemcpyAsync(acc, D.acc64.p, 24 * t->n, cudaMemcpyDeviceToHost, st));
+    if (pot) CUDA_TRY(cudaMemcpyAsync(pot, D.pot64.p, 8 * t->n, cudaMemcpyDeviceToHost, st));
+    return read_status(t, st);
+  }
   if (!t->uploaded || t->sysp_dirty) {
     if ((rc = upload(t, st))) return rc;
   }
@@ -903,6 +961,194 @@ int forces_host(octgrav_tree* t, double eps, double theta, double G, double* acc
 }
 
 thread_local Device* tl_cache = nullptr;
+
+// ---------------------------------------------------------------- GPU build
+
+og::GpuBuild gpu_args(octgrav_tree* t, const int64_t* offsets, const double* pos, const double* mass) {
+  Device& D = *t->dev;
+  const int64_t n = t->n, cap = t->cell_cap;
+  og::GpuBuild a{};
+  a.pos = pos;
+  a.mass = mass;
+  a.n = n;
+  a.n_sys = t->n_sys;
+  a.offsets = offsets;
+  a.n_leaf = t->n_leaf;
+  a.n_group = t->n_group;
+  a.item_max = 32 * t->ppl;
+  a.cap = cap;
+  a.scratch = D.scratch.p;
+  a.scratch_bytes = D.scratch.cap;
+  a.parts = static_cast<float4*>(D.parts.p);
+  a.perm = static_cast<int*>(D.perm.p);
+  a.key = static_cast<uint64_t*>(D.key.p);
+  a.geo = static_cast<float4*>(D.geo.p);
+  a.link = static_cast<int2*>(D.link.p);
+  a.mp = static_cast<float4*>(D.mp.p);
+  double* pr = static_cast<double*>(D.props.p);  // bmin 3 | bmax 3 | cube 4 | M 1 | com 3 | S 6 (x cap)
+  a.bmin = pr;
+  a.bmax = pr + 3 * cap;
+  a.cube = pr + 6 * cap;
+  a.M = pr + 10 * cap;
+  a.com = pr + 11 * cap;
+  a.S = pr + 14 * cap;
+  a.pcount = static_cast<int*>(D.pcount.p);
+  a.cfirst = static_cast<int*>(D.cfirst.p);
+  int* gb = static_cast<int*>(D.groups.p);  // group cell | group system | first item (x n)
+  a.group_cell = gb;
+  a.group_sys = gb + n;
+  a.group_item = gb + 2 * n;
+  a.items = static_cast<int4*>(D.items.p);
+  a.ibox = static_cast<float4*>(D.ibox.p);
+  a.item_key = static_cast<uint64_t*>(D.ikey.p);
+  a.cell_off = static_cast<int64_t*>(D.celloff.p);
+  a.result = static_cast<int64_t*>(D.result.p);
+  return a;
+}
+
+int reserve_gpu_tree(Device& D, int64_t n, int n_sys, int64_t cap) {
+  int rc;
+  if ((rc = D.parts.reserve(32 * n)) || (rc = D.perm.reserve(4 * n)) || (rc = D.key.reserve(8 * cap)) ||
+      (rc = D.geo.reserve(16 * cap)) || (rc = D.link.reserve(8 * cap)) || (rc = D.mp.reserve(64 * cap)) ||
+      (rc = D.props.reserve(160 * cap)) || (rc = D.pcount.reserve(4 * cap)) || (rc = D.cfirst.reserve(4 * cap)) ||
+      (rc = D.groups.reserve(12 * n)) || (rc = D.items.reserve(16 * n)) || (rc = D.ibox.reserve(64 * n)) ||
+      (rc = D.ikey.reserve(8 * n)) || (rc = D.celloff.reserve(8 * (n_sys + 1))) ||
+      (rc = D.result.reserve(8 * og::GB_COUNT)) || (rc = D.scratch.reserve(og::gpu_build_scratch_bytes(n, n_sys, cap))))
+    return rc;
+  return OCTGRAV_OK;
+}
+
+// Read the result block of a GPU build (waits for the stream).
+int gpu_result(octgrav_tree* t, cudaStream_t st, int64_t* res) {
+  CUDA_TRY(cudaMemcpyAsync(res, t->dev->result.p, 8 * og::GB_COUNT, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return OCTGRAV_OK;
+}
+
+int build_gpu_common(int n_sys, const int64_t* offsets, const double* pos, const double* mass, int n_leaf,
+                     int n_group, cudaStream_t st, Device* dev, octgrav_tree** out) {
+  if (!out) return fail(OCTGRAV_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!pos || !mass || !offsets || n_sys < 1) return fail(OCTGRAV_ERR_ARG, "NULL input or n_sys < 1");
+  if (n_leaf < 1 || n_group < n_leaf) return fail(OCTGRAV_ERR_ARG, "need 1 <= n_leaf <= n_group");
+  if (offsets[0] != 0) return fail(OCTGRAV_ERR_ARG, "offsets[0] must be 0");
+  for (int s = 0; s < n_sys; ++s)
+    if (offsets[s + 1] <= offsets[s]) return fail(OCTGRAV_ERR_ARG, "empty or decreasing system %d", s);
+  const int64_t n = offsets[n_sys];
+  if (n >= (1ll << 31) - 64) return fail(OCTGRAV_ERR_ARG, "too many particles");
+  std::unique_ptr<octgrav_tree> t;
+  try {
+    t.reset(new octgrav_tree());
+    t->sys_off.assign(offsets, offsets + n_sys + 1);
+  } catch (const std::bad_alloc&) {
+    return fail(OCTGRAV_ERR_OOM, "host allocation failed");
+  }
+  t->n = n;
+  t->n_leaf = n_leaf;
+  t->n_group = n_group;
+  t->n_sys = n_sys;
+  t->gpu = true;
+  t->host_valid = false;
+  if (dev) t->dev = dev;
+  Device& D = *t->dev;
+  int cur = 0;
+  CUDA_TRY(cudaGetDevice(&cur));
+  if (D.device >= 0 && D.device != cur) D.release();
+  D.device = cur;
+  // every level holds at most n cells (they are disjoint and non-empty)
+  const int64_t bound = std::min<int64_t>(22 * n + n_sys, (1ll << 28) - 1);
+  int64_t cap = D.cell_cap > 0 ? D.cell_cap : 8 * n / (n_leaf + 1) + 64 * static_cast<int64_t>(n_sys) + 1024;
+  if (const char* e = getenv("OCTGRAV_GPU_CELL_CAP")) {
+    const long long v = atoll(e);
+    if (v > 0) cap = v;
+  }
+  cap = std::min(std::max<int64_t>(cap, n_sys + 8), bound);  // the roots always fit
+  int64_t res[og::GB_COUNT];
+  int rc;
+  for (;;) {
+    if ((rc = reserve_gpu_tree(D, n, n_sys, cap))) return rc;
+    t->cell_cap = cap;
+    const og::GpuBuild a = gpu_args(t.get(), offsets, pos, mass);
+    cudaError_t e = og::gpu_build(a, st);
+    if (e != cudaSuccess) return fail(OCTGRAV_ERR_CUDA, "GPU build launch failed: %s", cudaGetErrorString(e));
+    if ((rc = gpu_result(t.get(), st, res))) return rc;
+    if (res[og::GB_STATUS] & og::GPU_BUILD_BADINPUT)
+      return fail(OCTGRAV_ERR_NONFINITE, "non-finite position/mass or negative mass");
+    if (!(res[og::GB_STATUS] & og::GPU_BUILD_OVERFLOW)) break;
+    if (cap >= bound) return fail(OCTGRAV_ERR_ARG, "tree too large (more than %lld cells)", (long long)bound);
+    cap = std::min(bound, 4 * cap);
+  }
+  D.cell_cap = cap;
+  t->n_cells = res[og::GB_NCELLS];
+  t->n_groups = res[og::GB_NGROUPS];
+  t->n_items = res[og::GB_NITEMS];
+  t->depth_reached = static_cast<int>(res[og::GB_DEPTH]);
+  t->n_leaves = res[og::GB_NLEAVES];
+  t->max_group = res[og::GB_MAXGROUP];
+  t->cell_off.resize(n_sys + 1);
+  CUDA_TRY(cudaMemcpy(t->cell_off.data(), D.celloff.p, 8 * (n_sys + 1), cudaMemcpyDeviceToHost));
+  if ((rc = upload(t.get(), st))) return rc;  // counts, control word, tensor map
+  *out = t.release();
+  return OCTGRAV_OK;
+}
+
+// Fill the host images of a GPU-built tree (introspection and host-side paths).
+int host_images(octgrav_tree* t) {
+  if (!t->gpu || t->host_valid) return OCTGRAV_OK;
+  Device& D = *t->dev;
+  const int64_t n = t->n, nc = t->n_cells, ng = t->n_groups, ni = t->n_items, cap = t->cell_cap;
+  std::vector<int32_t> p32, c32, g32;
+  try {
+    t->parts.resize(2 * n);
+    t->geo.resize(nc);
+    t->link.resize(nc);
+    t->mp.resize(4 * nc);
+    t->items.resize(ni);
+    t->ibox.resize(4 * ni);
+    t->item_key.resize(ni);
+    t->key.resize(nc);
+    t->perm.resize(n);
+    t->bmin.resize(3 * nc);
+    t->bmax.resize(3 * nc);
+    t->cube.resize(4 * nc);
+    t->M.resize(nc);
+    t->com.resize(3 * nc);
+    t->S.resize(6 * nc);
+    t->pcount.resize(nc);
+    t->cfirst.resize(nc);
+    t->group_cell.resize(ng);
+    t->group_sys.resize(ng);
+    t->group_item.resize(ng);
+    p32.resize(n);
+    c32.resize(nc);
+  } catch (const std::bad_alloc&) {
+    return fail(OCTGRAV_ERR_OOM, "host allocation failed");
+  }
+  const double* pr = static_cast<const double*>(D.props.p);
+  const int* gb = static_cast<const int*>(D.groups.p);
+  struct Copy {
+    void* dst;
+    const void* src;
+    size_t bytes;
+  } copies[] = {
+      {t->parts.data(), D.parts.p, 32 * n},         {t->geo.data(), D.geo.p, 16 * nc},
+      {t->link.data(), D.link.p, 8 * nc},           {t->mp.data(), D.mp.p, 64 * nc},
+      {t->items.data(), D.items.p, 16 * ni},        {t->ibox.data(), D.ibox.p, 64 * ni},
+      {t->item_key.data(), D.ikey.p, 8 * ni},       {t->key.data(), D.key.p, 8 * nc},
+      {p32.data(), D.perm.p, 4 * n},                {t->bmin.data(), pr, 24 * nc},
+      {t->bmax.data(), pr + 3 * cap, 24 * nc},      {t->cube.data(), pr + 6 * cap, 32 * nc},
+      {t->M.data(), pr + 10 * cap, 8 * nc},         {t->com.data(), pr + 11 * cap, 24 * nc},
+      {t->S.data(), pr + 14 * cap, 48 * nc},        {c32.data(), D.pcount.p, 4 * nc},
+      {t->cfirst.data(), D.cfirst.p, 4 * nc},       {t->group_cell.data(), gb, 4 * ng},
+      {t->group_sys.data(), gb + n, 4 * ng},        {t->group_item.data(), gb + 2 * n, 4 * ng},
+  };
+  for (const Copy& c : copies)
+    if (c.bytes) CUDA_TRY(cudaMemcpy(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost));
+  for (int64_t k = 0; k < n; ++k) t->perm[k] = p32[k];
+  for (int64_t c = 0; c < nc; ++c) t->pcount[c] = c32[c];
+  t->host_valid = true;
+  return OCTGRAV_OK;
+}
 
 }  // namespace
 
@@ -981,6 +1227,51 @@ int octgrav_forces(const double* pos, const double* mass, int64_t n, double eps,
   return octgrav_forces_ex(pos, mass, n, eps, theta, 1.0, n_leaf, n_leaf, acc, pot, nullptr);
 }
 
+int octgrav_build_tree_gpu(const double* pos_dev, const double* mass_dev, int64_t n, int n_leaf, int n_group,
+                           void* stream, octgrav_tree** out) {
+  if (n < 1) return fail(OCTGRAV_ERR_ARG, "n must be >= 1");
+  const int64_t off[2] = {0, n};
+  return build_gpu_common(1, off, pos_dev, mass_dev, n_leaf, n_group, static_cast<cudaStream_t>(stream), nullptr, out);
+}
+
+int octgrav_build_batch_gpu(int n_sys, const int64_t* offsets, const double* pos_dev, const double* mass_dev,
+                            int n_leaf, int n_group, void* stream, octgrav_tree** out) {
+  return build_gpu_common(n_sys, offsets, pos_dev, mass_dev, n_leaf, n_group, static_cast<cudaStream_t>(stream),
+                          nullptr, out);
+}
+
+int octgrav_forces_tree_device64(octgrav_tree* t, double eps, double theta, double G, double* acc_dev,
+                                 double* pot_dev, void* stream) {
+  if (!t || !acc_dev) return fail(OCTGRAV_ERR_ARG, "NULL tree or output");
+  return forces_dev64(t, eps, theta, G, acc_dev, pot_dev, static_cast<cudaStream_t>(stream));
+}
+
+int octgrav_forces_gpu(const double* pos, const double* mass, int64_t n, double eps, double theta, double G,
+                       int n_leaf, int n_group, double* acc, double* pot, void* stream) {
+  if (!pos || !mass || !acc) return fail(OCTGRAV_ERR_ARG, "NULL input or output");
+  if (n < 1) return fail(OCTGRAV_ERR_ARG, "n must be >= 1");
+  int rc = check_params(eps, theta, G);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!tl_cache) tl_cache = new Device();
+  Device& D = *tl_cache;
+  int cur = 0;
+  CUDA_TRY(cudaGetDevice(&cur));
+  if (D.device >= 0 && D.device != cur) D.release();
+  D.device = cur;
+  if ((rc = D.in_pos.reserve(24 * n)) || (rc = D.in_mass.reserve(8 * n))) return rc;
+  CUDA_TRY(cudaMemcpyAsync(D.in_pos.p, pos, 24 * n, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(D.in_mass.p, mass, 8 * n, cudaMemcpyHostToDevice, st));
+  const int64_t off[2] = {0, n};
+  octgrav_tree* t = nullptr;
+  if ((rc = build_gpu_common(1, off, static_cast<const double*>(D.in_pos.p), static_cast<const double*>(D.in_mass.p),
+                             n_leaf, n_group, st, &D, &t)))
+    return rc;
+  rc = forces_host(t, eps, theta, G, acc, pot, st);
+  octgrav_free_tree(t);
+  return rc;
+}
+
 int octgrav_status(octgrav_tree* t, void* stream) {
   if (!t) return fail(OCTGRAV_ERR_ARG, "tree is NULL");
   if (!t->launched) return fail(OCTGRAV_ERR_STATE, "no launch on this tree yet");
@@ -989,20 +1280,22 @@ int octgrav_status(octgrav_tree* t, void* stream) {
 
 int octgrav_tree_stats(const octgrav_tree* t, int64_t* out, int n_out) {
   if (!t || !out) return fail(OCTGRAV_ERR_ARG, "NULL argument");
-  const int64_t v[8] = {t->n, t->n_cells, t->n_leaves, static_cast<int64_t>(t->group_cell.size()),
-                        static_cast<int64_t>(t->items.size()), t->depth_reached, t->n_sys, t->max_group};
+  const int64_t v[8] = {t->n, t->n_cells, t->n_leaves, t->n_groups, t->n_items, t->depth_reached, t->n_sys,
+                        t->max_group};
   for (int k = 0; k < n_out && k < 8; ++k) out[k] = v[k];
   return OCTGRAV_OK;
 }
 
 int octgrav_tree_perm(const octgrav_tree* t, int64_t* perm) {
   if (!t || !perm) return fail(OCTGRAV_ERR_ARG, "NULL argument");
+  if (int rc = host_images(const_cast<octgrav_tree*>(t))) return rc;
   std::memcpy(perm, t->perm.data(), sizeof(int64_t) * t->n);
   return OCTGRAV_OK;
 }
 
 int octgrav_tree_cell_keys(const octgrav_tree* t, uint64_t* keys) {
   if (!t || !keys) return fail(OCTGRAV_ERR_ARG, "NULL argument");
+  if (int rc = host_images(const_cast<octgrav_tree*>(t))) return rc;
   std::memcpy(keys, t->key.data(), sizeof(uint64_t) * t->n_cells);
   return OCTGRAV_OK;
 }
@@ -1010,6 +1303,7 @@ int octgrav_tree_cell_keys(const octgrav_tree* t, uint64_t* keys) {
 int octgrav_tree_cell_props(const octgrav_tree* t, double* bmin, double* bmax, double* cube, double* mass,
                             double* com, double* S, int64_t* count) {
   if (!t) return fail(OCTGRAV_ERR_ARG, "NULL argument");
+  if (int rc = host_images(const_cast<octgrav_tree*>(t))) return rc;
   const size_t nc = static_cast<size_t>(t->n_cells);
   if (bmin) std::memcpy(bmin, t->bmin.data(), 24 * nc);
   if (bmax) std::memcpy(bmax, t->bmax.data(), 24 * nc);
@@ -1023,6 +1317,7 @@ int octgrav_tree_cell_props(const octgrav_tree* t, double* bmin, double* bmax, d
 
 int octgrav_item_info(const octgrav_tree* t, uint64_t* group_key, int64_t* first, int32_t* count, int32_t* sys) {
   if (!t) return fail(OCTGRAV_ERR_ARG, "tree is NULL");
+  if (int rc = host_images(const_cast<octgrav_tree*>(t))) return rc;
   for (size_t k = 0; k < t->items.size(); ++k) {
     if (group_key) group_key[k] = t->item_key[k];
     if (first) first[k] = t->items[k].y;
@@ -1035,6 +1330,7 @@ int octgrav_item_info(const octgrav_tree* t, uint64_t* group_key, int64_t* first
 int octgrav_interaction_counts(octgrav_tree* t, int64_t* out, void* stream) {
   if (!t || !out) return fail(OCTGRAV_ERR_ARG, "NULL argument");
   if (!t->launched) return fail(OCTGRAV_ERR_STATE, "no launch on this tree yet");
+  if (int rc = host_images(t)) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   std::vector<int2> c(t->items.size());
   if (!c.empty())
@@ -1057,6 +1353,7 @@ int octgrav_debug_lists(octgrav_tree* t, double theta, int cap, uint64_t* cell_k
   if (!t || cap < 1 || !cell_keys || !n_cell || !leaf_keys || !n_leaf) return fail(OCTGRAV_ERR_ARG, "bad argument");
   int rc = check_params(1.0, theta, 1.0);
   if (rc) return rc;
+  if ((rc = host_images(t))) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t ni = t->items.size();
   if (!t->uploaded || t->sysp_dirty) {
@@ -1095,8 +1392,19 @@ int octgrav_set_launch(octgrav_tree* t, int particles_per_lane, int ctas_per_sm)
   t->ctas_per_sm = ctas_per_sm;
   if (particles_per_lane != t->ppl) {
     t->ppl = particles_per_lane;
-    make_items(t);
-    t->uploaded = false;
+    if (t->gpu) {  // rebuild the work items on the device
+      const og::GpuBuild a = gpu_args(t, t->sys_off.data(), nullptr, nullptr);
+      cudaError_t e = og::gpu_build_items(a, nullptr);
+      if (e != cudaSuccess) return fail(OCTGRAV_ERR_CUDA, "GPU item build failed: %s", cudaGetErrorString(e));
+      int64_t res[og::GB_COUNT];
+      if (int rc = gpu_result(t, nullptr, res)) return rc;
+      t->n_items = res[og::GB_NITEMS];
+      t->host_valid = false;
+      if (int rc = t->dev->counts.reserve(t->n_items * sizeof(int2))) return rc;
+    } else {
+      make_items(t);
+      t->uploaded = false;
+    }
   }
   return OCTGRAV_OK;
 }
@@ -1104,6 +1412,7 @@ int octgrav_set_launch(octgrav_tree* t, int particles_per_lane, int ctas_per_sm)
 int octgrav_forces_noalloc(octgrav_tree* t, void* arena, size_t* arena_bytes, double eps, double theta,
                            double G, float* acc4_dev, void* stream) {
   if (!t || !arena_bytes) return fail(OCTGRAV_ERR_ARG, "NULL tree or arena_bytes");
+  if (int rc = host_images(t)) return rc;
   // arena layout: the device arrays, each starting on a 256-byte boundary
   const size_t sizes[7] = {t->parts.size() * sizeof(float4), t->geo.size() * sizeof(float4),
                            t->link.size() * sizeof(int2),    t->mp.size() * sizeof(float4),
@@ -1362,6 +1671,7 @@ int octgrav_mlp_samples(octgrav_tree* t, const int64_t* groups, int64_t n_groups
   if (!t || !groups || n_groups < 0 || !n_out) return fail(OCTGRAV_ERR_ARG, "bad argument");
   int rc = check_params(eps, theta_walk, 1.0);
   if (rc) return rc;
+  if ((rc = host_images(t))) return rc;
   const int64_t ngr = static_cast<int64_t>(t->group_cell.size());
   const float th2 = static_cast<float>(theta_walk * theta_walk);
   std::vector<int32_t> s_item, s_cell;

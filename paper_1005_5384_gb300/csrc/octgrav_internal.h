@@ -123,4 +123,59 @@ cudaError_t encode_mp_map(CUtensorMap* map, const void* mp, int n_cells);
 cudaError_t launch_walk_eval_noalloc(KParams p, int ppl, int ctas_per_sm, cudaStream_t stream,
                                      int* status_bits);
 
+// ---- GPU tree build (octgrav_build.cu)
+
+// Status bits of a GPU build (result[GB_STATUS]).
+enum : int {
+  GPU_BUILD_OVERFLOW = 1,  // more cells than the capacity: enlarge and build again
+  GPU_BUILD_BADINPUT = 2,  // non-finite coordinate or mass, or a negative mass
+};
+// Entries of the result block (int64) the build writes at the end.
+enum : int { GB_NCELLS = 0, GB_NGROUPS, GB_NITEMS, GB_DEPTH, GB_NLEAVES, GB_MAXGROUP, GB_STATUS, GB_COUNT };
+
+// Arguments of the GPU build. Inputs: pos (3n) and mass (n) on the device,
+// offsets (n_sys + 1) on the host. Outputs (device, capacity-sized: cells
+// `cap`, particles / groups / items n): the arrays of the walk kernel in the
+// layout of KParams, the FP64 cell properties in final cell order (bmin,
+// bmax 3, cube 4, M 1, com 3, S 6 per cell), per cell the particle count and
+// first particle, per group its cell, system and first work item, per item
+// its group key, per system its root cell (cell_off, n_sys + 1), and the
+// result block.
+struct GpuBuild {
+  const double* pos;
+  const double* mass;
+  int64_t n;
+  int n_sys;
+  const int64_t* offsets;
+  int n_leaf, n_group, item_max;
+  int64_t cap;
+  void* scratch;
+  size_t scratch_bytes;
+  float4* parts;
+  int* perm;
+  uint64_t* key;
+  float4* geo;
+  int2* link;
+  float4* mp;
+  double *bmin, *bmax, *cube, *M, *com, *S;
+  int *pcount, *cfirst;
+  int *group_cell, *group_sys, *group_item;
+  int4* items;
+  float4* ibox;
+  uint64_t* item_key;
+  int64_t* cell_off;
+  int64_t* result;
+};
+
+// Scratch bytes of a build of n particles in n_sys systems with `cap` cells.
+size_t gpu_build_scratch_bytes(int64_t n, int n_sys, int64_t cap);
+// Enqueue the whole build on `stream` (no host synchronisation inside).
+cudaError_t gpu_build(const GpuBuild& a, cudaStream_t stream);
+// Rebuild the work items (another item_max) of a tree built by gpu_build with
+// the same arguments and scratch.
+cudaError_t gpu_build_items(const GpuBuild& a, cudaStream_t stream);
+// acc[3 perm[t] + k] = out[t].xyz, pot[perm[t]] = out[t].w (pot may be NULL).
+cudaError_t gpu_unpermute(const float4* out, const int* perm, int64_t n, double* acc, double* pot,
+                          cudaStream_t stream);
+
 }  // namespace og

@@ -1,7 +1,8 @@
 """Thin ctypes binding of liboctgrav.so (the C ABI in include/octgrav.h).
 
 Argument marshalling only: every step of the force calculation runs inside the
-library (host FP64 octree build, sm_103a walk + evaluation kernel). There is no
+library (FP64 octree build on the host or on the GPU, sm_103a walk + evaluation
+kernel). There is no
 Python or CPU fallback: if the library cannot be built or loaded, the calls
 raise.
 
@@ -45,6 +46,11 @@ _SIGS = {
     "octgrav_forces": (C.c_int, [_f64, _f64, C.c_int64, C.c_double, C.c_double, C.c_int, _vp, _vp]),
     "octgrav_forces_ex": (C.c_int, [_f64, _f64, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_int,
                                     C.c_int, _vp, _vp, _vp]),
+    "octgrav_build_tree_gpu": (C.c_int, [_vp, _vp, C.c_int64, C.c_int, C.c_int, _vp, C.POINTER(_vp)]),
+    "octgrav_build_batch_gpu": (C.c_int, [C.c_int, _i64, _vp, _vp, C.c_int, C.c_int, _vp, C.POINTER(_vp)]),
+    "octgrav_forces_tree_device64": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double, _vp, _vp, _vp]),
+    "octgrav_forces_gpu": (C.c_int, [_vp, _vp, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int,
+                                     _vp, _vp, _vp]),
     "octgrav_status": (C.c_int, [_vp, _vp]),
     "octgrav_tree_stats": (C.c_int, [_vp, _i64, C.c_int]),
     "octgrav_tree_perm": (C.c_int, [_vp, _i64]),
@@ -160,6 +166,40 @@ class Tree:
         t.offsets = off
         return t
 
+    @classmethod
+    def build_gpu(cls, pos, mass, n_leaf: int = 16, n_group: int | None = None, offsets=None,
+                  stream=None) -> "Tree":
+        """The same tree as build / build_batch, built on the GPU. pos [n,3] and
+        mass [n] are float64 CUDA tensors or host arrays (copied to the device);
+        offsets (host, n_sys + 1) makes it a batch of concatenated systems."""
+        import torch
+        lib = load()
+
+        def dev(a, shape):
+            if isinstance(a, torch.Tensor):
+                a = a.to(device="cuda", dtype=torch.float64).contiguous()
+            else:
+                a = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+            return a.reshape(shape)
+        m = dev(mass, (-1,))
+        x = dev(pos, (-1, 3))
+        n = m.shape[0]
+        if x.shape[0] != n:
+            raise ValueError("pos must have shape [n, 3] matching mass [n]")
+        h = C.c_void_p()
+        ng = int(n_group if n_group is not None else n_leaf)
+        st = _stream_handle(stream)
+        if offsets is None:
+            _check(lib.octgrav_build_tree_gpu(C.c_void_p(x.data_ptr()), C.c_void_p(m.data_ptr()), n, int(n_leaf), ng,
+                                              st, C.byref(h)))
+            return cls(h.value, n)
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        _check(lib.octgrav_build_batch_gpu(len(off) - 1, off, C.c_void_p(x.data_ptr()), C.c_void_p(m.data_ptr()),
+                                           int(n_leaf), ng, st, C.byref(h)))
+        t = cls(h.value, n)
+        t.offsets = off
+        return t
+
     def __del__(self):
         h = getattr(self, "_h", None)
         if h is not None and h.value and _lib is not None:
@@ -236,6 +276,14 @@ class Tree:
         _check(load().octgrav_forces_tree(self._h, float(eps), float(theta), float(G), _p(acc), _p(pot),
                                           _stream_handle(stream)))
         return acc, pot
+
+    def forces_device64(self, eps: float, theta: float, acc, pot=None, G: float = 1.0, stream=None):
+        """Input-order FP64 results on the device: acc a CUDA float64 tensor [n,3],
+        pot [n] or None. Enqueued only; check status()."""
+        _check(load().octgrav_forces_tree_device64(self._h, float(eps), float(theta), float(G),
+                                                   C.c_void_p(acc.data_ptr()),
+                                                   None if pot is None else C.c_void_p(pot.data_ptr()),
+                                                   _stream_handle(stream)))
 
     def noalloc_arena_bytes(self) -> int:
         """Device bytes the caller must provide to forces_noalloc for this tree."""
@@ -321,6 +369,29 @@ def forces(pos, mass, eps: float, theta: float, n_leaf: int = 16, n_group: int |
     _check(lib.octgrav_forces_ex(pos, mass, n, float(eps), float(theta), float(G), int(n_leaf),
                                  int(n_group if n_group is not None else n_leaf), _p(acc), _p(pot),
                                  _stream_handle(stream)))
+    return acc, pot
+
+
+def forces_gpu(pos, mass, eps: float, theta: float, n_leaf: int = 16, n_group: int | None = None, G: float = 1.0,
+               stream=None, out=None):
+    """One-shot C-ABI call with host buffers and the tree built on the GPU:
+    (acc [n,3], pot [n]) in input order. ``out`` = (acc, pot) host float64
+    arrays to fill (e.g. views of pinned memory); pos / mass should be pinned
+    too for link-speed copies."""
+    lib = load()
+    pos, mass = _pm(pos, mass)
+    n = mass.shape[0]
+    if out is None:
+        acc, pot = np.zeros((n, 3)), np.zeros(n)
+    else:
+        acc, pot = out
+        if acc.dtype != np.float64 or not acc.flags.c_contiguous or acc.size != 3 * n:
+            raise ValueError("acc must be a C-contiguous float64 array of n x 3")
+        if pot is not None and (pot.dtype != np.float64 or not pot.flags.c_contiguous or pot.size != n):
+            raise ValueError("pot must be a C-contiguous float64 array of n")
+    _check(lib.octgrav_forces_gpu(_p(pos), _p(mass), n, float(eps), float(theta), float(G), int(n_leaf),
+                                  int(n_group if n_group is not None else n_leaf), _p(acc), _p(pot),
+                                  _stream_handle(stream)))
     return acc, pot
 
 

@@ -1,0 +1,187 @@
+"""The octree built on the GPU against the host FP64 build and the oracle.
+
+The GPU build runs the same steps as the host build (Sec. 2.1: root cube,
+Morton keys, stable sort, level-by-level split, bottom-up moments, groups,
+work items) with the same FP64 operations in the same order, so every array
+must come out identical bit for bit; the forces of the two trees must then be
+identical too (the walk kernel is deterministic per particle). The GPU-built
+tree is also checked against the oracle directly, and on the edge cases of the
+build: one particle, coincident particles (depth limit), tiny and multi-chunk
+systems in a batch, a cell capacity that has to grow, invalid inputs.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1005_5384_gb300 import octgrav as G
+from paper_1005_5384_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    G.load()
+    return t
+
+
+def _bits(a):
+    a = np.ascontiguousarray(a)
+    return a.view(np.uint8)
+
+
+def _assert_same_tree(A, B):
+    assert A.stats == B.stats
+    assert np.array_equal(A.perm(), B.perm())
+    assert np.array_equal(A.cell_keys(), B.cell_keys())
+    pa, pb = A.cell_props(), B.cell_props()
+    for k in pa:
+        assert np.array_equal(_bits(pa[k]), _bits(pb[k])), k
+    ia, ib = A.item_info(), B.item_info()
+    for k in ia:
+        assert np.array_equal(ia[k], ib[k]), k
+
+
+def _device_forces(torch, T, eps, theta):
+    out = torch.empty((T.n, 4), dtype=torch.float32, device="cuda")
+    T.forces_device(eps, theta, out)
+    torch.cuda.synchronize()
+    assert T.status() == G.OK
+    return out.cpu().numpy()
+
+
+def _coincident(n):
+    return np.tile([[0.25, -0.5, 0.125]], (n, 1)), np.full(n, 1.0 / n)
+
+
+CASES = {
+    "plummer_16k": (lambda: W.plummer(16384, seed=1), 16, 16, 0.01),
+    "plummer_100k_ng64": (lambda: W.plummer(100000, seed=2), 16, 64, 0.01),
+    "plummer_262k_ng256": (lambda: W.plummer(262144, seed=3), 16, 256, 0.01),
+    "clustered_200k": (lambda: W.clustered(200000, 16, seed=4), 16, 64, 0.001),
+    "sphere_disc_131k": (lambda: W.sphere_disc(131072, seed=5), 16, 64, 0.01),
+    "uniform_nleaf1": (lambda: W.uniform_cube(50000, seed=6), 1, 8, 0.01),
+    "one_particle": (lambda: (np.array([[0.3, 0.2, 0.1]]), np.array([1.0])), 1, 1, 0.01),
+    "two_coincident": (lambda: _coincident(2), 1, 1, 0.01),
+    "coincident_100": (lambda: _coincident(100), 4, 8, 0.01),
+    "ragged_37": (lambda: W.plummer(37, seed=7), 4, 8, 0.01),
+    "chunk_edges_8193": (lambda: W.plummer(8193, seed=8), 16, 32, 0.01),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_gpu_build_equals_host_build(torch, name):
+    make, n_leaf, n_group, eps = CASES[name]
+    pos, m = make()
+    A = G.Tree.build(pos, m, n_leaf, n_group)
+    B = G.Tree.build_gpu(pos, m, n_leaf, n_group)
+    _assert_same_tree(A, B)
+    fa = _device_forces(torch, A, eps, 0.6)
+    fb = _device_forces(torch, B, eps, 0.6)
+    assert np.array_equal(_bits(fa), _bits(fb))
+
+
+def test_gpu_built_tree_matches_oracle(torch):
+    pos, m = W.plummer(16384, seed=11)
+    T = G.Tree.build_gpu(pos, m, 16, 32)
+    R = O.Tree(pos, m, 16, 32)
+    assert T.stats["n_cells"] == R.n_cells and T.stats["n_groups"] == R.n_groups
+    k = T.cell_keys()
+    assert np.array_equal(np.sort(k), np.sort(R.key))
+    acc, pot = T.forces(0.01, 0.5)
+    ra, rp, _, _, _ = R.forces(0.01, 0.5)
+    assert O.rel_rms(acc, ra) <= 1e-5
+    assert np.linalg.norm(pot - rp) / np.linalg.norm(rp) <= 1e-5
+
+
+def test_batch_gpu_build_equals_host_batch(torch):
+    sizes = (300, 1000, 17, 1, 2 * 4096 + 5, 4096, 2, 65)
+    systems = [W.plummer(n, seed=20 + s) for s, n in enumerate(sizes)]
+    A = G.Tree.build_batch(systems, 8, 32)
+    pos = np.concatenate([p for p, _ in systems])
+    m = np.concatenate([q for _, q in systems])
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    B = G.Tree.build_gpu(pos, m, 8, 32, offsets=off)
+    _assert_same_tree(A, B)
+    fa = _device_forces(torch, A, 0.01, 0.7)
+    fb = _device_forces(torch, B, 0.01, 0.7)
+    assert np.array_equal(_bits(fa), _bits(fb))
+
+
+def test_cell_capacity_grows(torch, monkeypatch):
+    pos, m = W.plummer(60000, seed=12)
+    monkeypatch.setenv("OCTGRAV_GPU_CELL_CAP", "64")
+    B = G.Tree.build_gpu(pos, m, 16, 64)
+    monkeypatch.delenv("OCTGRAV_GPU_CELL_CAP")
+    A = G.Tree.build(pos, m, 16, 64)
+    _assert_same_tree(A, B)
+
+
+@pytest.mark.parametrize("ppl", [1, 2])
+def test_work_items_rebuilt_on_the_device(torch, ppl):
+    pos, m = W.plummer(50000, seed=13)
+    A = G.Tree.build(pos, m, 16, 128)
+    B = G.Tree.build_gpu(pos, m, 16, 128)
+    B.item_info()  # host images made before the change must not go stale
+    A.set_launch(ppl)
+    B.set_launch(ppl)
+    _assert_same_tree(A, B)
+    assert np.array_equal(_bits(_device_forces(torch, A, 0.01, 0.5)), _bits(_device_forces(torch, B, 0.01, 0.5)))
+
+
+def test_one_shot_gpu_call_equals_host_path(torch):
+    pos, m = W.plummer(70000, seed=14)
+    acc, pot = G.forces(pos, m, 0.01, 0.5, 16, 64)
+    pin_x = torch.from_numpy(pos.copy()).pin_memory()
+    pin_m = torch.from_numpy(m.copy()).pin_memory()
+    out_a = torch.zeros((len(m), 3), dtype=torch.float64).pin_memory()
+    out_p = torch.zeros(len(m), dtype=torch.float64).pin_memory()
+    for _ in range(2):  # the second call reuses the cached device buffers
+        a2, p2 = G.forces_gpu(pin_x.numpy(), pin_m.numpy(), 0.01, 0.5, 16, 64, out=(out_a.numpy(), out_p.numpy()))
+        assert np.array_equal(_bits(acc), _bits(a2)) and np.array_equal(_bits(pot), _bits(p2))
+    a3, p3 = G.forces_gpu(pos, m, 0.01, 0.5, 16, 64)  # pageable buffers
+    assert np.array_equal(_bits(acc), _bits(a3)) and np.array_equal(_bits(pot), _bits(p3))
+
+
+def test_device64_outputs_in_input_order(torch):
+    pos, m = W.plummer(30000, seed=15)
+    for T in (G.Tree.build(pos, m, 16, 64), G.Tree.build_gpu(pos, m, 16, 64)):
+        acc, pot = T.forces(0.01, 0.5)
+        da = torch.empty((T.n, 3), dtype=torch.float64, device="cuda")
+        dp = torch.empty(T.n, dtype=torch.float64, device="cuda")
+        T.forces_device64(0.01, 0.5, da, dp)
+        assert T.status() == G.OK
+        assert np.array_equal(da.cpu().numpy(), acc) and np.array_equal(dp.cpu().numpy(), pot)
+
+
+def test_invalid_inputs_are_reported(torch):
+    pos, m = W.plummer(5000, seed=16)
+    bad = pos.copy()
+    bad[1234, 1] = np.nan
+    with pytest.raises(G.OctgravError) as e:
+        G.Tree.build_gpu(bad, m)
+    assert e.value.code == G.ERR_NONFINITE
+    neg = m.copy()
+    neg[17] = -1.0
+    with pytest.raises(G.OctgravError) as e:
+        G.Tree.build_gpu(pos, neg)
+    assert e.value.code == G.ERR_NONFINITE
+    with pytest.raises(G.OctgravError) as e:
+        G.Tree.build_gpu(pos, m, 16, 8)
+    assert e.value.code == G.ERR_ARG
+    with pytest.raises(G.OctgravError) as e:
+        G.Tree.build_gpu(pos, m, 16, 16, offsets=[0, 3000, 3000, 5000])
+    assert e.value.code == G.ERR_ARG
+    # the library still works after the refusals
+    T = G.Tree.build_gpu(pos, m, 16, 16)
+    assert T.stats["n"] == 5000
+
+
+def test_full_size_build_equals_host(torch):
+    pos, m = W.plummer(1 << 20, seed=1)
+    A = G.Tree.build(pos, m, 16, 512)
+    B = G.Tree.build_gpu(pos, m, 16, 512)
+    _assert_same_tree(A, B)
