@@ -26,11 +26,13 @@ constexpr int NLEV = MAXD + 1;    // levels 0..21
 constexpr int TB = 256;           // threads per block
 constexpr int IPT = 16;           // elements per thread in the chunked kernels
 constexpr int TILE = TB * IPT;    // particles per chunk (sort, box, keys)
-constexpr int GL = 1024;          // blocks of the level kernels = threads of their scan
+constexpr int GL = 4096;          // blocks of the level kernels
+constexpr int GLT = 1024;         // threads of the level scan (GL / GLT entries each)
 constexpr unsigned FULL = 0xffffffffu;
+constexpr int LBINS = 32;  // leaf size bins of the moment pass (32 = "32 or more")
 
-struct SysGeo {  // root cube of a system: lower corner and side
-  double lo[3], side;
+struct SysGeo {  // root cube of a system: lower corner, side, 2^21 * fl(1 / side)
+  double lo[3], side, rscale;
 };
 
 struct Chunk {  // TILE particles (or fewer) of one system
@@ -40,9 +42,9 @@ struct Chunk {  // TILE particles (or fewer) of one system
 
 // Scratch layout (byte offsets into one allocation).
 struct Layout {
-  size_t keyA, keyB, valA, valB, cnt, part, sg, xs, ms, chunks, offs, chunk0;
+  size_t keyA, keyB, valA, valB, cnt, dtot, part, sg, xs, ms, chunks, offs, chunk0;
   size_t ckey, cpar, cpf, cpc, csys, cfc, cnc, spl, lpre, bsum, lvl, misc;
-  size_t sstart, send, lofs, ni, gmark, gidx, gcell, nitem, ioff, sblk;
+  size_t sstart, send, lofs, ni, lorder, lhist, gmark, gidx, gcell, nitem, ioff, sblk;
   size_t total;
 };
 
@@ -61,6 +63,7 @@ Layout layout(int64_t n, int n_sys, int64_t n_chunks, int64_t cap) {
   L.valA = take(4 * n);
   L.valB = take(4 * n);
   L.cnt = take(4 * 256 * n_chunks);
+  L.dtot = take(4 * 256 * static_cast<size_t>(n_sys));
   L.part = take(8 * 6 * n_chunks);
   L.sg = take(sizeof(SysGeo) * n_sys);
   L.xs = take(24 * n);
@@ -84,6 +87,8 @@ Layout layout(int64_t n, int n_sys, int64_t n_chunks, int64_t cap) {
   L.send = take(4 * static_cast<size_t>(n_sys) * NLEV);
   L.lofs = take(4 * static_cast<size_t>(n_sys) * NLEV);
   L.ni = take(n_sys > 1 ? 4 * cap : 0);
+  L.lorder = take(4 * cap);
+  L.lhist = take(4 * 2 * LBINS);
   L.gmark = take(4 * n);
   L.gidx = take(4 * n);
   L.gcell = take(4 * n);
@@ -112,10 +117,16 @@ __device__ __forceinline__ uint64_t spread21(uint64_t v) {
   return v;
 }
 
+// Integer key with the order of `<` on non-NaN doubles (the two zeros equal),
+// so that min / max run on the integer pipe (FP64 is slow on this part).
+__device__ __forceinline__ long long order_key(double x) {
+  const long long b = __double_as_longlong(x);
+  return b >= 0 ? b : (b == (-0x7fffffffffffffffLL - 1) ? 0 : b ^ 0x7fffffffffffffffLL);
+}
 // min / max with the tie rule of std::min / std::max (the first argument
 // wins ties, so signed zeros come out as on the host)
-__device__ __forceinline__ double lesser(double a, double b) { return b < a ? b : a; }
-__device__ __forceinline__ double greater(double a, double b) { return a < b ? b : a; }
+__device__ __forceinline__ double lesser(double a, double b) { return order_key(b) < order_key(a) ? b : a; }
+__device__ __forceinline__ double greater(double a, double b) { return order_key(a) < order_key(b) ? b : a; }
 
 __device__ __forceinline__ int octant_at(uint64_t code, int child_depth) {
   return static_cast<int>((code >> (3 * (MAXD - child_depth))) & 7);
@@ -192,16 +203,39 @@ __global__ void __launch_bounds__(TB) k_bbox(const double* __restrict__ pos, con
 }
 
 // Root cube per system (the host build's arithmetic, operation for operation).
-__global__ void k_root(const double* __restrict__ part, const int* __restrict__ chunk0, int n_sys,
-                       SysGeo* __restrict__ sg) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n_sys) return;
+// One block per system.
+__global__ void __launch_bounds__(TB) k_root(const double* __restrict__ part, const int* __restrict__ chunk0,
+                                             SysGeo* __restrict__ sg) {
+  const int s = blockIdx.x;
   double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-  for (int b = chunk0[s]; b < chunk0[s + 1]; ++b)
+  for (int b = chunk0[s] + threadIdx.x; b < chunk0[s + 1]; b += TB)
     for (int d = 0; d < 3; ++d) {
       mn[d] = lesser(mn[d], part[6 * b + d]);
       mx[d] = greater(mx[d], part[6 * b + 3 + d]);
     }
+  __shared__ double red[6][TB / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int d = 0; d < 3; ++d) {
+    for (int o = 16; o; o >>= 1) {
+      mn[d] = lesser(mn[d], __shfl_xor_sync(FULL, mn[d], o));
+      mx[d] = greater(mx[d], __shfl_xor_sync(FULL, mx[d], o));
+    }
+    if (lane == 0) {
+      red[d][w] = mn[d];
+      red[3 + d][w] = mx[d];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x) return;
+  for (int k = 1; k < TB / 32; ++k)
+    for (int d = 0; d < 3; ++d) {
+      red[d][0] = lesser(red[d][0], red[d][k]);
+      red[3 + d][0] = greater(red[3 + d][0], red[3 + d][k]);
+    }
+  for (int d = 0; d < 3; ++d) {
+    mn[d] = red[d][0];
+    mx[d] = red[3 + d][0];
+  }
   double ext = mx[0] - mn[0];
   if (mx[1] - mn[1] > ext) ext = mx[1] - mn[1];
   if (mx[2] - mn[2] > ext) ext = mx[2] - mn[2];
@@ -209,6 +243,7 @@ __global__ void k_root(const double* __restrict__ part, const int* __restrict__ 
   const double side = ext * (1.0 + 1.0 / 1048576.0);
   for (int d = 0; d < 3; ++d) sg[s].lo[d] = (mn[d] + mx[d]) * 0.5 - side * 0.5;
   sg[s].side = side;
+  sg[s].rscale = (1.0 / side) * 2097152.0;
 }
 
 __global__ void __launch_bounds__(TB) k_morton(const double* __restrict__ pos, const Chunk* __restrict__ ch,
@@ -224,8 +259,15 @@ __global__ void __launch_bounds__(TB) k_morton(const double* __restrict__ pos, c
     const int64_t i = c.first + k;
     uint64_t q[3];
     for (int d = 0; d < 3; ++d) {
-      const double u = (pos[3 * i + d] - lo[d]) / side;
-      const double v = floor(u * scale);
+      // The quantised coordinate is floor(fl(fl(x - lo) / side) * 2^21) =
+      // floor(fl(fl(x - lo) * 2^21 / side)). a = fl(x - lo) * g.rscale is
+      // within 4 ulp (< 2^-29 for a <= 2^21) of fl(fl(x - lo) * 2^21 / side),
+      // so whenever no integer lies within 2^-28 of a the floors agree; the
+      // rare remaining cases take the division.
+      const double dx = pos[3 * i + d] - lo[d];
+      const double a = dx * g.rscale;
+      double v = floor(a - 0x1p-28);
+      if (v != floor(a + 0x1p-28)) v = floor((dx / side) * scale);
       q[d] = v <= 0 ? 0 : (v >= static_cast<double>(qmax) ? qmax : static_cast<uint64_t>(v));
     }
     key[i] = spread21(q[0]) | (spread21(q[1]) << 1) | (spread21(q[2]) << 2);
@@ -234,7 +276,7 @@ __global__ void __launch_bounds__(TB) k_morton(const double* __restrict__ pos, c
 }
 
 // Digit histogram of one chunk, stored at (system, digit, chunk within the
-// system) so that one linear exclusive scan gives every destination offset.
+// system): the scan over a (system, digit) row is then contiguous.
 __global__ void __launch_bounds__(TB) k_upsweep(const uint64_t* __restrict__ key, const Chunk* __restrict__ ch,
                                                 int shift, int* __restrict__ cnt) {
   __shared__ int h[256];
@@ -282,19 +324,48 @@ __global__ void __launch_bounds__(1024) k_scan_single(int* __restrict__ a, const
   if (threadIdx.x == 1023 && total) *total = ws[31];
 }
 
+// Per (system, digit): exclusive scan over the system's chunks in place, and
+// the digit's total. One warp per (system, digit).
+__global__ void __launch_bounds__(TB) k_scan_digits(int* __restrict__ cnt, const int* __restrict__ chunk0, int n_sys,
+                                                    int* __restrict__ dtot) {
+  const int seg = static_cast<int>((blockIdx.x * static_cast<int64_t>(TB) + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (seg >= 256 * n_sys) return;
+  const int s = seg >> 8, d = seg & 255;
+  const int cs = chunk0[s], nbs = chunk0[s + 1] - cs;
+  int* a = cnt + 256 * static_cast<int64_t>(cs) + static_cast<int64_t>(d) * nbs;
+  int run = 0;
+  for (int base = 0; base < nbs; base += 32) {
+    const int v = base + lane < nbs ? a[base + lane] : 0;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(FULL, x, o);
+      if (lane >= o) x += y;
+    }
+    if (base + lane < nbs) a[base + lane] = run + x - v;
+    run += __shfl_sync(FULL, x, 31);
+  }
+  if (lane == 0) dtot[seg] = run;
+}
+
 // Stable scatter of one chunk by the digit at `shift`: warp w ranks its 512
 // elements round by round (32 at a time, in order), the warps' counts are
 // combined in warp order, and the chunk's offsets come from the scan.
 __global__ void __launch_bounds__(TB) k_downsweep(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                   uint64_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                   const Chunk* __restrict__ ch, int shift,
-                                                  const int* __restrict__ cnt) {
+                                                  const int* __restrict__ cnt, const int* __restrict__ dtot) {
   __shared__ int wc[TB / 32][257];  // per-warp digit counters (+ one for empty slots)
   __shared__ int goff[256];
   const Chunk c = ch[blockIdx.x];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int k = threadIdx.x; k < (TB / 32) * 257; k += TB) (&wc[0][0])[k] = 0;
-  goff[threadIdx.x] = cnt[256 * c.cs + threadIdx.x * c.nbs + (blockIdx.x - c.cs)];
+  {  // destination of this chunk's first element of each digit
+    int unused;
+    const int dbase = block_scan_excl(dtot[256 * c.sys + threadIdx.x], &unused);
+    goff[threadIdx.x] = ch[c.cs].first + dbase + cnt[256 * c.cs + threadIdx.x * c.nbs + (blockIdx.x - c.cs)];
+  }
   __syncthreads();
   uint64_t kk[IPT];
   uint32_t vv[IPT];
@@ -390,53 +461,100 @@ __device__ __forceinline__ void level_range(const int* lvl, int L, int& lb, int&
   c1 = min(le, c0 + chunk);
 }
 
-// Split points of every cell of level L (the host's partition points), and
-// the block-local exclusive prefix of the children counts.
+// First position p in [a, b) whose child octant at depth D is >= o (b if
+// none); octants ascend inside a cell. The warp probes 32 evenly spaced
+// positions per round (all lanes get the same answer).
+__device__ int warp_partition(const uint64_t* __restrict__ code, int a, int b, int D, int o, int lane) {
+  // invariant: the answer lies in [a, b], and b is the end or a known hit
+  while (b - a > 32) {
+    const int64_t span = b - a;
+    const int p = a + static_cast<int>((lane + 1) * span / 33);
+    const unsigned m = __ballot_sync(FULL, octant_at(code[p], D) >= o);
+    const int k = m ? __ffs(m) - 1 : 32;
+    const int lo = k == 0 ? a : a + static_cast<int>(k * span / 33) + 1;
+    const int hi = k == 32 ? b : a + static_cast<int>((k + 1) * span / 33);
+    a = lo;
+    b = hi;
+  }
+  const int p = a + lane;
+  const unsigned m = __ballot_sync(FULL, p < b && octant_at(code[p], D) >= o);
+  return m ? a + __ffs(m) - 1 : b;
+}
+
+// Split points of a cell holding particles [f, f + cnt): sp[o] = the first
+// position whose child octant at depth D is >= o, sp[0] = f, sp[8] = f + cnt.
+// One warp; a cell of at most 32 particles takes a single round of loads.
+// Every lane returns the same sp.
+__device__ void warp_split(const uint64_t* __restrict__ code, int f, int cnt, int D, int lane, int* sp) {
+  sp[0] = f;
+  sp[8] = f + cnt;
+  if (cnt <= 32) {  // one probe per particle
+    const int oc = lane < cnt ? octant_at(code[f + lane], D) : 8;
+    for (int o = 1; o < 8; ++o) {
+      const unsigned m = __ballot_sync(FULL, oc >= o);
+      sp[o] = m ? f + __ffs(m) - 1 : f + cnt;
+    }
+    return;
+  }
+  for (int o = 1; o < 8; ++o) sp[o] = warp_partition(code, sp[o - 1], f + cnt, D, o, lane);
+}
+
+// Split points of every cell of level L (the host's partition points; one
+// warp per cell), and the block-local exclusive prefix of the children counts.
 __global__ void __launch_bounds__(TB) k_split(int L, const uint64_t* __restrict__ code, Cells C, int n_leaf,
                                               const int* __restrict__ lvl, int* __restrict__ spl,
                                               int* __restrict__ lpre, int* __restrict__ bsum) {
+  constexpr int W = TB / 32;
+  __shared__ int sn[W];
+  __shared__ int carry;
   int lb, le, c0, c1;
   level_range(lvl, L, lb, le, c0, c1);
-  int carry = 0;
-  for (int base = c0; base < c1; base += TB) {
-    const int c = base + threadIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  for (int base = c0; base < c1; base += W) {
+    const int c = base + w;
     int nch = 0;
-    if (c < c1) {
+    if (c < c1) {  // warp-uniform
       const int f = C.pf[c], cnt = C.pc[c];
       int sp[9];
-      sp[0] = f;
-      sp[8] = f + cnt;
       if (cnt <= n_leaf || L >= MAXD) {
-        for (int o = 1; o < 8; ++o) sp[o] = f;
-        sp[8] = f;
+        for (int o = 0; o < 9; ++o) sp[o] = f;
       } else {
-        for (int o = 1; o < 8; ++o) {  // first position whose child octant is >= o
-          int a = sp[o - 1], b = f + cnt;
-          while (a < b) {
-            const int mid = a + ((b - a) >> 1);
-            if (octant_at(code[mid], L + 1) < o) a = mid + 1; else b = mid;
-          }
-          sp[o] = a;
-        }
+        warp_split(code, f, cnt, L + 1, lane, sp);
         for (int o = 0; o < 8; ++o) nch += sp[o + 1] > sp[o];
       }
-      int* d = &spl[9 * static_cast<int64_t>(c - lb)];
-      for (int o = 0; o < 9; ++o) d[o] = sp[o];
+      if (lane == 0) {
+        int* d = &spl[9 * static_cast<int64_t>(c - lb)];
+        for (int o = 0; o < 9; ++o) d[o] = sp[o];
+      }
     }
-    int tot;
-    const int ex = block_scan_excl(nch, &tot);
-    if (c < c1) lpre[c - lb] = carry + ex;
-    carry += tot;
+    if (lane == 0) sn[w] = nch;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int run = carry;
+      for (int k = 0; k < W && base + k < c1; ++k) {
+        lpre[base + k - lb] = run;
+        run += sn[k];
+      }
+      carry = run;
+    }
+    __syncthreads();
   }
   if (threadIdx.x == 0) bsum[blockIdx.x] = carry;
 }
 
 // Offsets of the blocks' children and the end of level L + 1; a level that
 // does not fit the cell capacity stops the build (status overflow).
-__global__ void __launch_bounds__(GL) k_scan_level(int L, int* __restrict__ bsum, int* __restrict__ lvl, int cap,
-                                                   int* __restrict__ misc) {
+__global__ void __launch_bounds__(GLT) k_scan_level(int L, int* __restrict__ bsum, int* __restrict__ lvl, int cap,
+                                                    int* __restrict__ misc) {
+  constexpr int PER = GL / GLT;
   __shared__ int ws[32];
-  const int v = bsum[threadIdx.x];
+  int e[PER], v = 0;
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    e[k] = bsum[PER * threadIdx.x + k];
+    v += e[k];
+  }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   int x = v;
   for (int d = 1; d < 32; d <<= 1) {
@@ -454,7 +572,12 @@ __global__ void __launch_bounds__(GL) k_scan_level(int L, int* __restrict__ bsum
     ws[lane] = t;
   }
   __syncthreads();
-  bsum[threadIdx.x] = (w ? ws[w - 1] : 0) + x - v;
+  int run = (w ? ws[w - 1] : 0) + x - v;
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    bsum[PER * threadIdx.x + k] = run;
+    run += e[k];
+  }
   if (threadIdx.x == 0) {
     const int le = lvl[L + 1];
     const int64_t next = static_cast<int64_t>(le) + ws[31];
@@ -582,109 +705,177 @@ struct Props {  // final-order FP64 arrays and records
 
 __device__ __forceinline__ int final_index(const int* ni, int c) { return ni ? ni[c] : c; }
 
-// Cells of level L: tight box, boundary cube, mass, centre of mass and second
-// moments (leaves from their particles, nodes from their children with the
-// parallel-axis shift), then the cell's records.
-__global__ void k_props(int L, Cells C, const int* __restrict__ lvl, const int* __restrict__ ni,
-                        const double* __restrict__ xs, const double* __restrict__ ms, Props P,
-                        int* __restrict__ misc) {
-  const int lb = lvl[L], le = lvl[L + 1];
-  int leaves = 0;
-  for (int c = lb + blockIdx.x * blockDim.x + threadIdx.x; c < le; c += gridDim.x * blockDim.x) {
-    const int j = final_index(ni, c);
-    double bn[3] = {INFINITY, INFINITY, INFINITY}, bx[3] = {-INFINITY, -INFINITY, -INFINITY};
-    double Mc = 0, sx = 0, sy = 0, sz = 0;
-    const int f = C.pf[c], cnt = C.pc[c], nch = C.nc[c];
-    const int jc = nch ? final_index(ni, C.fc[c]) : 0;  // children are contiguous in both orders
-    if (nch == 0) {
-      ++leaves;
-      for (int t = f; t < f + cnt; ++t) {
-        const double* xp = &xs[3 * static_cast<int64_t>(t)];
-        for (int d = 0; d < 3; ++d) {
-          bn[d] = lesser(bn[d], xp[d]);
-          bx[d] = greater(bx[d], xp[d]);
-        }
-        Mc += ms[t];
-        sx += ms[t] * xp[0];
-        sy += ms[t] * xp[1];
-        sz += ms[t] * xp[2];
+// Tight box, boundary cube, mass, centre of mass and second moments of cell
+// c (a leaf from its particles, a node from its children with the
+// parallel-axis shift, in the host build's operation order), then its records.
+template <bool LEAF>
+__device__ __forceinline__ void cell_props(int c, Cells C, const int* __restrict__ ni, const double* __restrict__ xs,
+                                           const double* __restrict__ ms, const Props& P) {
+  const int j = final_index(ni, c);
+  double bn[3] = {INFINITY, INFINITY, INFINITY}, bx[3] = {-INFINITY, -INFINITY, -INFINITY};
+  double Mc = 0, sx = 0, sy = 0, sz = 0;
+  const int f = C.pf[c], cnt = C.pc[c], nch = LEAF ? 0 : C.nc[c];
+  const int jc = LEAF ? 0 : final_index(ni, C.fc[c]);  // children are contiguous in both orders
+  if (LEAF) {
+    for (int t = f; t < f + cnt; ++t) {
+      const double* xp = &xs[3 * static_cast<int64_t>(t)];
+      const double x0 = xp[0], x1 = xp[1], x2 = xp[2], m = ms[t];
+      bn[0] = lesser(bn[0], x0);
+      bn[1] = lesser(bn[1], x1);
+      bn[2] = lesser(bn[2], x2);
+      bx[0] = greater(bx[0], x0);
+      bx[1] = greater(bx[1], x1);
+      bx[2] = greater(bx[2], x2);
+      Mc += m;
+      sx = fma(m, x0, sx);
+      sy = fma(m, x1, sy);
+      sz = fma(m, x2, sz);
+    }
+  } else {
+    for (int q = jc; q < jc + nch; ++q) {
+      for (int d = 0; d < 3; ++d) {
+        bn[d] = lesser(bn[d], P.bmin[3 * q + d]);
+        bx[d] = greater(bx[d], P.bmax[3 * q + d]);
       }
-    } else {
-      for (int q = jc; q < jc + nch; ++q) {
-        for (int d = 0; d < 3; ++d) {
-          bn[d] = lesser(bn[d], P.bmin[3 * q + d]);
-          bx[d] = greater(bx[d], P.bmax[3 * q + d]);
-        }
-        Mc += P.M[q];
-        sx += P.M[q] * P.com[3 * q];
-        sy += P.M[q] * P.com[3 * q + 1];
-        sz += P.M[q] * P.com[3 * q + 2];
-      }
+      const double m = P.M[q];
+      Mc += m;
+      sx = fma(m, P.com[3 * q], sx);
+      sy = fma(m, P.com[3 * q + 1], sy);
+      sz = fma(m, P.com[3 * q + 2], sz);
     }
-    double cu[4], cm[3], s6[6] = {0, 0, 0, 0, 0, 0};
-    for (int d = 0; d < 3; ++d) cu[d] = (bn[d] + bx[d]) * 0.5;
-    double e = bx[0] - bn[0];
-    if (bx[1] - bn[1] > e) e = bx[1] - bn[1];
-    if (bx[2] - bn[2] > e) e = bx[2] - bn[2];
-    cu[3] = 0.5 * e;
-    if (Mc > 0) {
-      cm[0] = sx / Mc;
-      cm[1] = sy / Mc;
-      cm[2] = sz / Mc;
-    } else {
-      cm[0] = cu[0];
-      cm[1] = cu[1];
-      cm[2] = cu[2];
-    }
-    auto add_outer = [&](double wt, double y0, double y1, double y2) {
-      s6[0] += wt * y0 * y0;
-      s6[1] += wt * y1 * y1;
-      s6[2] += wt * y2 * y2;
-      s6[3] += wt * y0 * y1;
-      s6[4] += wt * y0 * y2;
-      s6[5] += wt * y1 * y2;
-    };
-    if (nch == 0) {
-      for (int t = f; t < f + cnt; ++t) {
-        const double* xp = &xs[3 * static_cast<int64_t>(t)];
-        add_outer(ms[t], xp[0] - cm[0], xp[1] - cm[1], xp[2] - cm[2]);
-      }
-    } else {
-      for (int q = jc; q < jc + nch; ++q) {
-        for (int k = 0; k < 6; ++k) s6[k] += P.S[6 * q + k];
-        add_outer(P.M[q], P.com[3 * q] - cm[0], P.com[3 * q + 1] - cm[1], P.com[3 * q + 2] - cm[2]);
-      }
-    }
-    for (int d = 0; d < 3; ++d) {
-      P.bmin[3 * j + d] = bn[d];
-      P.bmax[3 * j + d] = bx[d];
-      P.com[3 * j + d] = cm[d];
-    }
-    for (int d = 0; d < 4; ++d) P.cube[4 * j + d] = cu[d];
-    for (int k = 0; k < 6; ++k) P.S[6 * j + k] = s6[k];
-    P.M[j] = Mc;
-    // records read by the walk kernel
-    P.key[j] = C.key[c];
-    P.geo[j] = make_float4(static_cast<float>(cu[0]), static_cast<float>(cu[1]), static_cast<float>(cu[2]),
-                           static_cast<float>(cu[3]));
-    P.link[j] = nch ? make_int2(jc, nch) : make_int2(f, -cnt);
-    float chi[3], clo[3];
-    for (int d = 0; d < 3; ++d) {
-      chi[d] = static_cast<float>(cm[d]);
-      clo[d] = static_cast<float>(cm[d] - static_cast<double>(chi[d]));
-    }
-    const double tr = s6[0] + s6[1] + s6[2];
-    P.mp[4 * j] = make_float4(chi[0], chi[1], chi[2], static_cast<float>(Mc));
-    P.mp[4 * j + 1] = make_float4(clo[0], clo[1], clo[2], static_cast<float>(cnt));
-    P.mp[4 * j + 2] = make_float4(static_cast<float>(3.0 * s6[0]), static_cast<float>(3.0 * s6[1]),
-                                  static_cast<float>(3.0 * s6[2]), static_cast<float>(3.0 * s6[3]));
-    P.mp[4 * j + 3] = make_float4(static_cast<float>(3.0 * s6[4]), static_cast<float>(3.0 * s6[5]),
-                                  static_cast<float>(1.5 * tr), static_cast<float>(0.5 * tr));
-    P.pcount[j] = cnt;
-    P.cfirst[j] = f;
   }
+  double cu[4], cm[3], s6[6] = {0, 0, 0, 0, 0, 0};
+  for (int d = 0; d < 3; ++d) cu[d] = (bn[d] + bx[d]) * 0.5;
+  double e = bx[0] - bn[0];
+  if (bx[1] - bn[1] > e) e = bx[1] - bn[1];
+  if (bx[2] - bn[2] > e) e = bx[2] - bn[2];
+  cu[3] = 0.5 * e;
+  if (Mc > 0) {
+    cm[0] = sx / Mc;
+    cm[1] = sy / Mc;
+    cm[2] = sz / Mc;
+  } else {
+    cm[0] = cu[0];
+    cm[1] = cu[1];
+    cm[2] = cu[2];
+  }
+  auto add_outer = [&](double wt, double y0, double y1, double y2) {
+    const double w0 = wt * y0, w1 = wt * y1, w2 = wt * y2;
+    s6[0] = fma(w0, y0, s6[0]);
+    s6[1] = fma(w1, y1, s6[1]);
+    s6[2] = fma(w2, y2, s6[2]);
+    s6[3] = fma(w0, y1, s6[3]);
+    s6[4] = fma(w0, y2, s6[4]);
+    s6[5] = fma(w1, y2, s6[5]);
+  };
+  if (LEAF) {
+    for (int t = f; t < f + cnt; ++t) {
+      const double* xp = &xs[3 * static_cast<int64_t>(t)];
+      add_outer(ms[t], xp[0] - cm[0], xp[1] - cm[1], xp[2] - cm[2]);
+    }
+  } else {
+    for (int q = jc; q < jc + nch; ++q) {
+      for (int k = 0; k < 6; ++k) s6[k] += P.S[6 * q + k];
+      add_outer(P.M[q], P.com[3 * q] - cm[0], P.com[3 * q + 1] - cm[1], P.com[3 * q + 2] - cm[2]);
+    }
+  }
+  for (int d = 0; d < 3; ++d) {
+    P.bmin[3 * j + d] = bn[d];
+    P.bmax[3 * j + d] = bx[d];
+    P.com[3 * j + d] = cm[d];
+  }
+  for (int d = 0; d < 4; ++d) P.cube[4 * j + d] = cu[d];
+  for (int k = 0; k < 6; ++k) P.S[6 * j + k] = s6[k];
+  P.M[j] = Mc;
+  // records read by the walk kernel
+  P.key[j] = C.key[c];
+  P.geo[j] = make_float4(static_cast<float>(cu[0]), static_cast<float>(cu[1]), static_cast<float>(cu[2]),
+                         static_cast<float>(cu[3]));
+  P.link[j] = LEAF ? make_int2(f, -cnt) : make_int2(jc, nch);
+  float chi[3], clo[3];
+  for (int d = 0; d < 3; ++d) {
+    chi[d] = static_cast<float>(cm[d]);
+    clo[d] = static_cast<float>(cm[d] - static_cast<double>(chi[d]));
+  }
+  const double tr = s6[0] + s6[1] + s6[2];
+  P.mp[4 * j] = make_float4(chi[0], chi[1], chi[2], static_cast<float>(Mc));
+  P.mp[4 * j + 1] = make_float4(clo[0], clo[1], clo[2], static_cast<float>(cnt));
+  P.mp[4 * j + 2] = make_float4(static_cast<float>(3.0 * s6[0]), static_cast<float>(3.0 * s6[1]),
+                                static_cast<float>(3.0 * s6[2]), static_cast<float>(3.0 * s6[3]));
+  P.mp[4 * j + 3] = make_float4(static_cast<float>(3.0 * s6[4]), static_cast<float>(3.0 * s6[5]),
+                                static_cast<float>(1.5 * tr), static_cast<float>(0.5 * tr));
+  P.pcount[j] = cnt;
+  P.cfirst[j] = f;
+}
+
+// Leaves (of every level) bucketed by particle count, largest first, so that
+// the lanes of a warp loop over equally many particles: histogram, then
+// scatter of the cell indices into lorder.
+__device__ __forceinline__ int leaf_bin(int cnt) { return LBINS - min(cnt, LBINS); }  // 32+ -> bin 0
+
+__global__ void __launch_bounds__(TB) k_leaf_hist(Cells C, const int* __restrict__ lvl, int* __restrict__ lhist,
+                                                  int* __restrict__ misc) {
+  __shared__ int h[LBINS];
+  if (threadIdx.x < LBINS) h[threadIdx.x] = 0;
+  __syncthreads();
+  const int nc = lvl[NLEV];
+  int leaves = 0;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x)
+    if (C.nc[c] == 0) {
+      atomicAdd(&h[leaf_bin(C.pc[c])], 1);
+      ++leaves;
+    }
   for (int s = 16; s; s >>= 1) leaves += __shfl_xor_sync(FULL, leaves, s);
   if ((threadIdx.x & 31) == 0 && leaves) atomicAdd(&misc[M_NLEAVES], leaves);
+  __syncthreads();
+  if (threadIdx.x < LBINS && h[threadIdx.x]) atomicAdd(&lhist[threadIdx.x], h[threadIdx.x]);
+}
+
+__global__ void __launch_bounds__(TB) k_leaf_scatter(Cells C, const int* __restrict__ lvl,
+                                                     const int* __restrict__ lhist, int* __restrict__ lfill,
+                                                     int* __restrict__ lorder) {
+  __shared__ int base[LBINS], h[LBINS];
+  if (threadIdx.x < 32) {
+    const int v = lhist[threadIdx.x];
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(FULL, x, o);
+      if (threadIdx.x >= o) x += y;
+    }
+    base[threadIdx.x] = x - v;
+  }
+  const int nc = lvl[NLEV];
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t c0 = static_cast<int64_t>(blockIdx.x) * blockDim.x; c0 < nc; c0 += stride) {
+    if (threadIdx.x < LBINS) h[threadIdx.x] = 0;
+    __syncthreads();
+    const int c = static_cast<int>(c0) + threadIdx.x;
+    const bool leaf = c < nc && C.nc[c] == 0;
+    const int b = leaf ? leaf_bin(C.pc[c]) : 0;
+    const int r = leaf ? atomicAdd(&h[b], 1) : 0;  // rank within the block's bin
+    __syncthreads();
+    if (threadIdx.x < LBINS && h[threadIdx.x]) h[threadIdx.x] = atomicAdd(&lfill[threadIdx.x], h[threadIdx.x]);
+    __syncthreads();
+    if (leaf) lorder[base[b] + h[b] + r] = c;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(TB) k_leaf_props(Cells C, const int* __restrict__ lorder,
+                                                   const int* __restrict__ misc, const int* __restrict__ ni,
+                                                   const double* __restrict__ xs, const double* __restrict__ ms,
+                                                   Props P) {
+  const int nl = misc[M_NLEAVES];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nl; k += gridDim.x * blockDim.x)
+    cell_props<true>(lorder[k], C, ni, xs, ms, P);
+}
+
+// Nodes of level L (their children, one level deeper, are done).
+__global__ void __launch_bounds__(TB) k_node_props(int L, Cells C, const int* __restrict__ lvl,
+                                                   const int* __restrict__ ni, Props P) {
+  const int lb = lvl[L], le = lvl[L + 1];
+  for (int c = lb + blockIdx.x * blockDim.x + threadIdx.x; c < le; c += gridDim.x * blockDim.x)
+    if (C.nc[c] > 0) cell_props<false>(c, C, ni, nullptr, nullptr, P);
 }
 
 // ---------------------------------------------------------------- groups and items
@@ -913,16 +1104,17 @@ cudaError_t gpu_build(const GpuBuild& a, cudaStream_t st) {
 
   // ---- keys and the stable sort (8 passes of 8 bits over the 63-bit keys)
   k_bbox<<<nch, TB, 0, st>>>(a.pos, a.mass, dch, part, misc);
-  k_root<<<(a.n_sys + 127) / 128, 128, 0, st>>>(part, dchunk0, a.n_sys, sg);
+  k_root<<<a.n_sys, TB, 0, st>>>(part, dchunk0, sg);
   k_morton<<<nch, TB, 0, st>>>(a.pos, dch, sg, keyA, valA);
-  const int m = 256 * nch;
+  int* dtot = at<int>(S, Lo.dtot);
+  const int segblocks = (256 * a.n_sys + TB / 32 - 1) / (TB / 32);
   for (int pass = 0; pass < 8; ++pass) {
     const int sh = 8 * pass;
     const bool even = (pass & 1) == 0;
     k_upsweep<<<nch, TB, 0, st>>>(even ? keyA : keyB, dch, sh, cnt);
-    k_scan_single<<<1, 1024, 0, st>>>(cnt, nullptr, m, nullptr);
+    k_scan_digits<<<segblocks, TB, 0, st>>>(cnt, dchunk0, a.n_sys, dtot);
     k_downsweep<<<nch, TB, 0, st>>>(even ? keyA : keyB, even ? valA : valB, even ? keyB : keyA,
-                                    even ? valB : valA, dch, sh, cnt);
+                                    even ? valB : valA, dch, sh, cnt, dtot);
   }
   OG_TRY(cudaGetLastError());
   k_gather<<<grid_for(a.n, TB), TB, 0, st>>>(valA, a.pos, a.mass, a.n, xs, ms, a.parts, a.perm);
@@ -931,7 +1123,7 @@ cudaError_t gpu_build(const GpuBuild& a, cudaStream_t st) {
   k_roots<<<(std::max(a.n_sys, NLEV + 2) + 127) / 128, 128, 0, st>>>(a.n_sys, doffs, C, lvl);
   for (int L = 0; L < MAXD; ++L) {
     k_split<<<GL, TB, 0, st>>>(L, keyA, C, a.n_leaf, lvl, spl, lpre, bsum);
-    k_scan_level<<<1, GL, 0, st>>>(L, bsum, lvl, static_cast<int>(a.cap), misc);
+    k_scan_level<<<1, GLT, 0, st>>>(L, bsum, lvl, static_cast<int>(a.cap), misc);
     k_emit<<<GL, TB, 0, st>>>(L, C, lvl, spl, lpre, bsum, misc);
   }
   OG_TRY(cudaGetLastError());
@@ -953,8 +1145,14 @@ cudaError_t gpu_build(const GpuBuild& a, cudaStream_t st) {
     k_one_system_offsets<<<1, 1, 0, st>>>(lvl, a.cell_off);
   }
 
-  // ---- properties, deepest level first
-  for (int L = MAXD; L >= 0; --L) k_props<<<gc, TB, 0, st>>>(L, C, lvl, ni, xs, ms, P, misc);
+  // ---- properties: every leaf at once, then the nodes deepest level first
+  int* lorder = at<int>(S, Lo.lorder);
+  int* lhist = at<int>(S, Lo.lhist);
+  OG_TRY(cudaMemsetAsync(lhist, 0, 4 * 2 * LBINS, st));
+  k_leaf_hist<<<gc, TB, 0, st>>>(C, lvl, lhist, misc);
+  k_leaf_scatter<<<gc, TB, 0, st>>>(C, lvl, lhist, lhist + LBINS, lorder);
+  k_leaf_props<<<gc, TB, 0, st>>>(C, lorder, misc, ni, xs, ms, P);
+  for (int L = MAXD - 1; L >= 0; --L) k_node_props<<<gc, TB, 0, st>>>(L, C, lvl, ni, P);
   OG_TRY(cudaGetLastError());
 
   // ---- groups (ordered by first particle) and work items

@@ -15,7 +15,9 @@
 //    the longest box side, Fig. 1), mass, centre of mass and second moments.
 // The build sorts particles by Morton key (parallel LSD radix sort), splits
 // key ranges level by level, and combines moments bottom-up with the
-// parallel-axis theorem, all in FP64. Compile with -ffp-contract=off.
+// parallel-axis theorem, all in FP64 (products accumulated with explicit fused
+// multiply-adds). Compile with -ffp-contract=off: the GPU build reproduces
+// these operations one for one.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -421,9 +423,9 @@ int build_system(const double* pos, const double* mass, int64_t n, int n_leaf, i
               bx[d] = std::max(bx[d], xp[d]);
             }
             Mc += T.m[t];
-            sx += T.m[t] * xp[0];
-            sy += T.m[t] * xp[1];
-            sz += T.m[t] * xp[2];
+            sx = std::fma(T.m[t], xp[0], sx);
+            sy = std::fma(T.m[t], xp[1], sy);
+            sz = std::fma(T.m[t], xp[2], sz);
           }
         } else {
           for (int j = T.first_child[c]; j < T.first_child[c] + T.n_child[c]; ++j) {
@@ -432,9 +434,9 @@ int build_system(const double* pos, const double* mass, int64_t n, int n_leaf, i
               bx[d] = std::max(bx[d], T.bmax[3 * j + d]);
             }
             Mc += T.M[j];
-            sx += T.M[j] * T.com[3 * j];
-            sy += T.M[j] * T.com[3 * j + 1];
-            sz += T.M[j] * T.com[3 * j + 2];
+            sx = std::fma(T.M[j], T.com[3 * j], sx);
+            sy = std::fma(T.M[j], T.com[3 * j + 1], sy);
+            sz = std::fma(T.M[j], T.com[3 * j + 2], sz);
           }
         }
         double* cu = &T.cube[4 * c];
@@ -455,12 +457,13 @@ int build_system(const double* pos, const double* mass, int64_t n, int n_leaf, i
         }
         for (int q = 0; q < 6; ++q) s6[q] = 0;
         auto add_outer = [&](double w, double y0, double y1, double y2) {
-          s6[0] += w * y0 * y0;
-          s6[1] += w * y1 * y1;
-          s6[2] += w * y2 * y2;
-          s6[3] += w * y0 * y1;
-          s6[4] += w * y0 * y2;
-          s6[5] += w * y1 * y2;
+          const double w0 = w * y0, w1 = w * y1, w2 = w * y2;
+          s6[0] = std::fma(w0, y0, s6[0]);
+          s6[1] = std::fma(w1, y1, s6[1]);
+          s6[2] = std::fma(w2, y2, s6[2]);
+          s6[3] = std::fma(w0, y1, s6[3]);
+          s6[4] = std::fma(w0, y2, s6[4]);
+          s6[5] = std::fma(w1, y2, s6[5]);
         };
         if (T.n_child[c] == 0) {
           for (int64_t t = f; t < f + cnt; ++t)
