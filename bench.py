@@ -62,9 +62,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the theta scan, clustered and ensemble legs")
-    ap.add_argument("--leg", default="", choices=["", "learned"],
+    ap.add_argument("--leg", default="", choices=["", "learned", "build"],
                     help="learned: train the criterion on the 1M sphere+disc and launch the learned walk "
-                         "twice (a small driver for profilers; prints the interaction counts)")
+                         "twice (a small driver for profilers; prints the interaction counts); build: "
+                         "--warmup + --steps GPU tree builds of the workload (prints their wall times)")
     return ap.parse_args()
 
 
@@ -408,6 +409,26 @@ def run_learned_driver():
     print(json.dumps({"status": T.status(), "counts": T.interaction_counts()}), flush=True)
 
 
+def run_build_driver(a):
+    """The GPU tree build alone: warm-up builds, then --steps builds of the
+    workload's tree from device-resident positions (profiling driver)."""
+    import torch
+    from paper_1005_5384_gb300 import octgrav as G
+    pos, m = W.plummer(a.n, seed=a.seed)
+    xd = torch.from_numpy(np.ascontiguousarray(pos)).cuda()
+    md = torch.from_numpy(np.ascontiguousarray(m)).cuda()
+    ng = a.n_group if a.n_group > 0 else 512
+    ms = []
+    for k in range(a.warmup + a.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B = G.Tree.build_gpu(xd, md, a.n_leaf, ng)
+        if k >= a.warmup:
+            ms.append(1e3 * (time.perf_counter() - t0))
+        del B
+    print(json.dumps({"leg": "build", "n": a.n, "n_group": ng, "ms": ms}), flush=True)
+
+
 def run_reference(a, rank, world):
     if rank != 0:
         return
@@ -455,6 +476,9 @@ def main():
         return
     if a.leg == "learned":
         run_learned_driver()
+        return
+    if a.leg == "build":
+        run_build_driver(a)
         return
 
     import torch
