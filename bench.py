@@ -263,6 +263,23 @@ def extras(torch, G, a, pos, m, T, out, flush, stream, peak, steps):
                          "identical": bool(np.array_equal(B.cell_keys(), H.cell_keys())
                                            and np.array_equal(B.perm(), H.perm()))}
     del B, H, xd, md
+    # time integration: leapfrog steps of a 1M Plummer sphere in equilibrium, the
+    # tree rebuilt on the GPU for every force evaluation, state on the device
+    xs, vs, ms_ = W.plummer_pv(a.n, seed=a.seed)
+    S = G.Sim(xs, vs, ms_, a.eps, a.theta, n_leaf=a.n_leaf, n_group=a.n_group, stream=stream)
+    e0 = sum(S.energy(stream=stream))
+    S.step(1.0 / 128, 1, stream=stream)
+    nsteps = 8
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    S.step(1.0 / 128, nsteps, stream=stream)
+    dt_wall = time.perf_counter() - t0
+    e1 = sum(S.energy(stream=stream))
+    res["leapfrog_plummer_1M"] = {"dt": 1.0 / 128, "steps": nsteps, "ms_per_step": 1e3 * dt_wall / nsteps,
+                                  "particle_steps_per_s": a.n * nsteps / dt_wall,
+                                  "rel_energy_change_9_steps": (e1 - e0) / abs(e0),
+                                  "per_step": "kick+drift, GPU tree build, walk+evaluation, unpermute, kick"}
+    del S
     # C2 at theta = 0.75
     T.forces_device(a.eps, 0.75, out, stream=stream)
     ms = time_kernel(torch, lambda: T.forces_device(a.eps, 0.75, out, stream=stream), flush, steps, stream)

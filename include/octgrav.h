@@ -3,10 +3,12 @@
  *
  * Method: Gaburov, Bedorf & Portegies Zwart (2010), "Gravitational tree-code
  * on graphics processing units: implementation in CUDA". The octree, the
- * tight boxes, boundary cubes and multipole moments are built on the host in
- * FP64 (Sec. 2.1); the per-group tree walk that sorts cells into an
- * interaction list (Sec. 2.2, Listings 1-2) and the evaluation of that list
- * (Sec. 2.3, Listings 3-4) run on the GPU in one fused CUDA kernel.
+ * tight boxes, boundary cubes and multipole moments are built in FP64
+ * (Sec. 2.1) on the host or, with a byte-identical result, on the GPU; the
+ * per-group tree walk that sorts cells into an interaction list (Sec. 2.2,
+ * Listings 1-2) and the evaluation of that list (Sec. 2.3, Listings 3-4) run
+ * on the GPU in one fused CUDA kernel; a leapfrog integrator keeps an N-body
+ * state on the device.
  *
  * Conventions shared by every entry point:
  *  - Positions are xyz-interleaved FP64 arrays of length 3*n, masses FP64 of
@@ -53,6 +55,7 @@ extern "C" {
 #define OCTGRAV_MAX_ITEM 64        /* particles evaluated by one warp (larger groups are split) */
 
 typedef struct octgrav_tree octgrav_tree; /* opaque, library-owned */
+typedef struct octgrav_sim octgrav_sim;   /* opaque, library-owned integrator state */
 
 /* Build the octree of one system on the host in FP64 (Sec. 2.1).
  *   pos[3n], mass[n]: input order, caller-owned, only read during the call.
@@ -156,6 +159,44 @@ int octgrav_forces_tree_device64(octgrav_tree *t, double eps, double theta, doub
  * ERR_TIMEOUT, ERR_INDEX). */
 int octgrav_forces_gpu(const double *pos, const double *mass, int64_t n, double eps, double theta,
                        double G, int n_leaf, int n_group, double *acc, double *pot, void *stream);
+
+/* ---- Time integration on the device.
+ *
+ * The paper integrates on the host and does not name its scheme; this is the
+ * standard kick-drift-kick leapfrog with one shared step dt, with the whole
+ * state (FP64 positions, velocities, masses, accelerations, potentials, input
+ * order) resident on the current device. Every force evaluation builds the
+ * tree on the GPU (octgrav_build_tree_gpu) and runs the walk kernel; buffers
+ * are reused from step to step. */
+
+/* Create the integrator from HOST arrays pos, vel (n x 3) and mass (n), copied
+ * to the device, and evaluate the initial forces. eps, theta, G, n_leaf and
+ * n_group as for octgrav_forces_ex. Returns after the first force
+ * evaluation. Errors: ERR_ARG, ERR_NONFINITE (non-finite input, negative
+ * mass), ERR_OOM, ERR_CUDA and the launch status codes. */
+int octgrav_sim_create(const double *pos, const double *vel, const double *mass, int64_t n,
+                       double eps, double theta, double G, int n_leaf, int n_group, void *stream,
+                       octgrav_sim **out);
+
+/* Advance n_steps steps: v += a dt/2, x += v dt, forces, v += a dt/2 (each
+ * update one rounded product and one rounded sum per component). dt may be
+ * negative (the scheme is time-reversible). Returns when the steps are done.
+ * Errors: ERR_ARG (NULL, non-finite dt, n_steps < 0) and those of a force
+ * evaluation. */
+int octgrav_sim_step(octgrav_sim *s, double dt, int n_steps, void *stream);
+
+/* Kinetic energy sum m |v|^2 / 2 and potential energy sum m phi / 2 (phi of
+ * the last force evaluation, self term excluded), FP64, in a fixed
+ * summation order. Errors: ERR_ARG, ERR_CUDA. */
+int octgrav_sim_energy(octgrav_sim *s, double *kinetic, double *potential, void *stream);
+
+/* Copy the state to HOST arrays (any may be NULL): pos, vel, acc (n x 3),
+ * pot (n), input order. Errors: ERR_ARG, ERR_CUDA. */
+int octgrav_sim_state(octgrav_sim *s, double *pos, double *vel, double *acc, double *pot,
+                      void *stream);
+
+/* Release the integrator and its device memory (NULL is a no-op). */
+void octgrav_sim_free(octgrav_sim *s);
 
 /* Wait for stream and return the status of the last launch on this tree:
  * OK, ERR_STACK, ERR_TIMEOUT or ERR_INDEX. Clears nothing. */

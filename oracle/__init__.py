@@ -16,6 +16,7 @@ Steps (Gaburov, Bedorf & Portegies Zwart 2010):
                   evaluation (Sec. 2.3, Listings 3-4)
   Tree.mlp_*      O8  learned opening criterion: features, error labels, the
                   walk that consults the network (see oracle/mlp.py)
+  leapfrog()      O9  kick-drift-kick time integration with direct forces
 """
 from __future__ import annotations
 
@@ -128,6 +129,33 @@ def direct(pos, mass, eps: float, G: float = 1.0, targets=None, nthreads: int | 
     lib.ora_direct(pos.reshape(-1), mass, n, tp, nt, float(eps), float(G), acc.reshape(-1), pot,
                    int(nthreads or default_threads()))
     return acc, pot
+
+
+def leapfrog(pos, vel, mass, eps: float, dt: float, n_steps: int, G: float = 1.0, nthreads: int | None = None):
+    """O9: kick-drift-kick leapfrog with one shared step and direct-sum forces (O1).
+
+    The paper integrates on the host and does not name its scheme; this is
+    the standard second-order symplectic one. Per step: v += a dt/2,
+    x += v dt, a = forces(x), v += a dt/2. Returns (pos, vel, acc, pot).
+    """
+    x = np.array(pos, dtype=np.float64, copy=True)
+    v = np.array(vel, dtype=np.float64, copy=True)
+    m = np.ascontiguousarray(mass, dtype=np.float64)
+    a, phi = direct(x, m, eps, G, nthreads=nthreads)
+    h = 0.5 * dt
+    for _ in range(int(n_steps)):
+        v = v + a * h
+        x = x + v * dt
+        a, phi = direct(x, m, eps, G, nthreads=nthreads)
+        v = v + a * h
+    return x, v, a, phi
+
+
+def energies(vel, mass, pot):
+    """(kinetic, potential) = (sum m v^2 / 2, sum m phi / 2) in FP64."""
+    v = np.asarray(vel, dtype=np.float64)
+    m = np.asarray(mass, dtype=np.float64)
+    return 0.5 * float(np.sum(m * np.einsum("ij,ij->i", v, v))), 0.5 * float(np.sum(m * np.asarray(pot)))
 
 
 def theta2_f32(theta: float) -> np.float32:

@@ -56,6 +56,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     ko = os.path.join(BUILD, "octgrav_kernels.o")
     mo = os.path.join(BUILD, "octgrav_mlp.o")
     bo = os.path.join(BUILD, "octgrav_build.o")
+    so = os.path.join(BUILD, "octgrav_sim.o")
     ho = os.path.join(BUILD, "octgrav_host.o")
 
     def nv(src, obj, *extra):
@@ -65,10 +66,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
     k_cmd = nv("octgrav_kernels.cu", ko)
     m_cmd = nv("octgrav_mlp.cu", mo)
     b_cmd = nv("octgrav_build.cu", bo, "-fmad=false")
+    s_cmd = nv("octgrav_sim.cu", so, "-fmad=false")
     h_cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-fno-fast-math", "-pthread",
              "-I", os.path.join(cuda, "include"), "-I", INCLUDE,
              "-c", os.path.join(CSRC, "octgrav_host.cpp"), "-o", ho]
-    cmds = (k_cmd, m_cmd, b_cmd, h_cmd)
+    cmds = (k_cmd, m_cmd, b_cmd, s_cmd, h_cmd)
     procs = [subprocess.Popen(c, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True) for c in cmds]
     outs = [p.communicate()[0] for p in procs]
     for p, o, c in zip(procs, outs, cmds):
@@ -77,7 +79,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if verbose and o:
             print(o)
     tmp = LIB + ".%d.tmp" % os.getpid()
-    link = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, ko, mo, bo, ho, "-lpthread"]
+    link = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, ko, mo, bo, so, ho, "-lpthread"]
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed: %s\n%s" % (" ".join(link), r.stdout))

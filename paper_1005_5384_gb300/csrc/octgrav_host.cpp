@@ -586,6 +586,20 @@ struct octgrav_tree {
   std::vector<SysTree> sys_scratch;
 };
 
+// N-body state for the time integration, all on one device.
+struct octgrav_sim {
+  int64_t n = 0;
+  double eps = 0, theta = 0, G = 1;
+  int n_leaf = 16, n_group = 16;
+  Device dev;                        // tree and build buffers, reused every step
+  DevBuf x, v, m, a, phi, epart;     // FP64 state (input order) and energy partials
+  int64_t steps = 0;
+  ~octgrav_sim() {
+    for (DevBuf* b : {&x, &v, &m, &a, &phi, &epart}) b->release();
+    dev.release();
+  }
+};
+
 namespace {
 
 // Split every group into work items of at most 32 * ppl particles.
@@ -1274,6 +1288,109 @@ int octgrav_forces_gpu(const double* pos, const double* mass, int64_t n, double 
   octgrav_free_tree(t);
   return rc;
 }
+
+// ---- time integration
+
+namespace {
+
+// Forces at the current positions: tree built on the GPU, walk, unpermute
+// into the state's acceleration and potential arrays; waits for the stream.
+int sim_forces(octgrav_sim* s, cudaStream_t st) {
+  const int64_t off[2] = {0, s->n};
+  octgrav_tree* t = nullptr;
+  int rc = build_gpu_common(1, off, static_cast<const double*>(s->x.p), static_cast<const double*>(s->m.p),
+                            s->n_leaf, s->n_group, st, &s->dev, &t);
+  if (rc) return rc;
+  rc = forces_dev64(t, s->eps, s->theta, s->G, static_cast<double*>(s->a.p), static_cast<double*>(s->phi.p), st);
+  if (!rc) rc = read_status(t, st);
+  octgrav_free_tree(t);
+  return rc;
+}
+
+}  // namespace
+
+int octgrav_sim_create(const double* pos, const double* vel, const double* mass, int64_t n, double eps, double theta,
+                       double G, int n_leaf, int n_group, void* stream, octgrav_sim** out) {
+  if (!out) return fail(OCTGRAV_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!pos || !vel || !mass || n < 1) return fail(OCTGRAV_ERR_ARG, "NULL input or n < 1");
+  int rc = check_params(eps, theta, G);
+  if (rc) return rc;
+  for (int64_t i = 0; i < 3 * n; ++i)
+    if (!std::isfinite(vel[i])) return fail(OCTGRAV_ERR_NONFINITE, "non-finite velocity");
+  std::unique_ptr<octgrav_sim> s(new (std::nothrow) octgrav_sim());
+  if (!s) return fail(OCTGRAV_ERR_OOM, "host allocation failed");
+  s->n = n;
+  s->eps = eps;
+  s->theta = theta;
+  s->G = G;
+  s->n_leaf = n_leaf;
+  s->n_group = n_group;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if ((rc = s->x.reserve(24 * n)) || (rc = s->v.reserve(24 * n)) || (rc = s->m.reserve(8 * n)) ||
+      (rc = s->a.reserve(24 * n)) || (rc = s->phi.reserve(8 * n)) || (rc = s->epart.reserve(16 * og::SIM_EBLOCKS)))
+    return rc;
+  CUDA_TRY(cudaMemcpyAsync(s->x.p, pos, 24 * n, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(s->v.p, vel, 24 * n, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(s->m.p, mass, 8 * n, cudaMemcpyHostToDevice, st));
+  if ((rc = sim_forces(s.get(), st))) return rc;
+  *out = s.release();
+  return OCTGRAV_OK;
+}
+
+int octgrav_sim_step(octgrav_sim* s, double dt, int n_steps, void* stream) {
+  if (!s) return fail(OCTGRAV_ERR_ARG, "sim is NULL");
+  if (!std::isfinite(dt) || n_steps < 0) return fail(OCTGRAV_ERR_ARG, "need a finite dt and n_steps >= 0");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  double* x = static_cast<double*>(s->x.p);
+  double* v = static_cast<double*>(s->v.p);
+  const double* a = static_cast<const double*>(s->a.p);
+  const double h = 0.5 * dt;
+  for (int k = 0; k < n_steps; ++k) {
+    cudaError_t e = og::sim_kick_drift(x, v, a, s->n, h, dt, true, st);  // v += a dt/2, x += v dt
+    if (e != cudaSuccess) return fail(OCTGRAV_ERR_CUDA, "kick/drift launch failed: %s", cudaGetErrorString(e));
+    if (int rc = sim_forces(s, st)) return rc;
+    e = og::sim_kick_drift(x, v, a, s->n, h, 0.0, false, st);  // v += a dt/2
+    if (e != cudaSuccess) return fail(OCTGRAV_ERR_CUDA, "kick launch failed: %s", cudaGetErrorString(e));
+    ++s->steps;
+  }
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return OCTGRAV_OK;
+}
+
+int octgrav_sim_energy(octgrav_sim* s, double* kinetic, double* potential, void* stream) {
+  if (!s || !kinetic || !potential) return fail(OCTGRAV_ERR_ARG, "NULL argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = og::sim_energy_partials(static_cast<const double*>(s->v.p), static_cast<const double*>(s->m.p),
+                                          static_cast<const double*>(s->phi.p), s->n, static_cast<double*>(s->epart.p),
+                                          st);
+  if (e != cudaSuccess) return fail(OCTGRAV_ERR_CUDA, "energy launch failed: %s", cudaGetErrorString(e));
+  double part[2 * og::SIM_EBLOCKS];
+  CUDA_TRY(cudaMemcpyAsync(part, s->epart.p, sizeof part, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  double k = 0, w = 0;
+  for (int b = 0; b < og::SIM_EBLOCKS; ++b) {
+    k += part[2 * b];
+    w += part[2 * b + 1];
+  }
+  *kinetic = k;
+  *potential = w;
+  return OCTGRAV_OK;
+}
+
+int octgrav_sim_state(octgrav_sim* s, double* pos, double* vel, double* acc, double* pot, void* stream) {
+  if (!s) return fail(OCTGRAV_ERR_ARG, "sim is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t n = s->n;
+  if (pos) CUDA_TRY(cudaMemcpyAsync(pos, s->x.p, 24 * n, cudaMemcpyDeviceToHost, st));
+  if (vel) CUDA_TRY(cudaMemcpyAsync(vel, s->v.p, 24 * n, cudaMemcpyDeviceToHost, st));
+  if (acc) CUDA_TRY(cudaMemcpyAsync(acc, s->a.p, 24 * n, cudaMemcpyDeviceToHost, st));
+  if (pot) CUDA_TRY(cudaMemcpyAsync(pot, s->phi.p, 8 * n, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return OCTGRAV_OK;
+}
+
+void octgrav_sim_free(octgrav_sim* s) { delete s; }
 
 int octgrav_status(octgrav_tree* t, void* stream) {
   if (!t) return fail(OCTGRAV_ERR_ARG, "tree is NULL");

@@ -178,4 +178,14 @@ cudaError_t gpu_build_items(const GpuBuild& a, cudaStream_t stream);
 cudaError_t gpu_unpermute(const float4* out, const int* perm, int64_t n, double* acc, double* pot,
                           cudaStream_t stream);
 
+// ---- time integration (octgrav_sim.cu)
+
+constexpr int SIM_EBLOCKS = 256;  // blocks (and partial-sum pairs) of the energy reduction
+// v += a h; then x += v dt when drift (all arrays n x 3, FP64).
+cudaError_t sim_kick_drift(double* x, double* v, const double* a, int64_t n, double h, double dt, bool drift,
+                           cudaStream_t stream);
+// part[2 b], part[2 b + 1] = block b's sums of m |v|^2 / 2 and m phi / 2.
+cudaError_t sim_energy_partials(const double* v, const double* m, const double* pot, int64_t n, double* part,
+                                cudaStream_t stream);
+
 }  // namespace og

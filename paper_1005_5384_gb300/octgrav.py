@@ -51,6 +51,12 @@ _SIGS = {
     "octgrav_forces_tree_device64": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double, _vp, _vp, _vp]),
     "octgrav_forces_gpu": (C.c_int, [_vp, _vp, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int,
                                      _vp, _vp, _vp]),
+    "octgrav_sim_create": (C.c_int, [_vp, _vp, _vp, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_int,
+                                     C.c_int, _vp, C.POINTER(_vp)]),
+    "octgrav_sim_step": (C.c_int, [_vp, C.c_double, C.c_int, _vp]),
+    "octgrav_sim_energy": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double), _vp]),
+    "octgrav_sim_state": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "octgrav_sim_free": (None, [_vp]),
     "octgrav_status": (C.c_int, [_vp, _vp]),
     "octgrav_tree_stats": (C.c_int, [_vp, _i64, C.c_int]),
     "octgrav_tree_perm": (C.c_int, [_vp, _i64]),
@@ -393,6 +399,47 @@ def forces_gpu(pos, mass, eps: float, theta: float, n_leaf: int = 16, n_group: i
                                   int(n_group if n_group is not None else n_leaf), _p(acc), _p(pot),
                                   _stream_handle(stream)))
     return acc, pot
+
+
+class Sim:
+    """Leapfrog (kick-drift-kick) integrator with the state on the GPU and the
+    tree rebuilt on the GPU at every force evaluation."""
+
+    def __init__(self, pos, vel, mass, eps: float, theta: float, G: float = 1.0, n_leaf: int = 16,
+                 n_group: int | None = None, stream=None):
+        lib = load()
+        pos, mass = _pm(pos, mass)
+        vel = np.ascontiguousarray(vel, dtype=np.float64).reshape(-1)
+        if vel.shape != pos.shape:
+            raise ValueError("vel must have the shape of pos")
+        self.n = mass.shape[0]
+        h = C.c_void_p()
+        _check(lib.octgrav_sim_create(_p(pos), _p(vel), _p(mass), self.n, float(eps), float(theta), float(G),
+                                      int(n_leaf), int(n_group if n_group is not None else n_leaf),
+                                      _stream_handle(stream), C.byref(h)))
+        self._h = h
+
+    def step(self, dt: float, n_steps: int = 1, stream=None):
+        _check(load().octgrav_sim_step(self._h, float(dt), int(n_steps), _stream_handle(stream)))
+
+    def energy(self, stream=None):
+        """(kinetic, potential) in FP64."""
+        k, w = C.c_double(), C.c_double()
+        _check(load().octgrav_sim_energy(self._h, C.byref(k), C.byref(w), _stream_handle(stream)))
+        return k.value, w.value
+
+    def state(self, stream=None):
+        """(pos, vel, acc [n,3], pot [n]) on the host."""
+        x, v, a = np.zeros((self.n, 3)), np.zeros((self.n, 3)), np.zeros((self.n, 3))
+        p = np.zeros(self.n)
+        _check(load().octgrav_sim_state(self._h, _p(x), _p(v), _p(a), _p(p), _stream_handle(stream)))
+        return x, v, a, p
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.octgrav_sim_free(h)
+            self._h = None
 
 
 MLP_RECORD = 5105

@@ -70,6 +70,31 @@ def plummer(n: int, seed: int = 1, a: float = 1.0, rmax: float = 100.0,
     return np.ascontiguousarray(pos), mass
 
 
+def plummer_pv(n: int, seed: int = 1, a: float = 1.0, rmax: float = 100.0):
+    """Plummer sphere in equilibrium, G = M = 1: (pos [n,3], vel [n,3], mass [n]).
+
+    Positions as ``plummer``; each speed is q times the local escape speed
+    sqrt(2) (r^2 + a^2)^(-1/4), with q drawn from the speed law of the
+    isotropic distribution function, g(q) ~ q^2 (1 - q^2)^(7/2), by rejection
+    (g < 0.1 on [0, 1]); directions isotropic; total momentum removed.
+    """
+    pos, mass = plummer(n, seed=seed, a=a, rmax=rmax)
+    r2 = np.einsum("ij,ij->i", pos, pos)
+    vesc = np.sqrt(2.0) * np.power(r2 + a * a, -0.25)
+    q = np.empty(n)
+    todo = np.arange(n)
+    rng = _rng(seed + 1_000_003)
+    while todo.size:
+        x = rng.random(todo.size)
+        y = 0.1 * rng.random(todo.size)
+        ok = y < x * x * np.power(1.0 - x * x, 3.5)
+        q[todo[ok]] = x[ok]
+        todo = todo[~ok]
+    vel = _isotropic(rng, n) * (q * vesc)[:, None]
+    vel -= np.average(vel, axis=0, weights=mass)  # zero total momentum
+    return pos, np.ascontiguousarray(vel), mass
+
+
 def clustered(n: int = 4_194_304, n_clusters: int = 64, seed: int = 3,
               rs_min: float = 0.01, rs_max: float = 0.1, trunc: float = 20.0):
     """Sum of Plummer spheres; masses 1/N so each sphere weighs its share."""
