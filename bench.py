@@ -160,8 +160,10 @@ def measured_traffic(a):
         return None
 
 
-def cpu_baseline(pos, m, a, budget_s):
-    """Oracle timed on all host cores: full tree build + forces on a group sample."""
+def cpu_baseline(pos, m, a, budget_s, acc=None):
+    """Oracle timed on all host cores: full tree build + forces on a group sample.
+    With the kernel's accelerations (acc, input order) it also reports their
+    relative RMS deviation from the oracle's FP64 forces on that sample."""
     import oracle as O
     threads = O.default_threads()
     t0 = time.perf_counter()
@@ -177,27 +179,27 @@ def cpu_baseline(pos, m, a, budget_s):
     gs = np.sort(rng.choice(R.n_groups, size=ng, replace=False))
     npart = int(R.count[R.groups[gs]].sum())
     t0 = time.perf_counter()
-    R.forces(a.eps, a.theta, groups=gs, nthreads=threads, counts=False)
+    ra, _, _, _, _ = R.forces(a.eps, a.theta, groups=gs, nthreads=threads, counts=False)
     t_forces = time.perf_counter() - t0
     t_total = t_build + t_forces * (a.n / npart)
-    return {"value": a.n / t_total, "unit": "forces/s", "cores": threads, "kind": "oracle",
+    line = {"value": a.n / t_total, "unit": "forces/s", "cores": threads, "kind": "oracle",
             "sample": "full FP64 tree build (%.2fs) + forces of %d random groups (%d particles, %.2fs), "
                       "scaled to N=%d" % (t_build, ng, npart, t_forces, a.n),
-            "t_build_s": t_build, "t_forces_sample_s": t_forces}, R
+            "t_build_s": t_build, "t_forces_sample_s": t_forces}
+    if acc is not None:
+        idx = np.concatenate([R.cell_members(int(R.groups[g])) for g in gs])
+        line["kernel_vs_oracle_rel_rms"] = O.rel_rms(acc[idx], ra[idx])
+        line["kernel_vs_oracle_particles"] = int(len(idx))
+    return line
 
 
-def accuracy(acc, pos, m, a, R):
-    import oracle as O
-    gsel = np.unique(W.sample_indices(R.n_groups, 200, seed=9))
-    ra, _, _, _, _ = R.forces(a.eps, a.theta, groups=gsel, counts=False)
-    idx = np.concatenate([R.cell_members(int(R.groups[g])) for g in gsel])
-    rms = O.rel_rms(acc[idx], ra[idx])
+def accuracy(G, acc, pos, m, a):
+    """Delta a/a of the kernel against FP64 direct sums (on the GPU) at 1024 sampled particles."""
     samp = W.sample_indices(a.n, 1024, seed=17)
-    ad, _ = O.direct(pos, m, a.eps, targets=samp)
-    e = O.rel_err(acc[samp], ad)
-    return {"rel_rms_vs_fp64_oracle": rms, "oracle_particles": int(len(idx)),
-            "median_rel_err_vs_direct": float(np.median(e)), "p99_rel_err_vs_direct": float(np.percentile(e, 99)),
-            "direct_sample": int(len(samp))}
+    ad, _ = G.direct(pos, m, a.eps, targets=samp)
+    e = G.rel_err(acc[samp], ad)
+    return {"median_rel_err_vs_direct": float(np.median(e)), "p99_rel_err_vs_direct": float(np.percentile(e, 99)),
+            "direct_sample": int(len(samp)), "direct": "FP64 direct summation on the GPU (octgrav_direct)"}
 
 
 def time_kernel(torch, launch, flush, steps, stream):
@@ -220,15 +222,14 @@ def device_acc(torch, T, out, n):
     return acc
 
 
-def theta_for_median(torch, T, out, eps, samp, ad, target=1e-3, lo=0.5, hi=2.5, iters=9):
+def theta_for_median(torch, G, T, out, eps, samp, ad, target=1e-3, lo=0.5, hi=2.5, iters=9):
     """Bisect theta so that the median Delta a/a over the sampled particles hits target."""
-    import oracle as O
 
     def med(th):
         T.forces_device(eps, th, out)
         torch.cuda.synchronize()
         acc = device_acc(torch, T, out, T.n)
-        return float(np.median(O.rel_err(acc[samp], ad)))
+        return float(np.median(G.rel_err(acc[samp], ad)))
     m_lo, m_hi = med(lo), med(hi)
     if not (m_lo < target < m_hi):
         return None, None
@@ -243,7 +244,6 @@ def theta_for_median(torch, T, out, eps, samp, ad, target=1e-3, lo=0.5, hi=2.5, 
 
 
 def extras(torch, G, a, pos, m, T, out, flush, stream, peak, steps):
-    import oracle as O
     res = {}
     # tree build: the host FP64 build against the same tree built on the GPU
     xd = torch.from_numpy(np.ascontiguousarray(pos)).cuda()
@@ -288,8 +288,8 @@ def extras(torch, G, a, pos, m, T, out, flush, stream, peak, steps):
                                 "flops_per_particle": c["flops"] / a.n}
     # C2 at the theta whose median Delta a/a vs direct summation is 1e-3
     samp = W.sample_indices(a.n, 1024, seed=17)
-    ad, _ = O.direct(pos, m, a.eps, targets=samp)
-    th, md = theta_for_median(torch, T, out, a.eps, samp, ad)
+    ad, _ = G.direct(pos, m, a.eps, targets=samp)
+    th, md = theta_for_median(torch, G, T, out, a.eps, samp, ad)
     if th is not None:
         ms = time_kernel(torch, lambda: T.forces_device(a.eps, th, out, stream=stream), flush, steps, stream)
         c = T.interaction_counts()
@@ -304,19 +304,16 @@ def extras(torch, G, a, pos, m, T, out, flush, stream, peak, steps):
     ms = time_kernel(torch, lambda: CT.forces_device(0.001, 0.5, cout, stream=stream), flush, steps, stream)
     c = CT.interaction_counts()
     cacc = device_acc(torch, CT, cout, CT.n)
-    R = O.Tree(cpos, cm, a.n_leaf, a.n_group)
-    gsel = np.unique(W.sample_indices(R.n_groups, 100, seed=9))
-    ra, _, _, _, _ = R.forces(0.001, 0.5, groups=gsel, counts=False)
-    idx = np.concatenate([R.cell_members(int(R.groups[g])) for g in gsel])
-    csamp = W.sample_indices(CT.n, 512, seed=19)
-    cad, _ = O.direct(cpos, cm, 0.001, targets=csamp)
+    csamp = W.sample_indices(CT.n, 1024, seed=19)
+    cad, _ = G.direct(cpos, cm, 0.001, targets=csamp)
+    ce = G.rel_err(cacc[csamp], cad)
     res["clustered_4M"] = {"workload": "64 Plummer spheres N=4194304 theta=0.5 eps=0.001 N_leaf=%d N_group=%d"
                                        % (a.n_leaf, a.n_group),
                            "forces_per_s": CT.n / (ms * 1e-3), "ms": ms,
                            "frac_fp32_peak": c["flops"] / ms / 1e9 / peak,
-                           "rel_rms_vs_fp64_oracle": O.rel_rms(cacc[idx], ra[idx]),
-                           "median_rel_err_vs_direct": float(np.median(O.rel_err(cacc[csamp], cad)))}
-    del CT, cout, R
+                           "median_rel_err_vs_direct": float(np.median(ce)),
+                           "p99_rel_err_vs_direct": float(np.percentile(ce, 99))}
+    del CT, cout
     # C4: 256-system ensemble, one graph-captured persistent launch, autotuned
     systems = W.ensemble(256, seed=4)
     best = G.autotune(systems, n_leaf=a.n_leaf, eps=0.01, theta=0.6, candidates=(16, 32, 64, 128, 256, 512),
@@ -333,16 +330,17 @@ def extras(torch, G, a, pos, m, T, out, flush, stream, peak, steps):
     c = ET.interaction_counts(stream=gstream)
     eacc = device_acc(torch, ET, eout, ET.n)
     errs = []
-    for s in range(0, 256, 37):
+    for s in range(0, 256, 37):  # Delta a/a against direct sums inside each sampled system
         pos_s, m_s = systems[s]
-        ra, _, _, _, _ = O.Tree(pos_s, m_s, a.n_leaf, best["n_group"]).forces(0.01, 0.6, counts=False)
-        errs.append(O.rel_rms(eacc[ET.offsets[s]:ET.offsets[s + 1]], ra))
+        sa = W.sample_indices(len(m_s), 256, seed=s)
+        ds, _ = G.direct(pos_s, m_s, 0.01, targets=sa)
+        errs.append(float(np.median(G.rel_err(eacc[ET.offsets[s]:ET.offsets[s + 1]][sa], ds))))
     res["ensemble_256"] = {"workload": "256 Plummer systems, N log-uniform in [1024, 65536], total N=%d, theta=0.6 "
                                        "eps=0.01 N_leaf=%d" % (ET.n, a.n_leaf),
                            "autotuned": best, "launch": "CUDA graph replay of one persistent launch",
                            "forces_per_s": ET.n / (ms * 1e-3), "ms": ms,
                            "frac_fp32_peak": c["flops"] / ms / 1e9 / peak,
-                           "max_rel_rms_vs_fp64_oracle_7_systems": max(errs)}
+                           "median_rel_err_vs_direct_7_systems": errs}
     res["learned_criterion_sphere_disc_1M"] = learned_leg(torch, G, a, flush, stream, peak, steps)
     return res
 
@@ -350,7 +348,6 @@ def extras(torch, G, a, pos, m, T, out, flush, stream, peak, steps):
 def learned_leg(torch, G, a, flush, stream, peak, steps):
     """C5: sphere + disc, N = 1,048,576; the plain theta walk and the learned
     criterion, each tuned to a median Delta a/a of 1e-3 against direct sums."""
-    import oracle as O
     n = 1_048_576
     band = dict(theta_lo=0.8, theta_hi=1.3, theta_fb=1.0)
     t0 = time.perf_counter()
@@ -365,12 +362,12 @@ def learned_leg(torch, G, a, flush, stream, peak, steps):
     T = G.Tree.build(pos, m, a.n_leaf, 64)
     out = torch.empty((n, 4), dtype=torch.float32, device="cuda")
     samp = W.sample_indices(n, 1024, seed=23)
-    ad, _ = O.direct(pos, m, 0.01, targets=samp)
+    ad, _ = G.direct(pos, m, 0.01, targets=samp)
 
     def med(theta):
         T.forces_device(0.01, theta, out, stream=stream)
         torch.cuda.synchronize()
-        return float(np.median(O.rel_err(device_acc(torch, T, out, n)[samp], ad)))
+        return float(np.median(G.rel_err(device_acc(torch, T, out, n)[samp], ad)))
 
     def bisect(fn, lo, hi, iters=10):
         for _ in range(iters):
@@ -618,18 +615,12 @@ def main():
         "wall_s_timed_loop_incl_flush": wall,
         "tree": s,
     }
+    acc = np.empty((a.n, 3))
+    acc[T.perm()] = out.cpu().numpy()[:, :3]
+    if not a.no_cpu_baseline and rank == 0:
+        line["cpu_baseline"] = cpu_baseline(pos, m, a, a.cpu_seconds, acc)
     if not a.no_accuracy:
-        acc = np.empty((a.n, 3))
-        perm = T.perm()
-        acc[perm] = out.cpu().numpy()[:, :3]
-        import oracle as O  # noqa: F401
-        R = None
-        if not a.no_cpu_baseline:
-            line["cpu_baseline"], R = cpu_baseline(pos, m, a, a.cpu_seconds)
-        if R is None:
-            import oracle as O
-            R = O.Tree(pos, m, a.n_leaf, a.n_group)
-        line["accuracy"] = accuracy(acc, pos, m, a, R)
+        line["accuracy"] = accuracy(G, acc, pos, m, a)
     if not a.no_extras:
         line["extras"] = extras(torch, G, a, pos, m, T, out, flush, stream, peak, min(a.steps, 10))
     print(json.dumps(line), flush=True)

@@ -160,6 +160,16 @@ int octgrav_forces_tree_device64(octgrav_tree *t, double eps, double theta, doub
 int octgrav_forces_gpu(const double *pos, const double *mass, int64_t n, double eps, double theta,
                        double G, int n_leaf, int n_group, double *acc, double *pot, void *stream);
 
+/* Direct Plummer-softened summation in FP64 on the GPU at nt target
+ * particles (the exact reference of the error measure Delta a / a, Sec. 3.1):
+ * targets[k] indexes pos/mass (HOST arrays, n particles); NULL targets means
+ * the first nt particles. acc (nt x 3) and pot (nt) are HOST outputs; the
+ * self term is excluded; eps >= 0. O(n * nt) work, deterministic order.
+ * Returns after the copies. Errors: ERR_ARG (NULL, n < 1, nt < 0, target
+ * out of range, bad eps/G), ERR_OOM, ERR_CUDA. */
+int octgrav_direct(const double *pos, const double *mass, int64_t n, const int64_t *targets,
+                   int64_t nt, double eps, double G, double *acc, double *pot, void *stream);
+
 /* ---- Time integration on the device.
  *
  * The paper integrates on the host and does not name its scheme; this is the

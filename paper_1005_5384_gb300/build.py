@@ -57,6 +57,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     mo = os.path.join(BUILD, "octgrav_mlp.o")
     bo = os.path.join(BUILD, "octgrav_build.o")
     so = os.path.join(BUILD, "octgrav_sim.o")
+    do = os.path.join(BUILD, "octgrav_direct.o")
     ho = os.path.join(BUILD, "octgrav_host.o")
 
     def nv(src, obj, *extra):
@@ -67,10 +68,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
     m_cmd = nv("octgrav_mlp.cu", mo)
     b_cmd = nv("octgrav_build.cu", bo, "-fmad=false")
     s_cmd = nv("octgrav_sim.cu", so, "-fmad=false")
+    d_cmd = nv("octgrav_direct.cu", do)
     h_cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-fno-fast-math", "-pthread",
              "-I", os.path.join(cuda, "include"), "-I", INCLUDE,
              "-c", os.path.join(CSRC, "octgrav_host.cpp"), "-o", ho]
-    cmds = (k_cmd, m_cmd, b_cmd, s_cmd, h_cmd)
+    cmds = (k_cmd, m_cmd, b_cmd, s_cmd, d_cmd, h_cmd)
     procs = [subprocess.Popen(c, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True) for c in cmds]
     outs = [p.communicate()[0] for p in procs]
     for p, o, c in zip(procs, outs, cmds):
@@ -79,7 +81,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if verbose and o:
             print(o)
     tmp = LIB + ".%d.tmp" % os.getpid()
-    link = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, ko, mo, bo, so, ho, "-lpthread"]
+    link = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, ko, mo, bo, so, do, ho, "-lpthread"]
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed: %s\n%s" % (" ".join(link), r.stdout))

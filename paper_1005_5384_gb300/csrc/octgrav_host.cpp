@@ -1289,6 +1289,36 @@ int octgrav_forces_gpu(const double* pos, const double* mass, int64_t n, double 
   return rc;
 }
 
+int octgrav_direct(const double* pos, const double* mass, int64_t n, const int64_t* targets, int64_t nt,
+                   double eps, double G, double* acc, double* pot, void* stream) {
+  if (!pos || !mass || !acc || !pot || n < 1 || nt < 0) return fail(OCTGRAV_ERR_ARG, "bad argument");
+  if (!(eps >= 0) || !std::isfinite(eps) || !std::isfinite(G)) return fail(OCTGRAV_ERR_ARG, "need finite eps >= 0, G");
+  if (!targets && nt > n) return fail(OCTGRAV_ERR_ARG, "nt > n without targets");
+  if (targets)
+    for (int64_t k = 0; k < nt; ++k)
+      if (targets[k] < 0 || targets[k] >= n) return fail(OCTGRAV_ERR_ARG, "target %lld out of range", (long long)k);
+  if (nt == 0) return OCTGRAV_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  DevBuf dp, dm, dt, dpart, da, dpot;
+  int rc;
+  if ((rc = dp.reserve(24 * n)) || (rc = dm.reserve(8 * n)) || (rc = dt.reserve(targets ? 8 * nt : 8)) ||
+      (rc = dpart.reserve(32 * og::direct_chunks(n) * nt)) || (rc = da.reserve(24 * nt)) || (rc = dpot.reserve(8 * nt)))
+    return rc;
+  CUDA_TRY(cudaMemcpyAsync(dp.p, pos, 24 * n, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(dm.p, mass, 8 * n, cudaMemcpyHostToDevice, st));
+  if (targets) CUDA_TRY(cudaMemcpyAsync(dt.p, targets, 8 * nt, cudaMemcpyHostToDevice, st));
+  cudaError_t e = og::direct_sum(static_cast<const double*>(dp.p), static_cast<const double*>(dm.p), n,
+                                 targets ? static_cast<const int64_t*>(dt.p) : nullptr, nt, eps, G,
+                                 static_cast<double*>(dpart.p), static_cast<double*>(da.p),
+                                 static_cast<double*>(dpot.p), st);
+  if (e != cudaSuccess) return fail(OCTGRAV_ERR_CUDA, "direct-sum launch failed: %s", cudaGetErrorString(e));
+  CUDA_TRY(cudaMemcpyAsync(acc, da.p, 24 * nt, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(pot, dpot.p, 8 * nt, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  for (DevBuf* b : {&dp, &dm, &dt, &dpart, &da, &dpot}) b->release();
+  return OCTGRAV_OK;
+}
+
 // ---- time integration
 
 namespace {

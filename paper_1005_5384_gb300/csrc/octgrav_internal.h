@@ -188,4 +188,14 @@ cudaError_t sim_kick_drift(double* x, double* v, const double* a, int64_t n, dou
 cudaError_t sim_energy_partials(const double* v, const double* m, const double* pot, int64_t n, double* part,
                                 cudaStream_t stream);
 
+// ---- direct summation (octgrav_direct.cu)
+
+// Source chunks of a direct sum over n sources (the partial-sum buffer holds
+// 4 * chunks * nt doubles).
+int64_t direct_chunks(int64_t n);
+// FP64 direct sum at nt targets (indices into pos/mass, or the first nt
+// particles when targets is NULL): acc (nt x 3), pot (nt), self excluded.
+cudaError_t direct_sum(const double* pos, const double* mass, int64_t n, const int64_t* targets, int64_t nt,
+                       double eps, double G, double* part, double* acc, double* pot, cudaStream_t stream);
+
 }  // namespace og

@@ -57,6 +57,7 @@ _SIGS = {
     "octgrav_sim_energy": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double), _vp]),
     "octgrav_sim_state": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "octgrav_sim_free": (None, [_vp]),
+    "octgrav_direct": (C.c_int, [_vp, _vp, C.c_int64, _vp, C.c_int64, C.c_double, C.c_double, _vp, _vp, _vp]),
     "octgrav_status": (C.c_int, [_vp, _vp]),
     "octgrav_tree_stats": (C.c_int, [_vp, _i64, C.c_int]),
     "octgrav_tree_perm": (C.c_int, [_vp, _i64]),
@@ -399,6 +400,29 @@ def forces_gpu(pos, mass, eps: float, theta: float, n_leaf: int = 16, n_group: i
                                   int(n_group if n_group is not None else n_leaf), _p(acc), _p(pot),
                                   _stream_handle(stream)))
     return acc, pot
+
+
+def direct(pos, mass, eps: float, G: float = 1.0, targets=None, stream=None):
+    """FP64 direct summation on the GPU at ``targets`` (all particles when
+    None): (acc [nt,3], pot [nt]); the reference of the error measurements."""
+    lib = load()
+    pos, mass = _pm(pos, mass)
+    n = mass.shape[0]
+    if targets is None:
+        t, nt = None, n
+    else:
+        t = np.ascontiguousarray(targets, dtype=np.int64)
+        nt = t.shape[0]
+    acc = np.zeros((nt, 3))
+    pot = np.zeros(nt)
+    _check(lib.octgrav_direct(_p(pos), _p(mass), n, _p(t), nt, float(eps), float(G), _p(acc), _p(pot),
+                              _stream_handle(stream)))
+    return acc, pot
+
+
+def rel_err(a, a_ref):
+    """Per-particle |a - a_ref| / |a_ref| (the paper's Delta a / a)."""
+    return np.linalg.norm(np.asarray(a) - a_ref, axis=1) / np.linalg.norm(a_ref, axis=1)
 
 
 class Sim:
