@@ -62,10 +62,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the theta scan, clustered and ensemble legs")
-    ap.add_argument("--leg", default="", choices=["", "learned", "build"],
+    ap.add_argument("--sweep-n", default="30000,100000,300000,1000000",
+                    help="particle numbers of --leg accuracy (comma separated)")
+    ap.add_argument("--leg", default="", choices=["", "learned", "build", "accuracy"],
                     help="learned: train the criterion on the 1M sphere+disc and launch the learned walk "
                          "twice (a small driver for profilers; prints the interaction counts); build: "
-                         "--warmup + --steps GPU tree builds of the workload (prints their wall times)")
+                         "--warmup + --steps GPU tree builds of the workload (prints their wall times); "
+                         "accuracy: error distribution and throughput over theta, N and N_leaf on the "
+                         "galaxy stand-in (one JSON line per configuration, then the fitted theta slopes)")
     return ap.parse_args()
 
 
@@ -443,6 +447,62 @@ def run_build_driver(a):
     print(json.dumps({"leg": "build", "n": a.n, "n_group": ng, "ms": ms}), flush=True)
 
 
+def run_accuracy_driver(a):
+    """The paper's accuracy study (Sec. 3.1): Delta a/a of the tree against FP64
+    direct sums at 1024 sampled particles, for theta = 0.2 ... 0.7, several N
+    and N_leaf in {8, 16, 64} (N_group = max(64, N_leaf), the paper's 64), on
+    the galaxy stand-in (bulge : disc : halo = 1 : 1 : 4), eps = 0.01; the
+    kernel time is the median of 3 CUDA-event timings (no L2 flush)."""
+    import torch
+    from paper_1005_5384_gb300 import octgrav as G
+    G.load()
+    thetas = (0.2, 0.3, 0.4, 0.5, 0.6, 0.7)
+    eps = 0.01
+    peak, _, _ = fp32_peak_tflops(torch)
+    fits = []
+    for n in (int(v) for v in a.sweep_n.split(",")):
+        pos, m = W.galaxy(n, seed=9)
+        samp = W.sample_indices(n, 1024, seed=31)
+        ad, _ = G.direct(pos, m, eps, targets=samp)
+        xd = torch.from_numpy(pos).cuda()
+        md = torch.from_numpy(m).cuda()
+        for nl in (8, 16, 64):
+            ng = max(64, nl)
+            T = G.Tree.build_gpu(xd, md, nl, ng)
+            perm = T.perm()
+            out = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+            meds = []
+            for th in thetas:
+                T.forces_device(eps, th, out)
+                torch.cuda.synchronize()
+                ts = []
+                for _ in range(3):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    T.forces_device(eps, th, out)
+                    e1.record()
+                    e1.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                ms = statistics.median(ts)
+                if T.status() != G.OK:
+                    raise SystemExit("device status %d" % T.status())
+                acc = np.empty((n, 3))
+                acc[perm] = out.cpu().numpy()[:, :3]
+                err = G.rel_err(acc[samp], ad)
+                c = T.interaction_counts()
+                meds.append(float(np.median(err)))
+                print(json.dumps({"n": n, "n_leaf": nl, "n_group": ng, "theta": th,
+                                  "median": float(np.median(err)), "p90": float(np.percentile(err, 90)),
+                                  "p99": float(np.percentile(err, 99)), "ms": ms, "forces_per_s": n / (ms * 1e-3),
+                                  "flops_per_particle": c["flops"] / n,
+                                  "frac_fp32_peak": c["flops"] / ms / 1e9 / peak}), flush=True)
+            slope = float(np.polyfit(np.log(thetas), np.log(meds), 1)[0])
+            fits.append({"n": n, "n_leaf": nl, "median_theta_slope": slope})
+            del T, out
+    print(json.dumps({"leg": "accuracy", "workload": "galaxy stand-in (bulge:disc:halo 1:1:4), eps=0.01",
+                      "fits": fits}), flush=True)
+
+
 def run_reference(a, rank, world):
     if rank != 0:
         return
@@ -493,6 +553,9 @@ def main():
         return
     if a.leg == "build":
         run_build_driver(a)
+        return
+    if a.leg == "accuracy":
+        run_accuracy_driver(a)
         return
 
     import torch

@@ -145,6 +145,39 @@ def sphere_disc(n: int = 1_048_576, seed: int = 5, r_sphere: float = 1.0,
     return pos, np.full(n, 1.0 / n)
 
 
+def _hernquist_radii(rng: np.random.Generator, n: int, a: float, rmax: float) -> np.ndarray:
+    # M(<r) / M = r^2 / (r + a)^2  =>  r = a sqrt(u) / (1 - sqrt(u)), truncated at rmax
+    umax = (rmax / (rmax + a)) ** 2
+    s = np.sqrt(rng.random(n) * umax)
+    return a * s / (1.0 - s)
+
+
+def galaxy(n: int, seed: int = 9, r_d: float = 1.0, z_d: float = 0.1, a_bulge: float = 0.2,
+           a_halo: float = 6.0):
+    """Disc galaxy stand-in with bulge : disc : halo masses 1 : 1 : 4, equal-mass
+    particles (n/6, n/6, 2n/3), total mass 1: Hernquist bulge (scale a_bulge,
+    truncated at 10 a_bulge), exponential sech^2 disc (scale length r_d, height
+    z_d), Hernquist halo (scale a_halo, truncated at 10 a_halo). Returns
+    (pos [n,3], mass [n])."""
+    rng = _rng(seed)
+    nb = n // 6
+    nd = n // 6
+    nh = n - nb - nd
+    rb = _hernquist_radii(rng, nb, a_bulge, 10 * a_bulge)
+    bulge = _isotropic(rng, nb) * rb[:, None]
+    u1 = rng.random(nd)
+    u2 = rng.random(nd)
+    R = -r_d * (np.log1p(-u1) + np.log1p(-u2))
+    phi = 2.0 * math.pi * rng.random(nd)
+    uz = np.clip(rng.random(nd), 1e-15, 1.0 - 1e-15)
+    z = z_d * np.arctanh(2.0 * uz - 1.0)
+    disc = np.stack([R * np.cos(phi), R * np.sin(phi), z], axis=1)
+    rh = _hernquist_radii(rng, nh, a_halo, 10 * a_halo)
+    halo = _isotropic(rng, nh) * rh[:, None]
+    pos = np.ascontiguousarray(np.concatenate([bulge, disc, halo], axis=0))
+    return pos, np.full(n, 1.0 / n)
+
+
 def uniform_cube(n: int, seed: int = 7, side: float = 1.0):
     rng = _rng(seed)
     pos = np.ascontiguousarray(rng.random((n, 3)) * side)

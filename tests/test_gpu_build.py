@@ -69,6 +69,7 @@ CASES = {
     "coincident_100": (lambda: _coincident(100), 4, 8, 0.01),
     "ragged_37": (lambda: W.plummer(37, seed=7), 4, 8, 0.01),
     "chunk_edges_8193": (lambda: W.plummer(8193, seed=8), 16, 32, 0.01),
+    "galaxy_60k": (lambda: W.galaxy(60000, seed=9), 16, 64, 0.01),
 }
 
 
@@ -92,6 +93,16 @@ def test_gpu_built_tree_matches_oracle(torch):
     k = T.cell_keys()
     assert np.array_equal(np.sort(k), np.sort(R.key))
     acc, pot = T.forces(0.01, 0.5)
+    ra, rp, _, _, _ = R.forces(0.01, 0.5)
+    assert O.rel_rms(acc, ra) <= 1e-5
+    assert np.linalg.norm(pot - rp) / np.linalg.norm(rp) <= 1e-5
+
+
+def test_galaxy_forces_match_oracle(torch):
+    pos, m = W.galaxy(30000, seed=10)
+    T = G.Tree.build_gpu(pos, m, 16, 64)
+    acc, pot = T.forces(0.01, 0.5)
+    R = O.Tree(pos, m, 16, 64)
     ra, rp, _, _, _ = R.forces(0.01, 0.5)
     assert O.rel_rms(acc, ra) <= 1e-5
     assert np.linalg.norm(pot - rp) / np.linalg.norm(rp) <= 1e-5
