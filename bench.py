@@ -38,6 +38,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_1005_5384_gb300 import ranks as RK  # noqa: E402
 from paper_1005_5384_gb300 import workloads as W  # noqa: E402
 
 METRIC = "particle forces/sec and GFLOP/s (frac of FP32 peak) at N=1M θ=0.5, at median rel err 1e-3"
@@ -569,7 +570,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    pos, m = W.plummer(a.n, seed=a.seed + rank)
+    pos, m = W.plummer(a.n, seed=RK.rank_seed(a.seed, rank))
     G.load()
     tuned = None
     if a.n_group <= 0 or a.ppl <= 0:
@@ -610,16 +611,13 @@ def main():
         dist.barrier()
     clk = clocks.stop()
     ms = [s.elapsed_time(e) for s, e in ev]
-    ms_step = statistics.mean(ms)
-    if dist:
-        tt = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_step = float(tt.item())
+    ms_local = statistics.mean(ms)
+    ms_step = RK.max_over_ranks(dist, ms_local, device="cuda")  # the slowest rank
     st = T.status()
     if st != G.OK:
         raise SystemExit("device status %d after timing" % st)
 
-    value = world * a.n / (ms_step * 1e-3)
+    value = RK.job_rate(dist, a.n, ms_local * 1e-3, device="cuda")  # all ranks' particles / slowest time
     peak, sms, mhz = fp32_peak_tflops(torch)
     achieved = counts["flops"] / (ms_step * 1e-3) / 1e12
 
