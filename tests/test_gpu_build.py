@@ -122,6 +122,17 @@ def test_batch_gpu_build_equals_host_batch(torch):
     assert np.array_equal(_bits(fa), _bits(fb))
 
 
+def test_ensemble_gpu_build_equals_host_batch(torch):
+    systems = W.ensemble(256, seed=4)
+    A = G.Tree.build_batch(systems, 16, 64)
+    pos = np.concatenate([p for p, _ in systems])
+    m = np.concatenate([q for _, q in systems])
+    off = np.concatenate([[0], np.cumsum([len(q) for _, q in systems])])
+    B = G.Tree.build_gpu(pos, m, 16, 64, offsets=off)
+    _assert_same_tree(A, B)
+    assert np.array_equal(_bits(_device_forces(torch, A, 0.01, 0.6)), _bits(_device_forces(torch, B, 0.01, 0.6)))
+
+
 def test_cell_capacity_grows(torch, monkeypatch):
     pos, m = W.plummer(60000, seed=12)
     monkeypatch.setenv("OCTGRAV_GPU_CELL_CAP", "64")
