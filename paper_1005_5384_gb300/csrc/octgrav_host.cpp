@@ -526,12 +526,13 @@ struct Device {
   DevBuf parts, geo, link, mp, items, ibox, sysp, out, counts, ctl, dbg, mlp;
   // GPU build: tree arrays beyond the walk's, scratch, inputs and FP64 outputs
   DevBuf perm, key, props, pcount, cfirst, groups, ikey, celloff, result, scratch, in_pos, in_mass, acc64, pot64;
+  DevBuf order;  // work-item processing order (octgrav_balance)
   int device = -1;
   int64_t cell_cap = 0;  // cell capacity that last sufficed for a GPU build
   void release() {
     for (DevBuf* b : {&parts, &geo, &link, &mp, &items, &ibox, &sysp, &out, &counts, &ctl, &dbg, &mlp, &perm, &key,
                       &props, &pcount, &cfirst, &groups, &ikey, &celloff, &result, &scratch, &in_pos, &in_mass,
-                      &acc64, &pot64})
+                      &acc64, &pot64, &order})
       b->release();
     cell_cap = 0;
   }
@@ -581,6 +582,7 @@ struct octgrav_tree {
   bool host_valid = true;
   bool perm_on_device = false;  // Device::perm holds the permutation (int32)
   int64_t n_groups = 0, n_items = 0;
+  bool ordered = false;  // launches take the work items in Device::order (octgrav_balance)
   int64_t cell_cap = 0;  // cell capacity of the device arrays of a GPU-built tree
   cudaGraphExec_t gexec = nullptr;  // captured memset + kernel (octgrav_graph_capture)
   std::vector<SysTree> sys_scratch;
@@ -862,6 +864,7 @@ og::KParams make_params(octgrav_tree* t, float4* out) {
   p.work = reinterpret_cast<unsigned*>(static_cast<char*>(D.ctl.p) + 4);
   p.n_items = static_cast<int>(t->n_items);
   p.n_cells = static_cast<int>(t->n_cells);
+  p.order = t->ordered ? static_cast<const int*>(D.order.p) : nullptr;
   p.stage = t->stage;
   p.mp_map = t->mp_map;
   p.n_group = t->n_group;
@@ -1535,6 +1538,36 @@ int octgrav_debug_lists(octgrav_tree* t, double theta, int cap, uint64_t* cell_k
   return OCTGRAV_OK;
 }
 
+int octgrav_balance(octgrav_tree* t, int mode, void* stream) {
+  if (!t || mode < 0 || mode > 1) return fail(OCTGRAV_ERR_ARG, "NULL tree or mode not 0/1");
+  if (mode == 0) {
+    t->ordered = false;
+    return OCTGRAV_OK;
+  }
+  if (!t->launched) return fail(OCTGRAV_ERR_STATE, "no launch on this tree yet");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t ni = t->n_items;
+  std::vector<int2> c(ni);
+  std::vector<int4> it(ni);
+  if (ni) {
+    CUDA_TRY(cudaMemcpyAsync(c.data(), t->dev->counts.p, sizeof(int2) * ni, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(it.data(), t->dev->items.p, sizeof(int4) * ni, cudaMemcpyDeviceToHost, st));
+  }
+  CUDA_TRY(cudaStreamSynchronize(st));
+  // cost of an item: its particles times the flops of its lists
+  std::vector<double> cost(ni);
+  for (int64_t k = 0; k < ni; ++k) cost[k] = static_cast<double>(it[k].z) * (70.0 * c[k].x + 38.0 * (c[k].y - 1));
+  std::vector<int32_t> order(ni);
+  for (int64_t k = 0; k < ni; ++k) order[k] = static_cast<int32_t>(k);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
+  int rc = t->dev->order.reserve(4 * std::max<int64_t>(1, ni));
+  if (rc) return rc;
+  if (ni) CUDA_TRY(cudaMemcpyAsync(t->dev->order.p, order.data(), 4 * ni, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  t->ordered = true;
+  return OCTGRAV_OK;
+}
+
 int octgrav_set_launch(octgrav_tree* t, int particles_per_lane, int ctas_per_sm) {
   if (!t) return fail(OCTGRAV_ERR_ARG, "tree is NULL");
   if (particles_per_lane != 1 && particles_per_lane != 2) return fail(OCTGRAV_ERR_ARG, "particles_per_lane must be 1 or 2");
@@ -1542,6 +1575,7 @@ int octgrav_set_launch(octgrav_tree* t, int particles_per_lane, int ctas_per_sm)
   t->ctas_per_sm = ctas_per_sm;
   if (particles_per_lane != t->ppl) {
     t->ppl = particles_per_lane;
+    t->ordered = false;  // the work items change
     if (t->gpu) {  // rebuild the work items on the device
       const og::GpuBuild a = gpu_args(t, t->sys_off.data(), nullptr, nullptr);
       cudaError_t e = og::gpu_build_items(a, nullptr);
@@ -1697,6 +1731,7 @@ int octgrav_autotune(int n_sys, const int64_t* offsets, const double* pos, const
       if ((rc = octgrav_set_launch(t, ppl, 0))) break;
       float4* out = static_cast<float4*>(outb.p);
       if ((rc = launch(t, eps, theta, 1.0, out, st, false, nullptr, nullptr, nullptr, 0))) break;
+      if ((rc = octgrav_balance(t, 1, st))) break;  // time the longest-first order
       std::vector<float> ms;
       for (int k = 0; k < 3 && rc == OCTGRAV_OK; ++k) {
         cudaEventRecord(e0, st);

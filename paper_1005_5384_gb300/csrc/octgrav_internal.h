@@ -50,6 +50,7 @@ struct KParams {
   int2* counts;          // [ni] (n_pc, n_pp sources incl. self)
   int* status;           // device status word
   unsigned* work;        // work-queue counter (zeroed before the launch)
+  const int* order;      // [ni] processing order of the work items, or nullptr for 0, 1, ...
   int n_items;
   int n_cells;
   int stage;             // STAGING_*

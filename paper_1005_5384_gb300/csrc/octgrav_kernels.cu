@@ -417,7 +417,10 @@ __global__ void __launch_bounds__(CtaWarps<MLP>::v * 32, MLP ? 1 : 2) walk_eval_
 
   for (;;) {
     int item = 0;
-    if (lane == 0) item = static_cast<int>(atomicAdd(p.work, 1u));
+    if (lane == 0) {
+      item = static_cast<int>(atomicAdd(p.work, 1u));
+      if (p.order && item < p.n_items) item = __ldg(p.order + item);  // longest first
+    }
     item = __shfl_sync(FULL, item, 0);
     if (item >= p.n_items) break;
 

@@ -67,6 +67,7 @@ _SIGS = {
     "octgrav_interaction_counts": (C.c_int, [_vp, _i64, _vp]),
     "octgrav_debug_lists": (C.c_int, [_vp, C.c_double, C.c_int, _vp, _vp, _vp, _vp, _vp]),
     "octgrav_set_launch": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "octgrav_balance": (C.c_int, [_vp, C.c_int, _vp]),
     "octgrav_set_staging": (C.c_int, [_vp, C.c_int]),
     "octgrav_mlp_samples": (C.c_int, [_vp, _i64, C.c_int64, C.c_double, C.c_double, _vp, _vp, _vp, C.c_int64,
                                       C.POINTER(C.c_int64), _vp]),
@@ -252,6 +253,10 @@ class Tree:
     def set_launch(self, particles_per_lane: int = 2, ctas_per_sm: int = 0):
         _check(load().octgrav_set_launch(self._h, int(particles_per_lane), int(ctas_per_sm)))
         self.stats = self._stats()
+
+    def balance(self, mode: int = 1, stream=None):
+        """Longest-first work-item order from the last launch's costs (1) or tree order (0)."""
+        _check(load().octgrav_balance(self._h, int(mode), _stream_handle(stream)))
 
     def set_staging(self, mode: int):
         """0 = cp.async.bulk per record, 1 = 16-byte cp.async (default), 2 = TMA gather4."""

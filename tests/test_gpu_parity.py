@@ -190,3 +190,29 @@ def test_staging_modes_agree_bitwise(_cuda, stage):
     for k in range(0, len(gl), 5):
         rc, rl = R.list_keys(okey[int(info["group_key"][k])], 0.6)
         assert np.array_equal(gl[k][0], rc) and np.array_equal(gl[k][1], rl)
+
+
+def test_longest_first_order_changes_nothing_but_the_order(_cuda):
+    torch = _cuda
+    pos, m = W.plummer(60000, seed=12)
+    T = G.Tree.build(pos, m, 16, 128)
+    out = torch.empty((T.n, 4), dtype=torch.float32, device="cuda")
+    with pytest.raises(G.OctgravError) as e:
+        T.balance()
+    assert e.value.code == G.ERR_STATE
+    T.forces_device(0.01, 0.5, out)
+    torch.cuda.synchronize()
+    ref = out.cpu().numpy().copy()
+    c0 = T.interaction_counts()
+    T.balance()
+    out.zero_()
+    T.forces_device(0.01, 0.5, out)
+    torch.cuda.synchronize()
+    assert T.status() == G.OK
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), ref.view(np.uint32))
+    assert T.interaction_counts() == c0
+    T.set_launch(1)  # new work items: the order is dropped, results still right
+    T.forces_device(0.01, 0.5, out)
+    torch.cuda.synchronize()
+    assert T.status() == G.OK
+    T.balance(0)
