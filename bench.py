@@ -64,7 +64,8 @@ def parse():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the theta scan, clustered and ensemble legs")
     ap.add_argument("--no-balance", action="store_true",
-                    help="keep tree order for the work items (no longest-first order from the warm-up launch)")
+                    help="keep the default work-item order (most particles first) instead of longest first "
+                         "by the costs of the first warm-up launch")
     ap.add_argument("--sweep-n", default="30000,100000,300000,1000000",
                     help="particle numbers of --leg accuracy (comma separated)")
     ap.add_argument("--leg", default="", choices=["", "learned", "build", "accuracy", "pipes"],
@@ -685,7 +686,7 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload_name(a), "seed": a.seed, "particles_per_lane": a.ppl,
                    "autotuner": tuned,
-                   "item_order": "tree order" if a.no_balance else
+                   "item_order": "most particles first (default)" if a.no_balance else
                    "longest first, from the interaction counts of the first warm-up launch (octgrav_balance)",
                    "l2": "flushed (256 MiB write) before every timed step, outside the events",
                    "parallelism": "replica per GPU" if world > 1 else "1 GPU"},

@@ -252,14 +252,15 @@ int octgrav_interaction_counts(octgrav_tree *t, int64_t *out, void *stream);
 int octgrav_debug_lists(octgrav_tree *t, double theta, int cap, uint64_t *cell_keys,
                         int32_t *n_cell, uint64_t *leaf_keys, int32_t *n_leaf, void *stream);
 
-/* Work-item order of later launches on this tree. mode 1: longest first, by
+/* Order in which later launches on this tree take the work items (the
+ * persistent kernel's tail is shorter when the biggest items go first).
+ * Every new tree (and every octgrav_set_launch that rebuilds the items)
+ * starts with mode 2. mode 2: most particles first. mode 1: longest first by
  * the cost of each item in the last launch (its particles times 70 n_pc +
- * 38 n_pp, the interaction counts of that launch), which shortens the tail of
- * the persistent launch when the same tree is evaluated again (an N-body
- * step reusing the previous step's costs); waits for the stream. mode 0: back
- * to tree order. The order is dropped when the work items change
- * (octgrav_set_launch with another particles-per-lane). A captured graph keeps
- * the order it was captured with. Results do not depend on the order.
+ * 38 n_pp, that launch's interaction counts) -- an N-body code evaluating
+ * the same tree again, or reusing the previous step's costs. mode 0: tree
+ * order. Waits for the stream. A captured graph keeps the order it was
+ * captured with. Results do not depend on the order.
  * Errors: ERR_ARG, ERR_STATE (mode 1 before any launch), ERR_CUDA. */
 int octgrav_balance(octgrav_tree *t, int mode, void *stream);
 

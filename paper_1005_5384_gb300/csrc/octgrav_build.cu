@@ -30,6 +30,7 @@ constexpr int GL = 4096;          // blocks of the level kernels
 constexpr int GLT = 1024;         // threads of the level scan (GL / GLT entries each)
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int LBINS = 32;  // leaf size bins of the moment pass (32 = "32 or more")
+constexpr int IBINS = 256; // work-item size bins of the default processing order (item_max <= 256)
 
 struct SysGeo {  // root cube of a system: lower corner, side, 2^21 * fl(1 / side)
   double lo[3], side, rscale;
@@ -44,7 +45,7 @@ struct Chunk {  // TILE particles (or fewer) of one system
 struct Layout {
   size_t keyA, keyB, valA, valB, cnt, dtot, part, sg, xs, ms, chunks, offs, chunk0;
   size_t ckey, cpar, cpf, cpc, csys, cfc, cnc, spl, lpre, bsum, lvl, misc;
-  size_t sstart, send, lofs, ni, lorder, lhist, gmark, gidx, gcell, nitem, ioff, sblk;
+  size_t sstart, send, lofs, ni, lorder, lhist, ihist, gmark, gidx, gcell, nitem, ioff, sblk;
   size_t total;
 };
 
@@ -89,6 +90,7 @@ Layout layout(int64_t n, int n_sys, int64_t n_chunks, int64_t cap) {
   L.ni = take(n_sys > 1 ? 4 * cap : 0);
   L.lorder = take(4 * cap);
   L.lhist = take(4 * 2 * LBINS);
+  L.ihist = take(4 * 2 * IBINS);
   L.gmark = take(4 * n);
   L.gidx = take(4 * n);
   L.gcell = take(4 * n);
@@ -988,6 +990,51 @@ __global__ void k_items(const int* __restrict__ n_groups, const int* __restrict_
   }
 }
 
+// Default processing order of the work items: most particles first (a
+// counting sort on the item size; the order inside a size is arbitrary and
+// does not affect any result).
+__global__ void __launch_bounds__(TB) k_item_hist(const int* __restrict__ n_items, const int4* __restrict__ items,
+                                                  int* __restrict__ ihist) {
+  __shared__ int h[IBINS];
+  for (int k = threadIdx.x; k < IBINS; k += TB) h[k] = 0;
+  __syncthreads();
+  const int ni = *n_items;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ni; k += gridDim.x * blockDim.x)
+    atomicAdd(&h[IBINS - min(items[k].z, IBINS)], 1);
+  __syncthreads();
+  for (int k = threadIdx.x; k < IBINS; k += TB)
+    if (h[k]) atomicAdd(&ihist[k], h[k]);
+}
+
+__global__ void __launch_bounds__(TB) k_item_scatter(const int* __restrict__ n_items, const int4* __restrict__ items,
+                                                     const int* __restrict__ ihist, int* __restrict__ ifill,
+                                                     int* __restrict__ order) {
+  __shared__ int base[IBINS], h[IBINS];
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int k = 0; k < IBINS; ++k) {
+      base[k] = run;
+      run += ihist[k];
+    }
+  }
+  const int ni = *n_items;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t k0 = static_cast<int64_t>(blockIdx.x) * blockDim.x; k0 < ni; k0 += stride) {
+    for (int k = threadIdx.x; k < IBINS; k += TB) h[k] = 0;
+    __syncthreads();
+    const int k = static_cast<int>(k0) + threadIdx.x;
+    const bool live = k < ni;
+    const int b = live ? IBINS - min(items[k].z, IBINS) : 0;
+    const int r = live ? atomicAdd(&h[b], 1) : 0;
+    __syncthreads();
+    for (int q = threadIdx.x; q < IBINS; q += TB)
+      if (h[q]) h[q] = atomicAdd(&ifill[q], h[q]);
+    __syncthreads();
+    if (live) order[base[b] + h[b] + r] = k;
+    __syncthreads();
+  }
+}
+
 __global__ void k_finish(const int* __restrict__ lvl, const int* __restrict__ misc, int64_t* __restrict__ res) {
   int depth = 0;
   for (int L = 0; L < NLEV; ++L)
@@ -1034,6 +1081,11 @@ cudaError_t enqueue_items(const GpuBuild& a, const Layout& Lo, int item_max, cud
   k_scan_down<<<nb, TB, 0, st>>>(nitem, &misc[M_NGROUPS], nmax, sblk, ioff);
   k_items<<<grid_for(a.n, TB), TB, 0, st>>>(&misc[M_NGROUPS], a.group_cell, a.group_sys, ioff, a.cell_off, P,
                                             item_max, a.items, a.ibox, a.item_key, a.group_item);
+  int* ihist = at<int>(a.scratch, Lo.ihist);
+  cudaError_t e = cudaMemsetAsync(ihist, 0, 4 * 2 * IBINS, st);
+  if (e != cudaSuccess) return e;
+  k_item_hist<<<grid_for(a.n, TB), TB, 0, st>>>(&misc[M_NITEMS], a.items, ihist);
+  k_item_scatter<<<grid_for(a.n, TB), TB, 0, st>>>(&misc[M_NITEMS], a.items, ihist, ihist + IBINS, a.order);
   return cudaGetLastError();
 }
 

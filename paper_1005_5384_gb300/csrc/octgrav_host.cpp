@@ -583,6 +583,7 @@ struct octgrav_tree {
   bool perm_on_device = false;  // Device::perm holds the permutation (int32)
   int64_t n_groups = 0, n_items = 0;
   bool ordered = false;  // launches take the work items in Device::order (octgrav_balance)
+  std::vector<int32_t> item_order;  // host image of the default order (host-built trees)
   int64_t cell_cap = 0;  // cell capacity of the device arrays of a GPU-built tree
   cudaGraphExec_t gexec = nullptr;  // captured memset + kernel (octgrav_graph_capture)
   std::vector<SysTree> sys_scratch;
@@ -651,6 +652,12 @@ void make_items(octgrav_tree* t) {
   }
   t->n_groups = static_cast<int64_t>(t->group_cell.size());
   t->n_items = static_cast<int64_t>(t->items.size());
+  // default processing order: most particles first
+  t->item_order.resize(t->items.size());
+  for (size_t k = 0; k < t->items.size(); ++k) t->item_order[k] = static_cast<int32_t>(k);
+  std::stable_sort(t->item_order.begin(), t->item_order.end(),
+                   [&](int32_t a, int32_t b) { return t->items[a].z > t->items[b].z; });
+  t->ordered = true;
 }
 
 // Concatenate the systems' trees into the device-array images.
@@ -823,7 +830,8 @@ int upload(octgrav_tree* t, cudaStream_t st) {
   if (!t->gpu) {  // a GPU-built tree already lives in these arrays
     if ((rc = upload_vec(D.parts, t->parts, st)) || (rc = upload_vec(D.geo, t->geo, st)) ||
         (rc = upload_vec(D.link, t->link, st)) || (rc = upload_vec(D.mp, t->mp, st)) ||
-        (rc = upload_vec(D.items, t->items, st)) || (rc = upload_vec(D.ibox, t->ibox, st)))
+        (rc = upload_vec(D.items, t->items, st)) || (rc = upload_vec(D.ibox, t->ibox, st)) ||
+        (rc = upload_vec(D.order, t->item_order, st)))
       return rc;
     t->perm_on_device = false;
   }
@@ -1021,6 +1029,7 @@ og::GpuBuild gpu_args(octgrav_tree* t, const int64_t* offsets, const double* pos
   a.items = static_cast<int4*>(D.items.p);
   a.ibox = static_cast<float4*>(D.ibox.p);
   a.item_key = static_cast<uint64_t*>(D.ikey.p);
+  a.order = static_cast<int*>(D.order.p);
   a.cell_off = static_cast<int64_t*>(D.celloff.p);
   a.result = static_cast<int64_t*>(D.result.p);
   return a;
@@ -1032,7 +1041,7 @@ int reserve_gpu_tree(Device& D, int64_t n, int n_sys, int64_t cap) {
       (rc = D.geo.reserve(16 * cap)) || (rc = D.link.reserve(8 * cap)) || (rc = D.mp.reserve(64 * cap)) ||
       (rc = D.props.reserve(160 * cap)) || (rc = D.pcount.reserve(4 * cap)) || (rc = D.cfirst.reserve(4 * cap)) ||
       (rc = D.groups.reserve(12 * n)) || (rc = D.items.reserve(16 * n)) || (rc = D.ibox.reserve(64 * n)) ||
-      (rc = D.ikey.reserve(8 * n)) || (rc = D.celloff.reserve(8 * (n_sys + 1))) ||
+      (rc = D.ikey.reserve(8 * n)) || (rc = D.order.reserve(4 * n)) || (rc = D.celloff.reserve(8 * (n_sys + 1))) ||
       (rc = D.result.reserve(8 * og::GB_COUNT)) || (rc = D.scratch.reserve(og::gpu_build_scratch_bytes(n, n_sys, cap))))
     return rc;
   return OCTGRAV_OK;
@@ -1105,6 +1114,7 @@ int build_gpu_common(int n_sys, const int64_t* offsets, const double* pos, const
   t->depth_reached = static_cast<int>(res[og::GB_DEPTH]);
   t->n_leaves = res[og::GB_NLEAVES];
   t->max_group = res[og::GB_MAXGROUP];
+  t->ordered = true;  // the build wrote the default order (most particles first)
   t->cell_off.resize(n_sys + 1);
   CUDA_TRY(cudaMemcpy(t->cell_off.data(), D.celloff.p, 8 * (n_sys + 1), cudaMemcpyDeviceToHost));
   if ((rc = upload(t.get(), st))) return rc;  // counts, control word, tensor map
@@ -1539,24 +1549,27 @@ int octgrav_debug_lists(octgrav_tree* t, double theta, int cap, uint64_t* cell_k
 }
 
 int octgrav_balance(octgrav_tree* t, int mode, void* stream) {
-  if (!t || mode < 0 || mode > 1) return fail(OCTGRAV_ERR_ARG, "NULL tree or mode not 0/1");
+  if (!t || mode < 0 || mode > 2) return fail(OCTGRAV_ERR_ARG, "NULL tree or mode not 0/1/2");
   if (mode == 0) {
     t->ordered = false;
     return OCTGRAV_OK;
   }
-  if (!t->launched) return fail(OCTGRAV_ERR_STATE, "no launch on this tree yet");
+  if (mode == 1 && !t->launched) return fail(OCTGRAV_ERR_STATE, "no launch on this tree yet");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int64_t ni = t->n_items;
-  std::vector<int2> c(ni);
+  std::vector<int2> c(mode == 1 ? ni : 0);
   std::vector<int4> it(ni);
   if (ni) {
-    CUDA_TRY(cudaMemcpyAsync(c.data(), t->dev->counts.p, sizeof(int2) * ni, cudaMemcpyDeviceToHost, st));
+    if (mode == 1)
+      CUDA_TRY(cudaMemcpyAsync(c.data(), t->dev->counts.p, sizeof(int2) * ni, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaMemcpyAsync(it.data(), t->dev->items.p, sizeof(int4) * ni, cudaMemcpyDeviceToHost, st));
   }
   CUDA_TRY(cudaStreamSynchronize(st));
-  // cost of an item: its particles times the flops of its lists
+  // cost of an item: its particles times the flops of its lists (mode 1), or
+  // its particles alone (mode 2, no launch needed)
   std::vector<double> cost(ni);
-  for (int64_t k = 0; k < ni; ++k) cost[k] = static_cast<double>(it[k].z) * (70.0 * c[k].x + 38.0 * (c[k].y - 1));
+  for (int64_t k = 0; k < ni; ++k)
+    cost[k] = static_cast<double>(it[k].z) * (mode == 1 ? 70.0 * c[k].x + 38.0 * (c[k].y - 1) : 1.0);
   std::vector<int32_t> order(ni);
   for (int64_t k = 0; k < ni; ++k) order[k] = static_cast<int32_t>(k);
   std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
@@ -1564,6 +1577,7 @@ int octgrav_balance(octgrav_tree* t, int mode, void* stream) {
   if (rc) return rc;
   if (ni) CUDA_TRY(cudaMemcpyAsync(t->dev->order.p, order.data(), 4 * ni, cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaStreamSynchronize(st));
+  if (!t->gpu) t->item_order = order;  // a later re-upload keeps it
   t->ordered = true;
   return OCTGRAV_OK;
 }
@@ -1575,14 +1589,14 @@ int octgrav_set_launch(octgrav_tree* t, int particles_per_lane, int ctas_per_sm)
   t->ctas_per_sm = ctas_per_sm;
   if (particles_per_lane != t->ppl) {
     t->ppl = particles_per_lane;
-    t->ordered = false;  // the work items change
-    if (t->gpu) {  // rebuild the work items on the device
+    if (t->gpu) {  // items and their default order rebuilt on the device  // rebuild the work items on the device
       const og::GpuBuild a = gpu_args(t, t->sys_off.data(), nullptr, nullptr);
       cudaError_t e = og::gpu_build_items(a, nullptr);
       if (e != cudaSuccess) return fail(OCTGRAV_ERR_CUDA, "GPU item build failed: %s", cudaGetErrorString(e));
       int64_t res[og::GB_COUNT];
       if (int rc = gpu_result(t, nullptr, res)) return rc;
       t->n_items = res[og::GB_NITEMS];
+      t->ordered = true;
       t->host_valid = false;
       if (int rc = t->dev->counts.reserve(t->n_items * sizeof(int2))) return rc;
     } else {

@@ -164,6 +164,7 @@ struct GpuBuild {
   int4* items;
   float4* ibox;
   uint64_t* item_key;
+  int* order;         // [n] default processing order of the items: most particles first
   int64_t* cell_off;
   int64_t* result;
 };

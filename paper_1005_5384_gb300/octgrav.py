@@ -255,7 +255,8 @@ class Tree:
         self.stats = self._stats()
 
     def balance(self, mode: int = 1, stream=None):
-        """Longest-first work-item order from the last launch's costs (1) or tree order (0)."""
+        """Work-item order of later launches: longest first by the last launch's
+        costs (1), most particles first (2, every new tree's default) or tree order (0)."""
         _check(load().octgrav_balance(self._h, int(mode), _stream_handle(stream)))
 
     def set_staging(self, mode: int):

@@ -211,7 +211,13 @@ def test_longest_first_order_changes_nothing_but_the_order(_cuda):
     assert T.status() == G.OK
     assert np.array_equal(out.cpu().numpy().view(np.uint32), ref.view(np.uint32))
     assert T.interaction_counts() == c0
-    T.set_launch(1)  # new work items: the order is dropped, results still right
+    for mode in (0, 2):  # tree order and most-particles-first: the same bits
+        T.balance(mode)
+        out.zero_()
+        T.forces_device(0.01, 0.5, out)
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy().view(np.uint32), ref.view(np.uint32))
+    T.set_launch(1)  # new work items with their default order, results still right
     T.forces_device(0.01, 0.5, out)
     torch.cuda.synchronize()
     assert T.status() == G.OK
