@@ -1117,10 +1117,30 @@ size_t gpu_build_scratch_bytes(int64_t n, int n_sys, int64_t cap) {
   return layout(n, n_sys, chunks, cap).total;
 }
 
-cudaError_t gpu_build(const GpuBuild& a, cudaStream_t st) {
+cudaError_t gpu_build_tables(const GpuBuild& a, cudaStream_t st) {
   std::vector<int> chunk0;
   const std::vector<Chunk> ch = make_chunks(a.offsets, a.n_sys, chunk0);
-  const int nch = static_cast<int>(ch.size());
+  const Layout Lo = layout(a.n, a.n_sys, (a.n + TILE - 1) / TILE + a.n_sys, a.cap);
+  if (Lo.total > a.scratch_bytes) return cudaErrorInvalidValue;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(at<Chunk>(a.scratch, Lo.chunks), ch.data(), sizeof(Chunk) * ch.size(),
+                           cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(at<int64_t>(a.scratch, Lo.offs), a.offsets, 8 * (a.n_sys + 1), cudaMemcpyHostToDevice,
+                           st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(at<int>(a.scratch, Lo.chunk0), chunk0.data(), 4 * (a.n_sys + 1), cudaMemcpyHostToDevice,
+                           st)) != cudaSuccess)
+    return e;
+  return cudaSuccess;
+}
+
+cudaError_t gpu_build(const GpuBuild& a, cudaStream_t st) {
+  cudaError_t e = gpu_build_tables(a, st);
+  return e != cudaSuccess ? e : gpu_build_kernels(a, st);
+}
+
+cudaError_t gpu_build_kernels(const GpuBuild& a, cudaStream_t st) {
+  int nch = 0;
+  for (int s = 0; s < a.n_sys; ++s) nch += static_cast<int>((a.offsets[s + 1] - a.offsets[s] + TILE - 1) / TILE);
   const Layout Lo = layout(a.n, a.n_sys, (a.n + TILE - 1) / TILE + a.n_sys, a.cap);
   if (Lo.total > a.scratch_bytes) return cudaErrorInvalidValue;
   void* S = a.scratch;
@@ -1149,9 +1169,6 @@ cudaError_t gpu_build(const GpuBuild& a, cudaStream_t st) {
   do {                                  \
     if ((e = (x)) != cudaSuccess) return e; \
   } while (0)
-  OG_TRY(cudaMemcpyAsync(dch, ch.data(), sizeof(Chunk) * nch, cudaMemcpyHostToDevice, st));
-  OG_TRY(cudaMemcpyAsync(doffs, a.offsets, 8 * (a.n_sys + 1), cudaMemcpyHostToDevice, st));
-  OG_TRY(cudaMemcpyAsync(dchunk0, chunk0.data(), 4 * (a.n_sys + 1), cudaMemcpyHostToDevice, st));
   OG_TRY(cudaMemsetAsync(misc, 0, 4 * 16, st));
 
   // ---- keys and the stable sort (8 passes of 8 bits over the 63-bit keys)

@@ -529,7 +529,24 @@ struct Device {
   DevBuf order;  // work-item processing order (octgrav_balance)
   int device = -1;
   int64_t cell_cap = 0;  // cell capacity that last sufficed for a GPU build
+  // the GPU build's kernels captured as a graph, replayed on gstream while
+  // build_key (every argument, pointers included) stays the same
+  cudaGraphExec_t build_exec = nullptr;
+  std::vector<int64_t> build_key;
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  void release_graph() {
+    if (build_exec) cudaGraphExecDestroy(build_exec);
+    build_exec = nullptr;
+    build_key.clear();
+  }
   void release() {
+    release_graph();
+    if (gstream) cudaStreamDestroy(gstream);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    gstream = nullptr;
+    ev_in = ev_out = nullptr;
     for (DevBuf* b : {&parts, &geo, &link, &mp, &items, &ibox, &sysp, &out, &counts, &ctl, &dbg, &mlp, &perm, &key,
                       &props, &pcount, &cfirst, &groups, &ikey, &celloff, &result, &scratch, &in_pos, &in_mass,
                       &acc64, &pot64, &order})
@@ -1047,6 +1064,63 @@ int reserve_gpu_tree(Device& D, int64_t n, int n_sys, int64_t cap) {
   return OCTGRAV_OK;
 }
 
+// Every argument of a GPU build (pointers included) and the system offsets:
+// a captured build graph is valid while this stays the same.
+std::vector<int64_t> build_key(const og::GpuBuild& a) {
+  auto P = [](const void* q) { return static_cast<int64_t>(reinterpret_cast<uintptr_t>(q)); };
+  std::vector<int64_t> k = {P(a.pos),     P(a.mass),     a.n,           a.n_sys,       a.n_leaf,       a.n_group,
+                            a.item_max,   a.cap,         P(a.scratch),  static_cast<int64_t>(a.scratch_bytes),
+                            P(a.parts),   P(a.perm),     P(a.key),      P(a.geo),      P(a.link),      P(a.mp),
+                            P(a.bmin),    P(a.bmax),     P(a.cube),     P(a.M),        P(a.com),       P(a.S),
+                            P(a.pcount),  P(a.cfirst),   P(a.group_cell), P(a.group_sys), P(a.group_item),
+                            P(a.items),   P(a.ibox),     P(a.item_key), P(a.order),    P(a.cell_off),  P(a.result)};
+  k.insert(k.end(), a.offsets, a.offsets + a.n_sys + 1);
+  return k;
+}
+
+// Enqueue a GPU build on st. The kernels are captured once into a graph and
+// replayed on the device's own stream (ordered after and before st by
+// events) while the arguments stay the same: ~125 small launches become one.
+int run_build(Device& D, const og::GpuBuild& a, cudaStream_t st, bool use_graph) {
+  cudaError_t e;
+  if (!use_graph) {  // a one-off build: capturing would cost more than it saves
+    if ((e = og::gpu_build(a, st)) != cudaSuccess)
+      return fail(OCTGRAV_ERR_CUDA, "GPU build launch failed: %s", cudaGetErrorString(e));
+    return OCTGRAV_OK;
+  }
+  if (!D.gstream) {
+    CUDA_TRY(cudaStreamCreateWithFlags(&D.gstream, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&D.ev_in, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&D.ev_out, cudaEventDisableTiming));
+  }
+  std::vector<int64_t> key = build_key(a);
+  if (!D.build_exec || key != D.build_key) {
+    D.release_graph();
+    if ((e = og::gpu_build_tables(a, st)) != cudaSuccess)
+      return fail(OCTGRAV_ERR_CUDA, "GPU build tables: %s", cudaGetErrorString(e));
+    CUDA_TRY(cudaStreamBeginCapture(D.gstream, cudaStreamCaptureModeThreadLocal));
+    const cudaError_t ek = og::gpu_build_kernels(a, D.gstream);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(D.gstream, &g);
+    if (ek == cudaSuccess && e == cudaSuccess) e = cudaGraphInstantiate(&D.build_exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (ek != cudaSuccess || e != cudaSuccess) {  // not capturable here: run the kernels directly
+      D.build_exec = nullptr;
+      cudaGetLastError();
+      if ((e = og::gpu_build_kernels(a, st)) != cudaSuccess)
+        return fail(OCTGRAV_ERR_CUDA, "GPU build launch failed: %s", cudaGetErrorString(e));
+      return OCTGRAV_OK;
+    }
+    D.build_key = std::move(key);
+  }
+  CUDA_TRY(cudaEventRecord(D.ev_in, st));
+  CUDA_TRY(cudaStreamWaitEvent(D.gstream, D.ev_in, 0));
+  CUDA_TRY(cudaGraphLaunch(D.build_exec, D.gstream));
+  CUDA_TRY(cudaEventRecord(D.ev_out, D.gstream));
+  CUDA_TRY(cudaStreamWaitEvent(st, D.ev_out, 0));
+  return OCTGRAV_OK;
+}
+
 // Read the result block of a GPU build (waits for the stream).
 int gpu_result(octgrav_tree* t, cudaStream_t st, int64_t* res) {
   CUDA_TRY(cudaMemcpyAsync(res, t->dev->result.p, 8 * og::GB_COUNT, cudaMemcpyDeviceToHost, st));
@@ -1098,8 +1172,7 @@ int build_gpu_common(int n_sys, const int64_t* offsets, const double* pos, const
     if ((rc = reserve_gpu_tree(D, n, n_sys, cap))) return rc;
     t->cell_cap = cap;
     const og::GpuBuild a = gpu_args(t.get(), offsets, pos, mass);
-    cudaError_t e = og::gpu_build(a, st);
-    if (e != cudaSuccess) return fail(OCTGRAV_ERR_CUDA, "GPU build launch failed: %s", cudaGetErrorString(e));
+    if ((rc = run_build(D, a, st, dev != nullptr))) return rc;  // cached buffers: replay a graph
     if ((rc = gpu_result(t.get(), st, res))) return rc;
     if (res[og::GB_STATUS] & og::GPU_BUILD_BADINPUT)
       return fail(OCTGRAV_ERR_NONFINITE, "non-finite position/mass or negative mass");

@@ -171,8 +171,14 @@ struct GpuBuild {
 
 // Scratch bytes of a build of n particles in n_sys systems with `cap` cells.
 size_t gpu_build_scratch_bytes(int64_t n, int n_sys, int64_t cap);
-// Enqueue the whole build on `stream` (no host synchronisation inside).
+// Enqueue the whole build on `stream` (no host synchronisation inside):
+// gpu_build_tables (host-made chunk tables copied into the scratch, from
+// pageable memory) followed by gpu_build_kernels (device work only, so it can
+// be captured into a CUDA graph and replayed while the tables and buffers
+// stay the same).
 cudaError_t gpu_build(const GpuBuild& a, cudaStream_t stream);
+cudaError_t gpu_build_tables(const GpuBuild& a, cudaStream_t stream);
+cudaError_t gpu_build_kernels(const GpuBuild& a, cudaStream_t stream);
 // Rebuild the work items (another item_max) of a tree built by gpu_build with
 // the same arguments and scratch.
 cudaError_t gpu_build_items(const GpuBuild& a, cudaStream_t stream);
