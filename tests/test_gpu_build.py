@@ -207,3 +207,20 @@ def test_full_size_build_equals_host(torch):
     A = G.Tree.build(pos, m, 16, 512)
     B = G.Tree.build_gpu(pos, m, 16, 512)
     _assert_same_tree(A, B)
+
+
+@pytest.mark.parametrize("case", ["clustered_8M_deep", "plummer_16M"])
+def test_large_builds_equal_host(torch, case):
+    if case == "clustered_8M_deep":
+        pos, m = W.clustered(1 << 23, 256, seed=21, rs_min=1e-4, rs_max=1e-3)
+    else:
+        pos, m = W.plummer(1 << 24, seed=22)
+    A = G.Tree.build(pos, m, 16, 256)
+    B = G.Tree.build_gpu(pos, m, 16, 256)
+    assert A.stats == B.stats
+    assert np.array_equal(A.perm(), B.perm())
+    assert np.array_equal(A.cell_keys(), B.cell_keys())
+    pa, pb = A.cell_props(), B.cell_props()
+    for k in ("M", "com", "S", "cube"):
+        kk = {"M": "mass"}.get(k, k)
+        assert np.array_equal(_bits(pa[kk]), _bits(pb[kk])), k
