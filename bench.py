@@ -431,14 +431,14 @@ def run_learned_driver():
     from paper_1005_5384_gb300 import octgrav as G
     n = 1_048_576
     pos, m = W.sphere_disc(n, seed=6)
-    TT = G.Tree.build(pos, m, 16, 64)
-    groups = np.sort(np.random.default_rng(0).choice(TT.stats["n_groups"], 128, replace=False))
+    TT = G.Tree.build(pos, m, 16, 256)
+    groups = np.sort(np.random.default_rng(0).choice(TT.stats["n_groups"], 64, replace=False))
     f, lab, _ = TT.mlp_samples(groups, 0.35, 0.01)      # includes one plain-test launch
     rec, _ = G.mlp_train(f, lab, steps=3000, batch=4096, lr=2e-3, seed=3)
     del TT
     pos, m = W.sphere_disc(n, seed=5)
-    T = G.Tree.build(pos, m, 16, 64)
-    T.set_criterion(rec, tau=-3.54, theta_lo=0.8, theta_hi=1.3, theta_fb=1.0)
+    T = G.Tree.build(pos, m, 16, 256)
+    T.set_criterion(rec, tau=-3.57, theta_lo=0.8, theta_hi=1.3, theta_fb=1.0)
     out = torch.empty((n, 4), dtype=torch.float32, device="cuda")
     for _ in range(2):
         T.forces_device(0.01, 0.5, out)
