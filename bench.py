@@ -199,6 +199,15 @@ def cpu_baseline(pos, m, a, budget_s, acc=None):
             "sample": "full FP64 tree build (%.2fs) + forces of %d random groups (%d particles, %.2fs), "
                       "scaled to N=%d" % (t_build, ng, npart, t_forces, a.n),
             "t_build_s": t_build, "t_forces_sample_s": t_forces}
+    # the same on one core (the build is single-threaded already), a smaller sample
+    g1 = gs[: max(8, len(gs) // (4 * threads))]
+    n1 = int(R.count[R.groups[g1]].sum())
+    t0 = time.perf_counter()
+    R.forces(a.eps, a.theta, groups=g1, nthreads=1, counts=False)
+    t1 = time.perf_counter() - t0
+    line["one_core"] = {"value": a.n / (t_build + t1 * (a.n / n1)), "unit": "forces/s", "cores": 1,
+                        "sample": "forces of %d groups (%d particles, %.2fs) on 1 thread, scaled to N=%d, "
+                                  "plus the build" % (len(g1), n1, t1, a.n)}
     if acc is not None:
         idx = np.concatenate([R.cell_members(int(R.groups[g])) for g in gs])
         line["kernel_vs_oracle_rel_rms"] = O.rel_rms(acc[idx], ra[idx])
