@@ -200,7 +200,7 @@ def cpu_baseline(pos, m, a, budget_s, acc=None):
                       "scaled to N=%d" % (t_build, ng, npart, t_forces, a.n),
             "t_build_s": t_build, "t_forces_sample_s": t_forces}
     # the same on one core (the build is single-threaded already), a smaller sample
-    g1 = gs[: max(8, len(gs) // (4 * threads))]
+    g1 = gs[:: max(1, min(4 * threads, len(gs) // 8))]  # every k-th sampled group
     n1 = int(R.count[R.groups[g1]].sum())
     t0 = time.perf_counter()
     R.forces(a.eps, a.theta, groups=g1, nthreads=1, counts=False)
