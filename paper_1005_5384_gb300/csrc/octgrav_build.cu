@@ -622,6 +622,19 @@ __global__ void __launch_bounds__(TB) k_emit(int L, Cells C, const int* __restri
   }
 }
 
+// After a level loop capped at max_level < MAXD: flag a cell of level
+// max_level that still needs splitting (the caller rebuilds without the cap),
+// and close the level table so that lvl[NLEV] is the cell count.
+__global__ void k_depth_check(int max_level, Cells C, int* __restrict__ lvl, int n_leaf, int* __restrict__ misc) {
+  const int lb = lvl[max_level], le = lvl[max_level + 1];
+  bool deeper = false;
+  for (int c = lb + blockIdx.x * blockDim.x + threadIdx.x; c < le; c += gridDim.x * blockDim.x)
+    deeper |= C.pc[c] > n_leaf;
+  if (__syncthreads_or(deeper) && threadIdx.x == 0) atomicOr(&misc[M_STATUS], GPU_BUILD_DEEPER);
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    for (int L = max_level + 2; L <= NLEV; ++L) lvl[L] = le;
+}
+
 // Level of cell c: the last L with lvl[L] <= c.
 __device__ __forceinline__ int level_of(const int* lvl, int c) {
   int L = 0;
@@ -1190,11 +1203,13 @@ cudaError_t gpu_build_kernels(const GpuBuild& a, cudaStream_t st) {
 
   // ---- cells, level by level (sizes live in lvl[] on the device)
   k_roots<<<(std::max(a.n_sys, NLEV + 2) + 127) / 128, 128, 0, st>>>(a.n_sys, doffs, C, lvl);
-  for (int L = 0; L < MAXD; ++L) {
+  const int top = std::min(std::max(a.max_level, 1), MAXD);  // deepest level built
+  for (int L = 0; L < top; ++L) {
     k_split<<<GL, TB, 0, st>>>(L, keyA, C, a.n_leaf, lvl, spl, lpre, bsum);
     k_scan_level<<<1, GLT, 0, st>>>(L, bsum, lvl, static_cast<int>(a.cap), misc);
     k_emit<<<GL, TB, 0, st>>>(L, C, lvl, spl, lpre, bsum, misc);
   }
+  if (top < MAXD) k_depth_check<<<grid_for(a.n, TB), TB, 0, st>>>(top, C, lvl, a.n_leaf, misc);
   OG_TRY(cudaGetLastError());
 
   // ---- final (system-major) cell order
@@ -1221,7 +1236,7 @@ cudaError_t gpu_build_kernels(const GpuBuild& a, cudaStream_t st) {
   k_leaf_hist<<<gc, TB, 0, st>>>(C, lvl, lhist, misc);
   k_leaf_scatter<<<gc, TB, 0, st>>>(C, lvl, lhist, lhist + LBINS, lorder);
   k_leaf_props<<<gc, TB, 0, st>>>(C, lorder, misc, ni, xs, ms, P);
-  for (int L = MAXD - 1; L >= 0; --L) k_node_props<<<gc, TB, 0, st>>>(L, C, lvl, ni, P);
+  for (int L = top - 1; L >= 0; --L) k_node_props<<<gc, TB, 0, st>>>(L, C, lvl, ni, P);
   OG_TRY(cudaGetLastError());
 
   // ---- groups (ordered by first particle) and work items

@@ -529,6 +529,7 @@ struct Device {
   DevBuf order;  // work-item processing order (octgrav_balance)
   int device = -1;
   int64_t cell_cap = 0;  // cell capacity that last sufficed for a GPU build
+  int level_hint = 0;    // depth of the last GPU build + 2 (0: none yet), caps the next level loop
   // the GPU build's kernels captured as a graph, replayed on gstream while
   // build_key (every argument, pointers included) stays the same
   cudaGraphExec_t build_exec = nullptr;
@@ -1021,6 +1022,7 @@ og::GpuBuild gpu_args(octgrav_tree* t, const int64_t* offsets, const double* pos
   a.n_leaf = t->n_leaf;
   a.n_group = t->n_group;
   a.item_max = 32 * t->ppl;
+  a.max_level = OCTGRAV_MAX_DEPTH;
   a.cap = cap;
   a.scratch = D.scratch.p;
   a.scratch_bytes = D.scratch.cap;
@@ -1069,7 +1071,7 @@ int reserve_gpu_tree(Device& D, int64_t n, int n_sys, int64_t cap) {
 std::vector<int64_t> build_key(const og::GpuBuild& a) {
   auto P = [](const void* q) { return static_cast<int64_t>(reinterpret_cast<uintptr_t>(q)); };
   std::vector<int64_t> k = {P(a.pos),     P(a.mass),     a.n,           a.n_sys,       a.n_leaf,       a.n_group,
-                            a.item_max,   a.cap,         P(a.scratch),  static_cast<int64_t>(a.scratch_bytes),
+                            a.item_max,   a.max_level,   a.cap,         P(a.scratch),  static_cast<int64_t>(a.scratch_bytes),
                             P(a.parts),   P(a.perm),     P(a.key),      P(a.geo),      P(a.link),      P(a.mp),
                             P(a.bmin),    P(a.bmax),     P(a.cube),     P(a.M),        P(a.com),       P(a.S),
                             P(a.pcount),  P(a.cfirst),   P(a.group_cell), P(a.group_sys), P(a.group_item),
@@ -1168,19 +1170,28 @@ int build_gpu_common(int n_sys, const int64_t* offsets, const double* pos, const
   cap = std::min(std::max<int64_t>(cap, n_sys + 8), bound);  // the roots always fit
   int64_t res[og::GB_COUNT];
   int rc;
+  // repeated builds on cached buffers stop the level loop two levels below the
+  // previous tree's depth; a deeper tree is detected on the device and rebuilt
+  int max_level = dev && D.level_hint > 0 ? std::min(D.level_hint, kMaxDepth) : kMaxDepth;
   for (;;) {
     if ((rc = reserve_gpu_tree(D, n, n_sys, cap))) return rc;
     t->cell_cap = cap;
-    const og::GpuBuild a = gpu_args(t.get(), offsets, pos, mass);
+    og::GpuBuild a = gpu_args(t.get(), offsets, pos, mass);
+    a.max_level = max_level;
     if ((rc = run_build(D, a, st, dev != nullptr))) return rc;  // cached buffers: replay a graph
     if ((rc = gpu_result(t.get(), st, res))) return rc;
     if (res[og::GB_STATUS] & og::GPU_BUILD_BADINPUT)
       return fail(OCTGRAV_ERR_NONFINITE, "non-finite position/mass or negative mass");
+    if ((res[og::GB_STATUS] & og::GPU_BUILD_DEEPER) && max_level < kMaxDepth) {
+      max_level = kMaxDepth;
+      continue;
+    }
     if (!(res[og::GB_STATUS] & og::GPU_BUILD_OVERFLOW)) break;
     if (cap >= bound) return fail(OCTGRAV_ERR_ARG, "tree too large (more than %lld cells)", (long long)bound);
     cap = std::min(bound, 4 * cap);
   }
   D.cell_cap = cap;
+  D.level_hint = static_cast<int>(std::min<int64_t>(kMaxDepth, res[og::GB_DEPTH] + 2));
   t->n_cells = res[og::GB_NCELLS];
   t->n_groups = res[og::GB_NGROUPS];
   t->n_items = res[og::GB_NITEMS];

@@ -130,6 +130,7 @@ cudaError_t launch_walk_eval_noalloc(KParams p, int ppl, int ctas_per_sm, cudaSt
 enum : int {
   GPU_BUILD_OVERFLOW = 1,  // more cells than the capacity: enlarge and build again
   GPU_BUILD_BADINPUT = 2,  // non-finite coordinate or mass, or a negative mass
+  GPU_BUILD_DEEPER = 4,    // the level cap was too low: build again without it
 };
 // Entries of the result block (int64) the build writes at the end.
 enum : int { GB_NCELLS = 0, GB_NGROUPS, GB_NITEMS, GB_DEPTH, GB_NLEAVES, GB_MAXGROUP, GB_STATUS, GB_COUNT };
@@ -149,6 +150,7 @@ struct GpuBuild {
   int n_sys;
   const int64_t* offsets;
   int n_leaf, n_group, item_max;
+  int max_level;  // deepest level the level loop builds (21 = no cap)
   int64_t cap;
   void* scratch;
   size_t scratch_bytes;

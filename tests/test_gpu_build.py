@@ -224,3 +224,16 @@ def test_large_builds_equal_host(torch, case):
     for k in ("M", "com", "S", "cube"):
         kk = {"M": "mass"}.get(k, k)
         assert np.array_equal(_bits(pa[kk]), _bits(pb[kk])), k
+
+
+def test_level_cap_from_a_shallow_tree_is_lifted_for_a_deep_one(torch):
+    # the one-shot call caches its buffers and caps the next level loop at the
+    # previous depth + 2; a much deeper system of the same size must still come out right
+    n = 50000
+    shallow = W.uniform_cube(n, seed=31)
+    deep = W.clustered(n, 8, seed=32, rs_min=1e-5, rs_max=1e-4)
+    G.forces_gpu(*shallow, 0.01, 0.5, 16, 64)
+    acc, pot = G.forces_gpu(*deep, 1e-6, 0.5, 16, 64)
+    ra, rp = G.Tree.build(*deep, 16, 64).forces(1e-6, 0.5)
+    assert np.array_equal(_bits(acc), _bits(ra)) and np.array_equal(_bits(pot), _bits(rp))
+    assert G.Tree.build(*deep, 16, 64).stats["depth"] > G.Tree.build(*shallow, 16, 64).stats["depth"] + 2
