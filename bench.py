@@ -549,7 +549,7 @@ def run_reference(a, rank, world):
     pos, m = W.plummer(a.n, seed=a.seed)
     threads = O.default_threads()
     if a.n_group <= 0:
-        a.n_group = 256  # the group size the GPU autotuner selects for this workload
+        a.n_group = 512  # the group size the GPU autotuner selects for this workload
     R = O.Tree(pos, m, a.n_leaf, a.n_group)
     rng = np.random.default_rng(5)
     budget = max(1.0, 120.0 / max(1, a.steps + a.warmup))
