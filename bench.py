@@ -297,10 +297,21 @@ def extras(torch, G, a, pos, m, T, out, flush, stream, peak, steps):
     S.step(1.0 / 128, nsteps, stream=stream)
     dt_wall = time.perf_counter() - t0
     e1 = sum(S.energy(stream=stream))
+    # the same with a full build every 4th step and refits in between
+    S.set_rebuild(4)
+    S.step(1.0 / 128, 4, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    S.step(1.0 / 128, nsteps, stream=stream)
+    dt_refit = time.perf_counter() - t0
+    e2 = sum(S.energy(stream=stream))
     res["leapfrog_plummer_1M"] = {"dt": 1.0 / 128, "steps": nsteps, "ms_per_step": 1e3 * dt_wall / nsteps,
                                   "particle_steps_per_s": a.n * nsteps / dt_wall,
                                   "rel_energy_change_9_steps": (e1 - e0) / abs(e0),
-                                  "per_step": "kick+drift, GPU tree build, walk+evaluation, unpermute, kick"}
+                                  "per_step": "kick+drift, GPU tree build, walk+evaluation, unpermute, kick",
+                                  "rebuild_every_4": {"ms_per_step": 1e3 * dt_refit / nsteps,
+                                                      "particle_steps_per_s": a.n * nsteps / dt_refit,
+                                                      "rel_energy_change_21_steps": (e2 - e0) / abs(e0)}}
     del S
     # C2 at theta = 0.75
     T.forces_device(a.eps, 0.75, out, stream=stream)

@@ -142,6 +142,17 @@ int octgrav_build_batch_gpu(int n_sys, const int64_t *offsets, const double *pos
                             const double *mass_dev, int n_leaf, int n_group, void *stream,
                             octgrav_tree **out);
 
+/* Refit a tree from octgrav_build_tree_gpu / octgrav_build_batch_gpu to new
+ * positions and masses of the same particles (DEVICE arrays, input order, as
+ * for the build): the cells keep their particles, order, groups and work
+ * items; the particle records and every cell's tight box, boundary cube,
+ * mass, centre of mass, second moments and the groups' boxes are recomputed
+ * in FP64 exactly as a build does from those particles (a refit at unchanged
+ * positions reproduces the tree bit for bit). Waits for the stream. Errors:
+ * ERR_ARG, ERR_STATE (not a GPU-built tree), ERR_NONFINITE, ERR_CUDA. */
+int octgrav_refit_tree_gpu(octgrav_tree *t, const double *pos_dev, const double *mass_dev,
+                           void *stream);
+
 /* Forces in INPUT order into DEVICE FP64 arrays: acc_dev (n x 3) and pot_dev
  * (n, may be NULL), for any tree (host- or GPU-built). Enqueued on stream and
  * not waited for: read the launch status with octgrav_status. Errors: ERR_ARG
@@ -207,6 +218,12 @@ int octgrav_sim_state(octgrav_sim *s, double *pos, double *vel, double *acc, dou
 
 /* Release the integrator and its device memory (NULL is a no-op). */
 void octgrav_sim_free(octgrav_sim *s);
+
+/* Rebuild the tree every `every` force evaluations (1, the default, rebuilds
+ * every step); in between the last tree is refitted (octgrav_refit_tree_gpu):
+ * cheaper, and still exact in its boxes and moments, but its cells loosen as
+ * particles move. Errors: ERR_ARG. */
+int octgrav_sim_set_rebuild(octgrav_sim *s, int every);
 
 /* Wait for stream and return the status of the last launch on this tree:
  * OK, ERR_STACK, ERR_TIMEOUT or ERR_INDEX. Clears nothing. */

@@ -1048,6 +1048,8 @@ __global__ void __launch_bounds__(TB) k_item_scatter(const int* __restrict__ n_i
   }
 }
 
+__global__ void k_clear_status(int* __restrict__ misc) { misc[M_STATUS] = 0; }
+
 __global__ void k_finish(const int* __restrict__ lvl, const int* __restrict__ misc, int64_t* __restrict__ res) {
   int depth = 0;
   for (int L = 0; L < NLEV; ++L)
@@ -1255,6 +1257,34 @@ cudaError_t gpu_build_kernels(const GpuBuild& a, cudaStream_t st) {
   k_finish<<<1, 1, 0, st>>>(lvl, misc, a.result);
 #undef OG_TRY
   return cudaGetLastError();
+}
+
+cudaError_t gpu_refit(const GpuBuild& a, cudaStream_t st) {
+  const Layout Lo = layout(a.n, a.n_sys, (a.n + TILE - 1) / TILE + a.n_sys, a.cap);
+  if (Lo.total > a.scratch_bytes) return cudaErrorInvalidValue;
+  void* S = a.scratch;
+  int nch = 0;
+  for (int s = 0; s < a.n_sys; ++s) nch += static_cast<int>((a.offsets[s + 1] - a.offsets[s] + TILE - 1) / TILE);
+  int* misc = at<int>(S, Lo.misc);
+  const int* lvl = at<int>(S, Lo.lvl);
+  Cells C{at<uint64_t>(S, Lo.ckey), at<int>(S, Lo.cpar), at<int>(S, Lo.cpf), at<int>(S, Lo.cpc),
+          at<int>(S, Lo.csys),      at<int>(S, Lo.cfc),  at<int>(S, Lo.cnc)};
+  Props P{a.bmin, a.bmax, a.cube, a.M, a.com, a.S, a.key, a.geo, a.link, a.mp, a.pcount, a.cfirst};
+  const int* ni = a.n_sys > 1 ? at<int>(S, Lo.ni) : nullptr;
+  const int gc = grid_for(a.cap, TB);
+  cudaError_t e;
+  // the status bits only: the counts of the build stay
+  k_clear_status<<<1, 1, 0, st>>>(misc);
+  k_bbox<<<nch, TB, 0, st>>>(a.pos, a.mass, at<Chunk>(S, Lo.chunks), at<double>(S, Lo.part), misc);
+  k_gather<<<grid_for(a.n, TB), TB, 0, st>>>(at<uint32_t>(S, Lo.valA), a.pos, a.mass, a.n, at<double>(S, Lo.xs),
+                                             at<double>(S, Lo.ms), a.parts, a.perm);
+  k_leaf_props<<<gc, TB, 0, st>>>(C, at<int>(S, Lo.lorder), misc, ni, at<double>(S, Lo.xs), at<double>(S, Lo.ms), P);
+  for (int L = MAXD - 1; L >= 0; --L) k_node_props<<<gc, TB, 0, st>>>(L, C, lvl, ni, P);
+  k_items<<<grid_for(a.n, TB), TB, 0, st>>>(&misc[M_NGROUPS], a.group_cell, a.group_sys, at<int>(S, Lo.ioff),
+                                            a.cell_off, P, a.item_max, a.items, a.ibox, a.item_key, a.group_item);
+  k_finish<<<1, 1, 0, st>>>(lvl, misc, a.result);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return cudaSuccess;
 }
 
 cudaError_t gpu_build_items(const GpuBuild& a, cudaStream_t st) {

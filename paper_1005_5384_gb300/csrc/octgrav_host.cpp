@@ -615,10 +615,10 @@ struct octgrav_sim {
   Device dev;                        // tree and build buffers, reused every step
   DevBuf x, v, m, a, phi, epart;     // FP64 state (input order) and energy partials
   int64_t steps = 0;
-  ~octgrav_sim() {
-    for (DevBuf* b : {&x, &v, &m, &a, &phi, &epart}) b->release();
-    dev.release();
-  }
+  int rebuild_every = 1;             // full build every k force evaluations, refit in between
+  int since_build = 0;
+  octgrav_tree* tree = nullptr;      // the last built tree (its buffers live in dev)
+  ~octgrav_sim();
 };
 
 namespace {
@@ -1420,17 +1420,39 @@ int octgrav_direct(const double* pos, const double* mass, int64_t n, const int64
 
 namespace {
 
-// Forces at the current positions: tree built on the GPU, walk, unpermute
-// into the state's acceleration and potential arrays; waits for the stream.
+// Refit a GPU-built tree to new positions and masses (device arrays) on the
+// scratch of its build; waits for the stream.
+int refit_tree(octgrav_tree* t, const double* pos, const double* mass, cudaStream_t st) {
+  const og::GpuBuild a = gpu_args(t, t->sys_off.data(), pos, mass);
+  cudaError_t e = og::gpu_refit(a, st);
+  if (e != cudaSuccess) return fail(OCTGRAV_ERR_CUDA, "refit launch failed: %s", cudaGetErrorString(e));
+  int64_t res[og::GB_COUNT];
+  if (int rc = gpu_result(t, st, res)) return rc;
+  t->host_valid = false;
+  if (res[og::GB_STATUS] & og::GPU_BUILD_BADINPUT)
+    return fail(OCTGRAV_ERR_NONFINITE, "non-finite position/mass or negative mass");
+  return OCTGRAV_OK;
+}
+
+// Forces at the current positions: the tree built on the GPU (or refitted,
+// between full builds), walk, unpermute into the state's acceleration and
+// potential arrays; waits for the stream.
 int sim_forces(octgrav_sim* s, cudaStream_t st) {
-  const int64_t off[2] = {0, s->n};
-  octgrav_tree* t = nullptr;
-  int rc = build_gpu_common(1, off, static_cast<const double*>(s->x.p), static_cast<const double*>(s->m.p),
-                            s->n_leaf, s->n_group, st, &s->dev, &t);
-  if (rc) return rc;
-  rc = forces_dev64(t, s->eps, s->theta, s->G, static_cast<double*>(s->a.p), static_cast<double*>(s->phi.p), st);
-  if (!rc) rc = read_status(t, st);
-  octgrav_free_tree(t);
+  const double* x = static_cast<const double*>(s->x.p);
+  const double* m = static_cast<const double*>(s->m.p);
+  int rc;
+  if (!s->tree || s->since_build + 1 >= s->rebuild_every) {
+    octgrav_free_tree(s->tree);
+    s->tree = nullptr;
+    const int64_t off[2] = {0, s->n};
+    if ((rc = build_gpu_common(1, off, x, m, s->n_leaf, s->n_group, st, &s->dev, &s->tree))) return rc;
+    s->since_build = 0;
+  } else {
+    if ((rc = refit_tree(s->tree, x, m, st))) return rc;
+    ++s->since_build;
+  }
+  rc = forces_dev64(s->tree, s->eps, s->theta, s->G, static_cast<double*>(s->a.p), static_cast<double*>(s->phi.p), st);
+  if (!rc) rc = read_status(s->tree, st);
   return rc;
 }
 
@@ -1518,6 +1540,19 @@ int octgrav_sim_state(octgrav_sim* s, double* pos, double* vel, double* acc, dou
 }
 
 void octgrav_sim_free(octgrav_sim* s) { delete s; }
+
+int octgrav_sim_set_rebuild(octgrav_sim* s, int every) {
+  if (!s || every < 1) return fail(OCTGRAV_ERR_ARG, "NULL sim or every < 1");
+  s->rebuild_every = every;
+  return OCTGRAV_OK;
+}
+
+int octgrav_refit_tree_gpu(octgrav_tree* t, const double* pos_dev, const double* mass_dev, void* stream) {
+  if (!t || !pos_dev || !mass_dev) return fail(OCTGRAV_ERR_ARG, "NULL argument");
+  if (!t->gpu || t->dev != &t->own)
+    return fail(OCTGRAV_ERR_STATE, "refit needs a tree from octgrav_build_tree_gpu / octgrav_build_batch_gpu");
+  return refit_tree(t, pos_dev, mass_dev, static_cast<cudaStream_t>(stream));
+}
 
 int octgrav_status(octgrav_tree* t, void* stream) {
   if (!t) return fail(OCTGRAV_ERR_ARG, "tree is NULL");
@@ -2175,3 +2210,9 @@ void octgrav_free_tree(octgrav_tree* t) {
 }
 
 }  // extern "C"
+
+octgrav_sim::~octgrav_sim() {
+  octgrav_free_tree(tree);
+  for (DevBuf* b : {&x, &v, &m, &a, &phi, &epart}) b->release();
+  dev.release();
+}

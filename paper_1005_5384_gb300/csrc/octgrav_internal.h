@@ -181,6 +181,12 @@ size_t gpu_build_scratch_bytes(int64_t n, int n_sys, int64_t cap);
 cudaError_t gpu_build(const GpuBuild& a, cudaStream_t stream);
 cudaError_t gpu_build_tables(const GpuBuild& a, cudaStream_t stream);
 cudaError_t gpu_build_kernels(const GpuBuild& a, cudaStream_t stream);
+// Refit the tree of the last gpu_build on this scratch to new positions and
+// masses of the same particles (pos / mass in a): membership, order, groups
+// and items stay; particle records, every cell's box, cube, moments and
+// records, and the items' group boxes are recomputed. The result block gets
+// the build's counts and the status of the new inputs.
+cudaError_t gpu_refit(const GpuBuild& a, cudaStream_t stream);
 // Rebuild the work items (another item_max) of a tree built by gpu_build with
 // the same arguments and scratch.
 cudaError_t gpu_build_items(const GpuBuild& a, cudaStream_t stream);

@@ -57,6 +57,8 @@ _SIGS = {
     "octgrav_sim_energy": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double), _vp]),
     "octgrav_sim_state": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "octgrav_sim_free": (None, [_vp]),
+    "octgrav_sim_set_rebuild": (C.c_int, [_vp, C.c_int]),
+    "octgrav_refit_tree_gpu": (C.c_int, [_vp, _vp, _vp, _vp]),
     "octgrav_direct": (C.c_int, [_vp, _vp, C.c_int64, _vp, C.c_int64, C.c_double, C.c_double, _vp, _vp, _vp]),
     "octgrav_status": (C.c_int, [_vp, _vp]),
     "octgrav_tree_stats": (C.c_int, [_vp, _i64, C.c_int]),
@@ -207,6 +209,17 @@ class Tree:
         t = cls(h.value, n)
         t.offsets = off
         return t
+
+    def refit(self, pos, mass, stream=None):
+        """Refit a GPU-built tree to new positions / masses of the same particles
+        (CUDA float64 tensors or host arrays, input order)."""
+        import torch
+        x = pos if isinstance(pos, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(pos, dtype=np.float64))
+        mm = mass if isinstance(mass, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(mass, dtype=np.float64))
+        x = x.to(device="cuda", dtype=torch.float64).contiguous()
+        mm = mm.to(device="cuda", dtype=torch.float64).contiguous()
+        _check(load().octgrav_refit_tree_gpu(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(mm.data_ptr()),
+                                             _stream_handle(stream)))
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -448,6 +461,10 @@ class Sim:
                                       int(n_leaf), int(n_group if n_group is not None else n_leaf),
                                       _stream_handle(stream), C.byref(h)))
         self._h = h
+
+    def set_rebuild(self, every: int):
+        """Full tree build every `every` force evaluations, refits in between."""
+        _check(load().octgrav_sim_set_rebuild(self._h, int(every)))
 
     def step(self, dt: float, n_steps: int = 1, stream=None):
         _check(load().octgrav_sim_step(self._h, float(dt), int(n_steps), _stream_handle(stream)))

@@ -237,3 +237,74 @@ def test_level_cap_from_a_shallow_tree_is_lifted_for_a_deep_one(torch):
     ra, rp = G.Tree.build(*deep, 16, 64).forces(1e-6, 0.5)
     assert np.array_equal(_bits(acc), _bits(ra)) and np.array_equal(_bits(pot), _bits(rp))
     assert G.Tree.build(*deep, 16, 64).stats["depth"] > G.Tree.build(*shallow, 16, 64).stats["depth"] + 2
+
+
+def test_refit_at_the_same_positions_is_the_same_tree(torch):
+    pos, m = W.plummer(40000, seed=41)
+    B = G.Tree.build_gpu(pos, m, 16, 64)
+    keys, props, info = B.cell_keys(), B.cell_props(), B.item_info()
+    f0 = _device_forces(torch, B, 0.01, 0.5)
+    B.refit(pos, m)
+    assert np.array_equal(B.cell_keys(), keys)
+    p1 = B.cell_props()
+    for k in props:
+        assert np.array_equal(_bits(p1[k]), _bits(props[k])), k
+    for k in info:
+        assert np.array_equal(B.item_info()[k], info[k]), k
+    assert np.array_equal(_bits(_device_forces(torch, B, 0.01, 0.5)), _bits(f0))
+
+
+def test_refit_recomputes_boxes_and_moments_from_the_new_positions(torch):
+    pos, m = W.plummer(20000, seed=42)
+    rng = np.random.default_rng(1)
+    pos1 = pos + 0.01 * rng.standard_normal(pos.shape)
+    m1 = m * (1.0 + 0.1 * rng.random(m.shape))
+    B = G.Tree.build_gpu(pos, m, 16, 64)
+    B.refit(pos1, m1)
+    perm = B.perm()
+    props = B.cell_props()
+    x = pos1[perm]
+    mm = m1[perm]
+    keys = B.cell_keys()
+    cnt = props["count"]
+    # first particle (tree position) of each cell: a child starts where its parent
+    # starts plus the counts of its earlier siblings (children ascend by octant)
+    first = np.zeros(B.stats["n_cells"], np.int64)
+    depth = np.floor(np.log2(keys.astype(np.float64)) / 3).astype(int)
+    where = {int(k): c for c, k in enumerate(keys)}
+    for L in range(1, depth.max() + 1):
+        for c in np.nonzero(depth == L)[0]:
+            parent = where[int(keys[c] >> np.uint64(3))]
+            base = int(keys[parent]) << 3
+            first[c] = first[parent] + sum(int(cnt[where[base | o]]) for o in range(int(keys[c]) & 7)
+                                           if (base | o) in where)
+    for c in rng.choice(B.stats["n_cells"], 300, replace=False):
+        sl = slice(first[c], first[c] + cnt[c])
+        xs, ms = x[sl], mm[sl]
+        assert np.array_equal(props["bmin"][c], xs.min(0)) and np.array_equal(props["bmax"][c], xs.max(0))
+        M = ms.sum()
+        com = (ms[:, None] * xs).sum(0) / M
+        y = xs - com
+        S = np.einsum("i,ij,ik->jk", ms, y, y)
+        assert abs(props["mass"][c] - M) <= 1e-13 * M
+        assert np.allclose(props["com"][c], com, rtol=0, atol=1e-12 * (1 + np.abs(com).max()))
+        s6 = np.array([S[0, 0], S[1, 1], S[2, 2], S[0, 1], S[0, 2], S[1, 2]])
+        assert np.allclose(props["S"][c], s6, rtol=1e-10, atol=1e-14 * max(1e-300, np.abs(s6).max()))
+    # the refitted tree still gives accurate forces
+    acc, _ = B.forces(0.01, 0.5)
+    samp = W.sample_indices(len(m1), 400, seed=3)
+    ad, _ = G.direct(pos1, m1, 0.01, targets=samp)
+    assert np.median(G.rel_err(acc[samp], ad)) < 5e-4
+
+
+def test_refit_refusals(torch):
+    pos, m = W.plummer(5000, seed=43)
+    with pytest.raises(G.OctgravError) as e:
+        G.Tree.build(pos, m).refit(pos, m)
+    assert e.value.code == G.ERR_STATE
+    B = G.Tree.build_gpu(pos, m)
+    bad = pos.copy()
+    bad[7, 0] = np.inf
+    with pytest.raises(G.OctgravError) as e:
+        B.refit(bad, m)
+    assert e.value.code == G.ERR_NONFINITE

@@ -97,3 +97,21 @@ def test_bad_arguments_are_refused():
     S.step(0.01, 0)
     x, v, _, _ = S.state()
     assert np.array_equal(x, x0) and np.array_equal(v, v0)
+
+
+def test_refit_between_rebuilds():
+    x0, v0, m = W.plummer_pv(16384, seed=8)
+    A = G.Sim(x0, v0, m, 0.01, 0.5, n_leaf=16, n_group=64)
+    B = G.Sim(x0, v0, m, 0.01, 0.5, n_leaf=16, n_group=64)
+    B.set_rebuild(4)
+    E0 = sum(B.energy())
+    A.step(1.0 / 128, 16)
+    B.step(1.0 / 128, 16)
+    xa, _, _, _ = A.state()
+    xb, _, _, _ = B.state()
+    # refitted trees give slightly different (still accurate) forces: nearby trajectories
+    assert np.linalg.norm(xa - xb) / np.linalg.norm(xa) < 1e-4
+    E1 = sum(B.energy())
+    assert abs(E1 - E0) < 5e-4 * abs(E0)
+    with pytest.raises(G.OctgravError):
+        B.set_rebuild(0)
