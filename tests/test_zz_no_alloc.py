@@ -76,3 +76,15 @@ def test_noalloc_rejects_small_arena_and_too_many_items(torch):
     with pytest.raises(G.OctgravError) as e:
         B.forces_noalloc(0.01, 0.5, 0, (arena.data_ptr(), 1 << 40))
     assert e.value.code == G.ERR_ARG
+
+
+def test_noalloc_with_a_gpu_built_tree(torch):
+    pos, m = W.plummer(30000, seed=14)
+    T = G.Tree.build_gpu(pos, m, 16, 64)
+    ref = torch.empty((T.n, 4), dtype=torch.float32, device="cuda")
+    T.forces_device(0.01, 0.5, ref)
+    torch.cuda.synchronize()
+    arena = torch.empty(T.noalloc_arena_bytes(), dtype=torch.uint8, device="cuda")
+    out = torch.zeros_like(ref)
+    T.forces_noalloc(0.01, 0.5, out, arena)
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), ref.cpu().numpy().view(np.uint32))
