@@ -181,10 +181,11 @@ inline uint64_t spread21(uint64_t v) {
 }
 
 // Stable LSD radix sort of (key, val) by key (63 significant bits, 7 x 9-bit digits).
-void radix_sort(std::vector<uint64_t>& key, std::vector<uint32_t>& val, bool parallel) {
+void radix_sort(std::vector<uint64_t>& key, std::vector<uint32_t>& val, std::vector<uint64_t>& k2,
+                std::vector<uint32_t>& v2, bool parallel) {
   const int64_t n = static_cast<int64_t>(key.size());
-  std::vector<uint64_t> k2(n);
-  std::vector<uint32_t> v2(n);
+  k2.resize(n);
+  v2.resize(n);
   constexpr int BITS = 9, B = 1 << BITS;
   const int T = parallel ? std::max(1, std::min<int>(Pool::get().size(), static_cast<int>(n / 65536))) : 1;
   std::vector<int64_t> hist(static_cast<size_t>(T) * B);
@@ -237,6 +238,24 @@ struct SysTree {
   int depth_reached = 0;
   int64_t max_group = 0;
   int64_t n_leaves = 0;
+  // scratch of the build (kept so that a reused SysTree allocates nothing)
+  std::vector<uint64_t> k2;
+  std::vector<uint32_t> v2;
+  std::vector<uint8_t> covered;
+  // empty every array but keep its memory, for a new build
+  void reset() {
+    n = 0;
+    for (auto* v : {&perm, &v2}) v->clear();
+    for (auto* v : {&code, &key, &k2}) v->clear();
+    for (auto* v : {&x, &m, &bmin, &bmax, &cube, &M, &com, &S}) v->clear();
+    for (auto* v : {&depth, &parent, &first_child, &n_child, &groups}) v->clear();
+    pfirst.clear();
+    pcount.clear();
+    covered.clear();
+    depth_reached = 0;
+    max_group = 0;
+    n_leaves = 0;
+  }
 };
 
 inline int octant_at(uint64_t code, int child_depth) {
@@ -245,6 +264,7 @@ inline int octant_at(uint64_t code, int child_depth) {
 
 int build_system(const double* pos, const double* mass, int64_t n, int n_leaf, int n_group,
                  bool parallel, SysTree& T) {
+  T.reset();
   T.n = n;
   const int64_t grain = parallel ? 16384 : (int64_t)1 << 62;
   // ---- bounding box and root cube
@@ -284,8 +304,10 @@ int build_system(const double* pos, const double* mass, int64_t n, int n_leaf, i
   const uint64_t qmax = (1ull << kMaxDepth) - 1;
 
   // ---- Morton codes and sort
-  std::vector<uint64_t> code(n);
-  std::vector<uint32_t> idx(n);
+  std::vector<uint64_t>& code = T.code;
+  std::vector<uint32_t>& idx = T.perm;
+  code.resize(n);
+  idx.resize(n);
   parallel_for(n, grain, [&](int64_t a, int64_t b) {
     for (int64_t i = a; i < b; ++i) {
       uint64_t q[3];
@@ -298,9 +320,7 @@ int build_system(const double* pos, const double* mass, int64_t n, int n_leaf, i
       idx[i] = static_cast<uint32_t>(i);
     }
   });
-  radix_sort(code, idx, parallel);
-  T.perm = std::move(idx);
-  T.code = std::move(code);
+  radix_sort(code, idx, T.k2, T.v2, parallel);
   T.x.resize(3 * n);
   T.m.resize(n);
   parallel_for(n, grain, [&](int64_t a, int64_t b) {
@@ -323,6 +343,13 @@ int build_system(const double* pos, const double* mass, int64_t n, int n_leaf, i
     T.pfirst.push_back(pf);
     T.pcount.push_back(pc);
   };
+  {  // room for the usual tree size, so that the level loop rarely reallocates
+    const size_t guess = static_cast<size_t>(8 * n / (n_leaf + 1) + 64);
+    for (auto* v : {&T.depth, &T.parent, &T.first_child, &T.n_child}) v->reserve(guess);
+    T.key.reserve(guess);
+    T.pfirst.reserve(guess);
+    T.pcount.reserve(guess);
+  }
   push_cell(1, 0, -1, 0, n);
   std::vector<int64_t> level_begin = {0};
   std::vector<int64_t> splits;  // 9 per cell of the level being split
@@ -479,7 +506,8 @@ int build_system(const double* pos, const double* mass, int64_t n, int n_leaf, i
   }
 
   // ---- groups: first cells from the root that are leaves or hold <= n_group
-  std::vector<uint8_t> covered(nc, 0);
+  std::vector<uint8_t>& covered = T.covered;
+  covered.assign(nc, 0);
   T.n_leaves = 0;
   for (int64_t c = 0; c < nc; ++c) {
     const bool par = c > 0 && covered[T.parent[c]];
@@ -626,55 +654,60 @@ namespace {
 // Split every group into work items of at most 32 * ppl particles.
 void make_items(octgrav_tree* t) {
   const int item_max = 32 * t->ppl;
-  t->items.clear();
-  t->ibox.clear();
-  t->item_key.clear();
-  t->group_item.assign(t->group_cell.size(), 0);
-  for (size_t g = 0; g < t->group_cell.size(); ++g) {
-    const int64_t c = t->group_cell[g];
-    const int s = t->group_sys[g];
-    const int64_t root = t->cell_off[s];
-    const int64_t cnt = t->pcount[c];
-    // first particle of the group: from the link of a leaf or by walking down to a leaf
-    int64_t cc = c;
-    while (t->link[cc].y > 0) cc = t->link[cc].x;
-    const int64_t pf = t->link[cc].x;
-    float4 b[3];
-    double C[3];
-    float chi[3], clo[3];
-    for (int d = 0; d < 3; ++d) {
-      C[d] = t->cube[4 * c + d];
-      chi[d] = static_cast<float>(C[d]);
-      clo[d] = static_cast<float>(C[d] - static_cast<double>(chi[d]));
-    }
-    b[0] = make_float4(static_cast<float>(t->bmin[3 * c]), static_cast<float>(t->bmin[3 * c + 1]),
-                       static_cast<float>(t->bmin[3 * c + 2]), chi[0]);
-    b[1] = make_float4(static_cast<float>(t->bmax[3 * c]), static_cast<float>(t->bmax[3 * c + 1]),
-                       static_cast<float>(t->bmax[3 * c + 2]), chi[1]);
-    b[2] = make_float4(clo[0], clo[1], clo[2], chi[2]);
-    float4 grange;  // (first particle, count) of the whole group, as int bits
-    const int32_t gr[2] = {static_cast<int32_t>(pf), static_cast<int32_t>(cnt)};
-    std::memcpy(&grange.x, &gr[0], 4);
-    std::memcpy(&grange.y, &gr[1], 4);
-    grange.z = grange.w = 0.f;
-    t->group_item[g] = static_cast<int32_t>(t->items.size());
-    for (int64_t off = 0; off < cnt; off += item_max) {
-      const int k = static_cast<int>(std::min<int64_t>(item_max, cnt - off));
-      t->items.push_back(make_int4(static_cast<int>(root), static_cast<int>(pf + off), k, s));
-      t->ibox.push_back(b[0]);
-      t->ibox.push_back(b[1]);
-      t->ibox.push_back(b[2]);
-      t->ibox.push_back(grange);
-      t->item_key.push_back(t->key[c]);
-    }
+  const int64_t ng = static_cast<int64_t>(t->group_cell.size());
+  t->group_item.assign(ng, 0);
+  int64_t ni = 0;
+  for (int64_t g = 0; g < ng; ++g) {
+    t->group_item[g] = static_cast<int32_t>(ni);
+    ni += (t->pcount[t->group_cell[g]] + item_max - 1) / item_max;
   }
-  t->n_groups = static_cast<int64_t>(t->group_cell.size());
-  t->n_items = static_cast<int64_t>(t->items.size());
-  // default processing order: most particles first
-  t->item_order.resize(t->items.size());
-  for (size_t k = 0; k < t->items.size(); ++k) t->item_order[k] = static_cast<int32_t>(k);
-  std::stable_sort(t->item_order.begin(), t->item_order.end(),
-                   [&](int32_t a, int32_t b) { return t->items[a].z > t->items[b].z; });
+  t->items.resize(ni);
+  t->ibox.resize(4 * ni);
+  t->item_key.resize(ni);
+  parallel_for(ng, 1024, [&](int64_t a, int64_t b) {
+    for (int64_t g = a; g < b; ++g) {
+      const int64_t c = t->group_cell[g];
+      const int s = t->group_sys[g];
+      const int64_t root = t->cell_off[s];
+      const int64_t cnt = t->pcount[c];
+      const int64_t pf = t->cfirst[c];  // first particle of the group (tree position)
+      float4 bx[3];
+      float chi[3], clo[3];
+      for (int d = 0; d < 3; ++d) {
+        const double C = t->cube[4 * c + d];
+        chi[d] = static_cast<float>(C);
+        clo[d] = static_cast<float>(C - static_cast<double>(chi[d]));
+      }
+      bx[0] = make_float4(static_cast<float>(t->bmin[3 * c]), static_cast<float>(t->bmin[3 * c + 1]),
+                          static_cast<float>(t->bmin[3 * c + 2]), chi[0]);
+      bx[1] = make_float4(static_cast<float>(t->bmax[3 * c]), static_cast<float>(t->bmax[3 * c + 1]),
+                          static_cast<float>(t->bmax[3 * c + 2]), chi[1]);
+      bx[2] = make_float4(clo[0], clo[1], clo[2], chi[2]);
+      float4 grange;  // (first particle, count) of the whole group, as int bits
+      const int32_t gr[2] = {static_cast<int32_t>(pf), static_cast<int32_t>(cnt)};
+      std::memcpy(&grange.x, &gr[0], 4);
+      std::memcpy(&grange.y, &gr[1], 4);
+      grange.z = grange.w = 0.f;
+      int64_t k = t->group_item[g];
+      for (int64_t off = 0; off < cnt; off += item_max, ++k) {
+        t->items[k] = make_int4(static_cast<int>(root), static_cast<int>(pf + off),
+                                static_cast<int>(std::min<int64_t>(item_max, cnt - off)), s);
+        t->ibox[4 * k] = bx[0];
+        t->ibox[4 * k + 1] = bx[1];
+        t->ibox[4 * k + 2] = bx[2];
+        t->ibox[4 * k + 3] = grange;
+        t->item_key[k] = t->key[c];
+      }
+    }
+  });
+  t->n_groups = ng;
+  t->n_items = ni;
+  // default processing order: most particles first (a stable counting sort by count)
+  std::vector<int64_t> start(item_max + 2, 0);
+  for (int64_t k = 0; k < ni; ++k) ++start[item_max - t->items[k].z + 1];
+  for (int b = 1; b <= item_max + 1; ++b) start[b] += start[b - 1];
+  t->item_order.resize(ni);
+  for (int64_t k = 0; k < ni; ++k) t->item_order[start[item_max - t->items[k].z]++] = static_cast<int32_t>(k);
   t->ordered = true;
 }
 
@@ -686,20 +719,24 @@ int assemble(octgrav_tree* t, std::vector<SysTree>& sys) {
   const int64_t nc = t->cell_off[ns];
   if (nc >= (1ll << 28)) return fail(OCTGRAV_ERR_ARG, "too many cells (%lld)", (long long)nc);
   t->n_cells = nc;
+  // one system: its FP64 cell arrays are moved, not copied, after the loop below
+  const bool single = ns == 1;
   t->perm.resize(t->n);
   t->parts.resize(2 * t->n);
-  t->key.resize(nc);
   t->geo.resize(nc);
   t->link.resize(nc);
   t->mp.resize(4 * nc);
-  t->bmin.resize(3 * nc);
-  t->bmax.resize(3 * nc);
-  t->cube.resize(4 * nc);
-  t->M.resize(nc);
-  t->com.resize(3 * nc);
-  t->S.resize(6 * nc);
-  t->pcount.resize(nc);
   t->cfirst.resize(nc);
+  if (!single) {
+    t->key.resize(nc);
+    t->bmin.resize(3 * nc);
+    t->bmax.resize(3 * nc);
+    t->cube.resize(4 * nc);
+    t->M.resize(nc);
+    t->com.resize(3 * nc);
+    t->S.resize(6 * nc);
+    t->pcount.resize(nc);
+  }
   t->group_cell.clear();
   t->group_sys.clear();
   t->n_leaves = 0;
@@ -725,7 +762,7 @@ int assemble(octgrav_tree* t, std::vector<SysTree>& sys) {
     parallel_for(ncs, 8192, [&](int64_t a, int64_t b) {
       for (int64_t c = a; c < b; ++c) {
         const int64_t g = c0 + c;
-        t->key[g] = T.key[c];
+        if (!single) t->key[g] = T.key[c];
         const double* cu = &T.cube[4 * c];
         t->geo[g] = make_float4(static_cast<float>(cu[0]), static_cast<float>(cu[1]),
                                 static_cast<float>(cu[2]), static_cast<float>(cu[3]));
@@ -747,18 +784,30 @@ int assemble(octgrav_tree* t, std::vector<SysTree>& sys) {
                                        static_cast<float>(3.0 * s6[2]), static_cast<float>(3.0 * s6[3]));
         t->mp[4 * g + 3] = make_float4(static_cast<float>(3.0 * s6[4]), static_cast<float>(3.0 * s6[5]),
                                        static_cast<float>(1.5 * tr), static_cast<float>(0.5 * tr));
-        for (int d = 0; d < 3; ++d) {
-          t->bmin[3 * g + d] = T.bmin[3 * c + d];
-          t->bmax[3 * g + d] = T.bmax[3 * c + d];
-          t->com[3 * g + d] = cm[d];
+        if (!single) {
+          for (int d = 0; d < 3; ++d) {
+            t->bmin[3 * g + d] = T.bmin[3 * c + d];
+            t->bmax[3 * g + d] = T.bmax[3 * c + d];
+            t->com[3 * g + d] = cm[d];
+          }
+          for (int d = 0; d < 4; ++d) t->cube[4 * g + d] = cu[d];
+          for (int d = 0; d < 6; ++d) t->S[6 * g + d] = s6[d];
+          t->M[g] = T.M[c];
+          t->pcount[g] = T.pcount[c];
         }
-        for (int d = 0; d < 4; ++d) t->cube[4 * g + d] = cu[d];
-        for (int d = 0; d < 6; ++d) t->S[6 * g + d] = s6[d];
-        t->M[g] = T.M[c];
-        t->pcount[g] = T.pcount[c];
         t->cfirst[g] = static_cast<int32_t>(p0 + T.pfirst[c]);
       }
     });
+    if (single) {  // the global arrays are this system's
+      t->key = std::move(T.key);
+      t->bmin = std::move(T.bmin);
+      t->bmax = std::move(T.bmax);
+      t->cube = std::move(T.cube);
+      t->M = std::move(T.M);
+      t->com = std::move(T.com);
+      t->S = std::move(T.S);
+      t->pcount = std::move(T.pcount);
+    }
     for (int32_t gc : T.groups) {
       t->group_cell.push_back(static_cast<int32_t>(c0 + gc));
       t->group_sys.push_back(s);
@@ -785,8 +834,57 @@ int check_inputs(const double* pos, const double* mass, int64_t n) {
   return bad.load() ? fail(OCTGRAV_ERR_NONFINITE, "non-finite position/mass or negative mass") : OCTGRAV_OK;
 }
 
+// Host memory reused by a thread's one-shot calls: the per-system build
+// arrays, the tree's host images and the download buffer keep their pages from
+// call to call (at N = 1M a call otherwise touches ~200 MB of fresh memory).
+struct HostCache {
+  std::vector<SysTree> sys;
+  octgrav_tree spare;  // holds the image vectors between calls
+  std::vector<float4> h;
+};
+
+void swap_images(octgrav_tree& a, octgrav_tree& b) {
+  std::swap(a.perm, b.perm);
+  std::swap(a.parts, b.parts);
+  std::swap(a.geo, b.geo);
+  std::swap(a.link, b.link);
+  std::swap(a.mp, b.mp);
+  std::swap(a.items, b.items);
+  std::swap(a.ibox, b.ibox);
+  std::swap(a.item_key, b.item_key);
+  std::swap(a.key, b.key);
+  std::swap(a.bmin, b.bmin);
+  std::swap(a.bmax, b.bmax);
+  std::swap(a.cube, b.cube);
+  std::swap(a.M, b.M);
+  std::swap(a.com, b.com);
+  std::swap(a.S, b.S);
+  std::swap(a.pcount, b.pcount);
+  std::swap(a.cfirst, b.cfirst);
+  std::swap(a.group_cell, b.group_cell);
+  std::swap(a.group_sys, b.group_sys);
+  std::swap(a.group_item, b.group_item);
+  std::swap(a.item_order, b.item_order);
+}
+
+// Return a one-shot tree's memory to the cache before the tree is freed.
+void give_back(octgrav_tree* t, HostCache* cache) {
+  if (cache->sys.size() == 1) {  // these were moved out of the system's arrays
+    SysTree& T = cache->sys[0];
+    std::swap(t->key, T.key);
+    std::swap(t->bmin, T.bmin);
+    std::swap(t->bmax, T.bmax);
+    std::swap(t->cube, T.cube);
+    std::swap(t->M, T.M);
+    std::swap(t->com, T.com);
+    std::swap(t->S, T.S);
+    std::swap(t->pcount, T.pcount);
+  }
+  swap_images(*t, cache->spare);
+}
+
 int build_common(int n_sys, const int64_t* offsets, const double* pos, const double* mass, int n_leaf,
-                 int n_group, octgrav_tree** out) {
+                 int n_group, octgrav_tree** out, HostCache* cache = nullptr) {
   if (!out) return fail(OCTGRAV_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (!pos || !mass || !offsets || n_sys < 1) return fail(OCTGRAV_ERR_ARG, "NULL input or n_sys < 1");
@@ -806,7 +904,10 @@ int build_common(int n_sys, const int64_t* offsets, const double* pos, const dou
     t->n_group = n_group;
     t->n_sys = n_sys;
     t->sys_off.assign(offsets, offsets + n_sys + 1);
-    std::vector<SysTree> sys(n_sys);
+    std::vector<SysTree> local;
+    std::vector<SysTree>& sys = cache ? cache->sys : local;
+    sys.resize(n_sys);  // build_system empties each (reused memory stays)
+    if (cache) swap_images(*t, cache->spare);
     std::vector<int> rcs(n_sys, 0);
     if (n_sys == 1) {
       rcs[0] = build_system(pos, mass, n, n_leaf, n_group, true, sys[0]);
@@ -972,7 +1073,7 @@ int forces_dev64(octgrav_tree* t, double eps, double theta, double G, double* ac
 }
 
 int forces_host(octgrav_tree* t, double eps, double theta, double G, double* acc, double* pot,
-                cudaStream_t st) {
+                cudaStream_t st, std::vector<float4>* hbuf = nullptr) {
   if (!acc) return fail(OCTGRAV_ERR_ARG, "acc is NULL");
   int rc = check_params(eps, theta, G);
   if (rc) return rc;
@@ -991,7 +1092,9 @@ int forces_host(octgrav_tree* t, double eps, double theta, double G, double* acc
   if ((rc = t->dev->out.reserve(sizeof(float4) * t->n))) return rc;
   if ((rc = launch(t, eps, theta, G, static_cast<float4*>(t->dev->out.p), st, false, nullptr, nullptr, nullptr, 0)))
     return rc;
-  std::vector<float4> h(t->n);
+  std::vector<float4> local;
+  std::vector<float4>& h = hbuf ? *hbuf : local;
+  h.resize(t->n);
   CUDA_TRY(cudaMemcpyAsync(h.data(), t->dev->out.p, sizeof(float4) * t->n, cudaMemcpyDeviceToHost, st));
   if ((rc = read_status(t, st))) return rc;
   parallel_for(t->n, 65536, [&](int64_t a, int64_t b) {
@@ -1327,11 +1430,15 @@ int octgrav_forces_ex(const double* pos, const double* mass, int64_t n, double e
                       int n_leaf, int n_group, double* acc, double* pot, void* stream) {
   int rc = check_params(eps, theta, G);
   if (rc) return rc;
+  if (n < 1) return fail(OCTGRAV_ERR_ARG, "n must be >= 1");
+  thread_local HostCache hcache;
+  const int64_t off[2] = {0, n};
   octgrav_tree* t = nullptr;
-  if ((rc = octgrav_build_tree(pos, mass, n, n_leaf, n_group, &t))) return rc;
+  if ((rc = build_common(1, off, pos, mass, n_leaf, n_group, &t, &hcache))) return rc;
   if (!tl_cache) tl_cache = new Device();
   t->dev = tl_cache;
-  rc = forces_host(t, eps, theta, G, acc, pot, static_cast<cudaStream_t>(stream));
+  rc = forces_host(t, eps, theta, G, acc, pot, static_cast<cudaStream_t>(stream), &hcache.h);
+  give_back(t, &hcache);
   octgrav_free_tree(t);
   return rc;
 }
