@@ -724,7 +724,7 @@ def main():
         "e2e": None if host_s != host_s else {
             "value": world * a.n / host_s, "unit": "forces/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "seconds_per_step": host_s,
-            "path": "octgrav_forces_ex (the north-star split: host FP64 tree build, upload, kernel, download, "
+            "path": "octgrav_forces_ex (the paper's split, Sec. 2: host FP64 tree build, upload, kernel, download, "
                     "host unpermute)",
             "gpu_build_path": None if e2e_s != e2e_s else {
                 "value": world * a.n / e2e_s, "unit": "forces/s", "h2d_bytes_per_step": h2d_gpu,
