@@ -20,6 +20,7 @@
 // these operations one for one.
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <condition_variable>
 #include <cstdarg>
@@ -31,6 +32,8 @@
 #include <new>
 #include <string>
 #include <thread>
+#include <type_traits>
+#include <utility>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -42,6 +45,32 @@
 namespace {
 
 constexpr int kMaxDepth = OCTGRAV_MAX_DEPTH;
+
+// Allocator whose construct() without arguments default-initialises, so that
+// resize() of a vector of plain numbers leaves the new elements unwritten. The
+// build's arrays are all filled completely (in parallel) right after they are
+// sized; value-initialisation would first zero them on one thread (~200 MB per
+// million particles).
+template <class T>
+struct NoInit : std::allocator<T> {
+  template <class U>
+  struct rebind {
+    using other = NoInit<U>;
+  };
+  NoInit() = default;
+  template <class U>
+  NoInit(const NoInit<U>&) noexcept {}
+  template <class U>
+  void construct(U* p) noexcept(std::is_nothrow_default_constructible<U>::value) {
+    ::new (static_cast<void*>(p)) U;
+  }
+  template <class U, class... A>
+  void construct(U* p, A&&... a) {
+    ::new (static_cast<void*>(p)) U(std::forward<A>(a)...);
+  }
+};
+template <class T>
+using hvec = std::vector<T, NoInit<T>>;
 
 // ---------------------------------------------------------------- errors
 
@@ -75,25 +104,29 @@ class Pool {
   int size() const { return static_cast<int>(threads_.size()) + 1; }
 
   // Run fn(chunk) for chunk in [0, nchunks) on all workers and the caller.
+  // Workers spin for a short while after a job before they sleep, so the many
+  // short parallel loops of a build do not each pay a wake-up of every thread.
   void run(int nchunks, const std::function<void(int)>& fn) {
     if (nchunks <= 0) return;
     if (threads_.empty() || nchunks == 1 || in_pool_) {
       for (int c = 0; c < nchunks; ++c) fn(c);
       return;
     }
-    std::unique_lock<std::mutex> lk(run_mu_);  // one parallel region at a time
-    {
-      std::lock_guard<std::mutex> g(mu_);
-      job_ = &fn;
-      nchunks_ = nchunks;
-      next_.store(0);
-      pending_ = static_cast<int>(threads_.size());
-      ++gen_;
+    std::lock_guard<std::mutex> one(run_mu_);  // one parallel region at a time
+    job_ = &fn;
+    nchunks_ = nchunks;
+    next_.store(0, std::memory_order_relaxed);
+    pending_.store(static_cast<int>(threads_.size()), std::memory_order_relaxed);
+    gen_.fetch_add(1, std::memory_order_seq_cst);
+    if (sleepers_.load(std::memory_order_seq_cst) > 0) {
+      { std::lock_guard<std::mutex> g(mu_); }
+      cv_.notify_all();
     }
-    cv_.notify_all();
     work();
-    std::unique_lock<std::mutex> g(mu_);
-    done_cv_.wait(g, [&] { return pending_ == 0; });
+    if (!spin_until([&] { return pending_.load(std::memory_order_acquire) == 0; })) {
+      std::unique_lock<std::mutex> g(mu_);
+      done_cv_.wait(g, [&] { return pending_.load(std::memory_order_acquire) == 0; });
+    }
     job_ = nullptr;
   }
 
@@ -106,18 +139,27 @@ class Pool {
     for (int t = 1; t < n; ++t) threads_.emplace_back([this] { loop(); });
   }
   ~Pool() {
+    stop_.store(true);
+    gen_.fetch_add(1, std::memory_order_release);
     {
       std::lock_guard<std::mutex> g(mu_);
-      stop_ = true;
-      ++gen_;
     }
     cv_.notify_all();
     for (auto& t : threads_) t.join();
   }
+  // Spin until pred() holds or ~50 us have passed; true if it holds.
+  template <class P>
+  static bool spin_until(P pred) {
+    auto t0 = std::chrono::steady_clock::now();
+    for (int k = 0;; ++k) {
+      if (pred()) return true;
+      if ((k & 255) == 255 && std::chrono::steady_clock::now() - t0 > std::chrono::microseconds(50)) return pred();
+    }
+  }
   void work() {
     in_pool_ = true;
     for (;;) {
-      int c = next_.fetch_add(1);
+      int c = next_.fetch_add(1, std::memory_order_relaxed);
       if (c >= nchunks_) break;
       (*job_)(c);
     }
@@ -126,16 +168,18 @@ class Pool {
   void loop() {
     uint64_t seen = 0;
     for (;;) {
-      {
+      if (!spin_until([&] { return gen_.load(std::memory_order_acquire) != seen; })) {
         std::unique_lock<std::mutex> g(mu_);
-        cv_.wait(g, [&] { return gen_ != seen; });
-        seen = gen_;
-        if (stop_) return;
+        sleepers_.fetch_add(1, std::memory_order_seq_cst);
+        cv_.wait(g, [&] { return gen_.load(std::memory_order_seq_cst) != seen; });
+        sleepers_.fetch_sub(1, std::memory_order_relaxed);
       }
+      seen = gen_.load(std::memory_order_acquire);
+      if (stop_.load()) return;
       work();
-      {
-        std::lock_guard<std::mutex> g(mu_);
-        if (--pending_ == 0) done_cv_.notify_all();
+      if (pending_.fetch_sub(1, std::memory_order_acq_rel) == 1) {
+        { std::lock_guard<std::mutex> g(mu_); }
+        done_cv_.notify_all();
       }
     }
   }
@@ -145,9 +189,10 @@ class Pool {
   const std::function<void(int)>* job_ = nullptr;
   int nchunks_ = 0;
   std::atomic<int> next_{0};
-  int pending_ = 0;
-  uint64_t gen_ = 0;
-  bool stop_ = false;
+  std::atomic<int> pending_{0};
+  std::atomic<int> sleepers_{0};
+  std::atomic<uint64_t> gen_{0};
+  std::atomic<bool> stop_{false};
   static thread_local bool in_pool_;
 };
 thread_local bool Pool::in_pool_ = false;
@@ -180,17 +225,17 @@ inline uint64_t spread21(uint64_t v) {
   return v;
 }
 
-// Stable LSD radix sort of (key, val) by key (63 significant bits, 7 x 9-bit digits).
-void radix_sort(std::vector<uint64_t>& key, std::vector<uint32_t>& val, std::vector<uint64_t>& k2,
-                std::vector<uint32_t>& v2, bool parallel) {
+// Stable LSD radix sort of (key, val) by key (63 significant bits, 9-bit digits).
+void radix_sort(hvec<uint64_t>& key, hvec<uint32_t>& val, hvec<uint64_t>& k2, hvec<uint32_t>& v2,
+                bool parallel) {
   const int64_t n = static_cast<int64_t>(key.size());
   k2.resize(n);
   v2.resize(n);
-  constexpr int BITS = 9, B = 1 << BITS;
+  constexpr int BITS = 9, B = 1 << BITS, PASSES = (63 + BITS - 1) / BITS;
   const int T = parallel ? std::max(1, std::min<int>(Pool::get().size(), static_cast<int>(n / 65536))) : 1;
   std::vector<int64_t> hist(static_cast<size_t>(T) * B);
   const int64_t step = (n + T - 1) / T;
-  for (int pass = 0; pass < 7; ++pass) {
+  for (int pass = 0; pass < PASSES; ++pass) {
     const int sh = pass * BITS;
     auto body_hist = [&](int t) {
       int64_t* h = &hist[static_cast<size_t>(t) * B];
@@ -225,23 +270,25 @@ void radix_sort(std::vector<uint64_t>& key, std::vector<uint32_t>& val, std::vec
 
 struct SysTree {
   int64_t n = 0;
-  std::vector<uint32_t> perm;  // tree position -> index within the system
-  std::vector<uint64_t> code;  // Morton code per tree position
-  std::vector<double> x;       // 3 per tree position
-  std::vector<double> m;
+  hvec<uint32_t> perm;  // tree position -> index within the system
+  hvec<uint64_t> code;  // Morton code per tree position
+  hvec<double> x;       // 3 per tree position
+  hvec<double> m;
   // cells in breadth-first order (children of a node are contiguous)
-  std::vector<uint64_t> key;
-  std::vector<int32_t> depth, parent, first_child, n_child;
-  std::vector<int64_t> pfirst, pcount;
-  std::vector<double> bmin, bmax, cube, M, com, S;  // 3, 3, 4, 1, 3, 6 per cell
-  std::vector<int32_t> groups;                      // cell index, tree (Morton) order
+  hvec<uint64_t> key;
+  hvec<int32_t> depth, parent, first_child, n_child;
+  hvec<int64_t> pfirst, pcount;
+  hvec<double> bmin, bmax, cube, M, com, S;  // 3, 3, 4, 1, 3, 6 per cell
+  hvec<int32_t> groups;                      // cell index, tree (Morton) order
   int depth_reached = 0;
   int64_t max_group = 0;
   int64_t n_leaves = 0;
   // scratch of the build (kept so that a reused SysTree allocates nothing)
-  std::vector<uint64_t> k2;
-  std::vector<uint32_t> v2;
-  std::vector<uint8_t> covered;
+  hvec<uint64_t> k2;
+  hvec<uint32_t> v2;
+  hvec<int64_t> splits;                      // 9 per cell of the level being split
+  std::vector<int32_t> nch;                  // children per cell of that level
+  std::vector<int64_t> child_base;           // first child per chunk of that level
   // empty every array but keep its memory, for a new build
   void reset() {
     n = 0;
@@ -249,9 +296,9 @@ struct SysTree {
     for (auto* v : {&code, &key, &k2}) v->clear();
     for (auto* v : {&x, &m, &bmin, &bmax, &cube, &M, &com, &S}) v->clear();
     for (auto* v : {&depth, &parent, &first_child, &n_child, &groups}) v->clear();
-    pfirst.clear();
-    pcount.clear();
-    covered.clear();
+    for (auto* v : {&pfirst, &pcount, &splits}) v->clear();
+    nch.clear();
+    child_base.clear();
     depth_reached = 0;
     max_group = 0;
     n_leaves = 0;
@@ -304,8 +351,8 @@ int build_system(const double* pos, const double* mass, int64_t n, int n_leaf, i
   const uint64_t qmax = (1ull << kMaxDepth) - 1;
 
   // ---- Morton codes and sort
-  std::vector<uint64_t>& code = T.code;
-  std::vector<uint32_t>& idx = T.perm;
+  hvec<uint64_t>& code = T.code;
+  hvec<uint32_t>& idx = T.perm;
   code.resize(n);
   idx.resize(n);
   parallel_for(n, grain, [&](int64_t a, int64_t b) {
@@ -324,7 +371,14 @@ int build_system(const double* pos, const double* mass, int64_t n, int n_leaf, i
   T.x.resize(3 * n);
   T.m.resize(n);
   parallel_for(n, grain, [&](int64_t a, int64_t b) {
+    constexpr int64_t ahead = 16;  // prefetch distance of the random reads
     for (int64_t t = a; t < b; ++t) {
+      if (t + ahead < b) {
+        const int64_t j = T.perm[t + ahead];
+        __builtin_prefetch(pos + 3 * j);
+        __builtin_prefetch(pos + 3 * j + 2);
+        __builtin_prefetch(mass + j);
+      }
       const int64_t i = T.perm[t];
       T.x[3 * t] = pos[3 * i];
       T.x[3 * t + 1] = pos[3 * i + 1];
@@ -352,18 +406,28 @@ int build_system(const double* pos, const double* mass, int64_t n, int n_leaf, i
   }
   push_cell(1, 0, -1, 0, n);
   std::vector<int64_t> level_begin = {0};
-  std::vector<int64_t> splits;  // 9 per cell of the level being split
+  hvec<int64_t>& splits = T.splits;  // read only where nch > 0
+  std::vector<int32_t>& nch = T.nch;
+  std::vector<int64_t>& child_base = T.child_base;
   for (int L = 0;; ++L) {
     const int64_t lb = level_begin.back(), le = static_cast<int64_t>(T.key.size());
     if (lb == le) break;
     const int64_t nl = le - lb;
-    splits.assign(9 * nl, 0);
-    std::vector<int32_t> nch(nl, 0);
-    parallel_for(nl, parallel ? 512 : (int64_t)1 << 62, [&](int64_t a, int64_t b) {
-      for (int64_t k = a; k < b; ++k) {
+    splits.resize(9 * nl);
+    nch.resize(nl);
+    // the level in fixed chunks: a first pass counts each chunk's children, a
+    // scan over the chunk totals places them in breadth-first order, and a
+    // second pass writes them
+    const int64_t nchunk = parallel ? std::min<int64_t>(8 * Pool::get().size(), std::max<int64_t>(1, nl / 256)) : 1;
+    const int64_t cstep = (nl + nchunk - 1) / nchunk;
+    child_base.assign(nchunk + 1, 0);
+    auto split_chunk = [&](int q) {
+      int64_t total = 0;
+      for (int64_t k = q * cstep; k < std::min(nl, (q + 1) * cstep); ++k) {
         const int64_t c = lb + k;
         const int64_t f = T.pfirst[c], cnt = T.pcount[c];
         int64_t* sp = &splits[9 * k];
+        nch[k] = 0;
         if (cnt <= n_leaf || L >= kMaxDepth) continue;
         sp[0] = f;
         sp[8] = f + cnt;
@@ -377,14 +441,13 @@ int build_system(const double* pos, const double* mass, int64_t n, int n_leaf, i
         int k8 = 0;
         for (int o = 0; o < 8; ++o) k8 += sp[o + 1] > sp[o];
         nch[k] = k8;
+        total += k8;
       }
-    });
-    int64_t next = le;
-    std::vector<int64_t> child_base(nl);
-    for (int64_t k = 0; k < nl; ++k) {
-      child_base[k] = next;
-      next += nch[k];
-    }
+      child_base[q + 1] = total;
+    };
+    Pool::get().run(static_cast<int>(nchunk), split_chunk);
+    for (int64_t q = 0; q < nchunk; ++q) child_base[q + 1] += child_base[q];
+    const int64_t next = le + child_base[nchunk];
     if (next == le) break;
     level_begin.push_back(le);
     if (next >= (1ll << 28)) return fail(OCTGRAV_ERR_ARG, "tree too large (%lld cells)", (long long)next);
@@ -395,11 +458,11 @@ int build_system(const double* pos, const double* mass, int64_t n, int n_leaf, i
     T.n_child.resize(next);
     T.pfirst.resize(next);
     T.pcount.resize(next);
-    parallel_for(nl, parallel ? 2048 : (int64_t)1 << 62, [&](int64_t a, int64_t b) {
-      for (int64_t k = a; k < b; ++k) {
+    auto emit_chunk = [&](int q) {
+      int64_t w = le + child_base[q];
+      for (int64_t k = q * cstep; k < std::min(nl, (q + 1) * cstep); ++k) {
         if (!nch[k]) continue;
         const int64_t c = lb + k;
-        int64_t w = child_base[k];
         T.first_child[c] = static_cast<int32_t>(w);
         T.n_child[c] = nch[k];
         const int64_t* sp = &splits[9 * k];
@@ -415,7 +478,8 @@ int build_system(const double* pos, const double* mass, int64_t n, int n_leaf, i
           ++w;
         }
       }
-    });
+    };
+    Pool::get().run(static_cast<int>(nchunk), emit_chunk);
   }
   const int64_t nc = static_cast<int64_t>(T.key.size());
   T.depth_reached = static_cast<int>(level_begin.size()) - 1;
@@ -505,17 +569,29 @@ int build_system(const double* pos, const double* mass, int64_t n, int n_leaf, i
     });
   }
 
-  // ---- groups: first cells from the root that are leaves or hold <= n_group
-  std::vector<uint8_t>& covered = T.covered;
-  covered.assign(nc, 0);
-  T.n_leaves = 0;
-  for (int64_t c = 0; c < nc; ++c) {
-    const bool par = c > 0 && covered[T.parent[c]];
-    const bool leaf = T.n_child[c] == 0;
-    T.n_leaves += leaf;
-    const bool elig = leaf || T.pcount[c] <= n_group;
-    if (!par && elig) T.groups.push_back(static_cast<int32_t>(c));
-    covered[c] = par || elig;
+  // ---- groups: first cells from the root that are leaves or hold <= n_group.
+  // Such eligibility passes from a cell to its children (a child of a leaf does
+  // not exist, and a child never holds more particles than its parent), so the
+  // first eligible cells on the paths from the root are the eligible cells
+  // whose parent is not eligible.
+  auto eligible = [&](int64_t c) { return T.n_child[c] == 0 || T.pcount[c] <= n_group; };
+  {
+    const int64_t chunks = parallel ? std::min<int64_t>(64, std::max<int64_t>(1, nc / 8192)) : 1;
+    const int64_t step = (nc + chunks - 1) / chunks;
+    std::vector<std::vector<int32_t>> found(chunks);
+    std::vector<int64_t> leaves(chunks, 0);
+    auto body = [&](int k) {
+      for (int64_t c = k * step; c < std::min(nc, (k + 1) * step); ++c) {
+        leaves[k] += T.n_child[c] == 0;
+        if (eligible(c) && (c == 0 || !eligible(T.parent[c]))) found[k].push_back(static_cast<int32_t>(c));
+      }
+    };
+    if (chunks > 1) Pool::get().run(static_cast<int>(chunks), body); else body(0);
+    T.n_leaves = 0;
+    for (int64_t k = 0; k < chunks; ++k) {
+      T.n_leaves += leaves[k];
+      T.groups.insert(T.groups.end(), found[k].begin(), found[k].end());
+    }
   }
   std::sort(T.groups.begin(), T.groups.end(),
             [&](int32_t a, int32_t b) { return T.pfirst[a] < T.pfirst[b]; });
@@ -598,21 +674,21 @@ struct octgrav_tree {
   CUtensorMap mp_map;
   std::vector<int64_t> sys_off;   // particle offsets per system (n_sys + 1)
   std::vector<int64_t> cell_off;  // cell offsets per system (n_sys + 1)
-  std::vector<int64_t> perm;      // tree position -> input index
-  std::vector<uint64_t> key;      // per global cell
+  hvec<int64_t> perm;             // tree position -> input index
+  hvec<uint64_t> key;             // per global cell
   std::vector<int32_t> group_cell;  // per group, global cell index
   std::vector<int32_t> group_sys;
   int64_t n_cells = 0, n_leaves = 0, max_group = 0;
   int depth_reached = 0;
   // host images of the device arrays
-  std::vector<float4> parts, geo, mp, ibox;
-  std::vector<int2> link;
-  std::vector<int4> items;
-  std::vector<uint64_t> item_key;
+  hvec<float4> parts, geo, mp, ibox;
+  hvec<int2> link;
+  hvec<int4> items;
+  hvec<uint64_t> item_key;
   // host FP64 cell properties (tests / introspection)
-  std::vector<double> bmin, bmax, cube, M, com, S;
-  std::vector<int64_t> pcount;
-  std::vector<int32_t> cfirst;    // first particle (tree position) of every cell
+  hvec<double> bmin, bmax, cube, M, com, S;
+  hvec<int64_t> pcount;
+  hvec<int32_t> cfirst;           // first particle (tree position) of every cell
   std::vector<int32_t> group_item;  // first work item of every group
   // per-system parameters (optional)
   std::vector<float4> sysp;
@@ -629,7 +705,7 @@ struct octgrav_tree {
   bool perm_on_device = false;  // Device::perm holds the permutation (int32)
   int64_t n_groups = 0, n_items = 0;
   bool ordered = false;  // launches take the work items in Device::order (octgrav_balance)
-  std::vector<int32_t> item_order;  // host image of the default order (host-built trees)
+  hvec<int32_t> item_order;  // host image of the default order (host-built trees)
   int64_t cell_cap = 0;  // cell capacity of the device arrays of a GPU-built tree
   cudaGraphExec_t gexec = nullptr;  // captured memset + kernel (octgrav_graph_capture)
   std::vector<SysTree> sys_scratch;
@@ -840,7 +916,7 @@ int check_inputs(const double* pos, const double* mass, int64_t n) {
 struct HostCache {
   std::vector<SysTree> sys;
   octgrav_tree spare;  // holds the image vectors between calls
-  std::vector<float4> h;
+  hvec<float4> h;
 };
 
 void swap_images(octgrav_tree& a, octgrav_tree& b) {
@@ -1073,7 +1149,7 @@ int forces_dev64(octgrav_tree* t, double eps, double theta, double G, double* ac
 }
 
 int forces_host(octgrav_tree* t, double eps, double theta, double G, double* acc, double* pot,
-                cudaStream_t st, std::vector<float4>* hbuf = nullptr) {
+                cudaStream_t st, hvec<float4>* hbuf = nullptr) {
   if (!acc) return fail(OCTGRAV_ERR_ARG, "acc is NULL");
   int rc = check_params(eps, theta, G);
   if (rc) return rc;
@@ -1092,8 +1168,8 @@ int forces_host(octgrav_tree* t, double eps, double theta, double G, double* acc
   if ((rc = t->dev->out.reserve(sizeof(float4) * t->n))) return rc;
   if ((rc = launch(t, eps, theta, G, static_cast<float4*>(t->dev->out.p), st, false, nullptr, nullptr, nullptr, 0)))
     return rc;
-  std::vector<float4> local;
-  std::vector<float4>& h = hbuf ? *hbuf : local;
+  hvec<float4> local;
+  hvec<float4>& h = hbuf ? *hbuf : local;
   h.resize(t->n);
   CUDA_TRY(cudaMemcpyAsync(h.data(), t->dev->out.p, sizeof(float4) * t->n, cudaMemcpyDeviceToHost, st));
   if ((rc = read_status(t, st))) return rc;
@@ -1343,21 +1419,22 @@ int host_images(octgrav_tree* t) {
   }
   const double* pr = static_cast<const double*>(D.props.p);
   const int* gb = static_cast<const int*>(D.groups.p);
+  const size_t zn = n, znc = nc, zni = ni, zng = ng;
   struct Copy {
     void* dst;
     const void* src;
     size_t bytes;
   } copies[] = {
-      {t->parts.data(), D.parts.p, 32 * n},         {t->geo.data(), D.geo.p, 16 * nc},
-      {t->link.data(), D.link.p, 8 * nc},           {t->mp.data(), D.mp.p, 64 * nc},
-      {t->items.data(), D.items.p, 16 * ni},        {t->ibox.data(), D.ibox.p, 64 * ni},
-      {t->item_key.data(), D.ikey.p, 8 * ni},       {t->key.data(), D.key.p, 8 * nc},
-      {p32.data(), D.perm.p, 4 * n},                {t->bmin.data(), pr, 24 * nc},
-      {t->bmax.data(), pr + 3 * cap, 24 * nc},      {t->cube.data(), pr + 6 * cap, 32 * nc},
-      {t->M.data(), pr + 10 * cap, 8 * nc},         {t->com.data(), pr + 11 * cap, 24 * nc},
-      {t->S.data(), pr + 14 * cap, 48 * nc},        {c32.data(), D.pcount.p, 4 * nc},
-      {t->cfirst.data(), D.cfirst.p, 4 * nc},       {t->group_cell.data(), gb, 4 * ng},
-      {t->group_sys.data(), gb + n, 4 * ng},        {t->group_item.data(), gb + 2 * n, 4 * ng},
+      {t->parts.data(), D.parts.p, 32 * zn},         {t->geo.data(), D.geo.p, 16 * znc},
+      {t->link.data(), D.link.p, 8 * znc},           {t->mp.data(), D.mp.p, 64 * znc},
+      {t->items.data(), D.items.p, 16 * zni},        {t->ibox.data(), D.ibox.p, 64 * zni},
+      {t->item_key.data(), D.ikey.p, 8 * zni},       {t->key.data(), D.key.p, 8 * znc},
+      {p32.data(), D.perm.p, 4 * zn},                {t->bmin.data(), pr, 24 * znc},
+      {t->bmax.data(), pr + 3 * cap, 24 * znc},      {t->cube.data(), pr + 6 * cap, 32 * znc},
+      {t->M.data(), pr + 10 * cap, 8 * znc},         {t->com.data(), pr + 11 * cap, 24 * znc},
+      {t->S.data(), pr + 14 * cap, 48 * znc},        {c32.data(), D.pcount.p, 4 * znc},
+      {t->cfirst.data(), D.cfirst.p, 4 * znc},       {t->group_cell.data(), gb, 4 * zng},
+      {t->group_sys.data(), gb + n, 4 * zng},        {t->group_item.data(), gb + 2 * n, 4 * zng},
   };
   for (const Copy& c : copies)
     if (c.bytes) CUDA_TRY(cudaMemcpy(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost));
@@ -1803,7 +1880,7 @@ int octgrav_balance(octgrav_tree* t, int mode, void* stream) {
   if (rc) return rc;
   if (ni) CUDA_TRY(cudaMemcpyAsync(t->dev->order.p, order.data(), 4 * ni, cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaStreamSynchronize(st));
-  if (!t->gpu) t->item_order = order;  // a later re-upload keeps it
+  if (!t->gpu) t->item_order.assign(order.begin(), order.end());  // a later re-upload keeps it
   t->ordered = true;
   return OCTGRAV_OK;
 }
