@@ -697,10 +697,11 @@ def main():
     e2e_s = statistics.mean(e2e_t[1:]) if len(e2e_t) > 1 else float("nan")
     host_s = statistics.mean(host_t[1:]) if len(host_t) > 1 else float("nan")
     s = T.stats
-    # host-build path: the tree's device arrays go up (particles 32 B, cells 16 + 8 + 64 B,
-    # items 16 + 64 B) and the float4 results come back
-    h2d = 32 * a.n + 88 * s["n_cells"] + 80 * s["n_items"]
-    d2h = 16 * a.n
+    # host-build path: the tree's device arrays go up (particles 32 B + the int32 permutation,
+    # cells 16 + 8 + 64 B, items 16 + 64 B + the 4-byte processing order) and the FP64
+    # results, unpermuted on the device, come back (24 + 8 B per particle)
+    h2d = 36 * a.n + 88 * s["n_cells"] + 84 * s["n_items"]
+    d2h = 32 * a.n
     h2d_gpu = 32 * a.n  # GPU-build path: positions (24 B) and masses (8 B)
     d2h_gpu = 32 * a.n  # accelerations (24 B) and potentials (8 B), FP64
 
@@ -724,8 +725,8 @@ def main():
         "e2e": None if host_s != host_s else {
             "value": world * a.n / host_s, "unit": "forces/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "seconds_per_step": host_s,
-            "path": "octgrav_forces_ex (the paper's split, Sec. 2: host FP64 tree build, upload, kernel, download, "
-                    "host unpermute)",
+            "path": "octgrav_forces_ex (the paper's split, Sec. 2: host FP64 tree build, upload, kernel, device "
+                    "unpermute, FP64 download)",
             "gpu_build_path": None if e2e_s != e2e_s else {
                 "value": world * a.n / e2e_s, "unit": "forces/s", "h2d_bytes_per_step": h2d_gpu,
                 "d2h_bytes_per_step": d2h_gpu, "seconds_per_step": e2e_s,

@@ -675,6 +675,7 @@ struct octgrav_tree {
   std::vector<int64_t> sys_off;   // particle offsets per system (n_sys + 1)
   std::vector<int64_t> cell_off;  // cell offsets per system (n_sys + 1)
   hvec<int64_t> perm;             // tree position -> input index
+  hvec<int32_t> perm32;           // the same as int32, the device image
   hvec<uint64_t> key;             // per global cell
   std::vector<int32_t> group_cell;  // per group, global cell index
   std::vector<int32_t> group_sys;
@@ -798,6 +799,7 @@ int assemble(octgrav_tree* t, std::vector<SysTree>& sys) {
   // one system: its FP64 cell arrays are moved, not copied, after the loop below
   const bool single = ns == 1;
   t->perm.resize(t->n);
+  t->perm32.resize(t->n);
   t->parts.resize(2 * t->n);
   t->geo.resize(nc);
   t->link.resize(nc);
@@ -825,6 +827,7 @@ int assemble(octgrav_tree* t, std::vector<SysTree>& sys) {
     parallel_for(n, 16384, [&](int64_t a, int64_t b) {
       for (int64_t k = a; k < b; ++k) {
         t->perm[p0 + k] = p0 + T.perm[k];
+        t->perm32[p0 + k] = static_cast<int32_t>(p0 + T.perm[k]);
         float hi[3], lo[3];
         for (int d = 0; d < 3; ++d) {
           const double v = T.x[3 * k + d];
@@ -911,16 +914,16 @@ int check_inputs(const double* pos, const double* mass, int64_t n) {
 }
 
 // Host memory reused by a thread's one-shot calls: the per-system build
-// arrays, the tree's host images and the download buffer keep their pages from
-// call to call (at N = 1M a call otherwise touches ~200 MB of fresh memory).
+// arrays and the tree's host images keep their pages from call to call (at
+// N = 1M a call otherwise touches ~200 MB of fresh memory).
 struct HostCache {
   std::vector<SysTree> sys;
   octgrav_tree spare;  // holds the image vectors between calls
-  hvec<float4> h;
 };
 
 void swap_images(octgrav_tree& a, octgrav_tree& b) {
   std::swap(a.perm, b.perm);
+  std::swap(a.perm32, b.perm32);
   std::swap(a.parts, b.parts);
   std::swap(a.geo, b.geo);
   std::swap(a.link, b.link);
@@ -1026,9 +1029,9 @@ int upload(octgrav_tree* t, cudaStream_t st) {
     if ((rc = upload_vec(D.parts, t->parts, st)) || (rc = upload_vec(D.geo, t->geo, st)) ||
         (rc = upload_vec(D.link, t->link, st)) || (rc = upload_vec(D.mp, t->mp, st)) ||
         (rc = upload_vec(D.items, t->items, st)) || (rc = upload_vec(D.ibox, t->ibox, st)) ||
-        (rc = upload_vec(D.order, t->item_order, st)))
+        (rc = upload_vec(D.order, t->item_order, st)) || (rc = upload_vec(D.perm, t->perm32, st)))
       return rc;
-    t->perm_on_device = false;
+    t->perm_on_device = true;
   }
   if ((rc = D.counts.reserve(t->n_items * sizeof(int2)))) return rc;
   if ((rc = D.ctl.reserve(64))) return rc;
@@ -1121,12 +1124,14 @@ int read_status(octgrav_tree* t, cudaStream_t st) {
 // The permutation on the device (int32); uploaded once for a host-built tree.
 int device_perm(octgrav_tree* t, cudaStream_t st) {
   if (t->gpu || t->perm_on_device) return OCTGRAV_OK;
-  std::vector<int32_t> p32(t->n);
-  for (int64_t k = 0; k < t->n; ++k) p32[k] = static_cast<int32_t>(t->perm[k]);
-  int rc = t->dev->perm.reserve(4 * t->n);
+  if (static_cast<int64_t>(t->perm32.size()) != t->n) {
+    t->perm32.resize(t->n);
+    parallel_for(t->n, 65536, [&](int64_t a, int64_t b) {
+      for (int64_t k = a; k < b; ++k) t->perm32[k] = static_cast<int32_t>(t->perm[k]);
+    });
+  }
+  int rc = upload_vec(t->dev->perm, t->perm32, st);
   if (rc) return rc;
-  CUDA_TRY(cudaMemcpyAsync(t->dev->perm.p, p32.data(), 4 * t->n, cudaMemcpyHostToDevice, st));
-  CUDA_TRY(cudaStreamSynchronize(st));
   t->perm_on_device = true;
   return OCTGRAV_OK;
 }
@@ -1149,40 +1154,18 @@ int forces_dev64(octgrav_tree* t, double eps, double theta, double G, double* ac
 }
 
 int forces_host(octgrav_tree* t, double eps, double theta, double G, double* acc, double* pot,
-                cudaStream_t st, hvec<float4>* hbuf = nullptr) {
+                cudaStream_t st) {
   if (!acc) return fail(OCTGRAV_ERR_ARG, "acc is NULL");
   int rc = check_params(eps, theta, G);
   if (rc) return rc;
-  if (t->gpu) {  // unpermute on the device, copy FP64 results straight into the caller's arrays
-    Device& D = *t->dev;
-    if ((rc = D.acc64.reserve(24 * t->n)) || (rc = D.pot64.reserve(8 * t->n))) return rc;
-    if ((rc = forces_dev64(t, eps, theta, G, static_cast<double*>(D.acc64.p), static_cast<double*>(D.pot64.p), st)))
-      return rc;
-    CUDA_TRY(cudaMemcpyAsync(acc, D.acc64.p, 24 * t->n, cudaMemcpyDeviceToHost, st));
-    if (pot) CUDA_TRY(cudaMemcpyAsync(pot, D.pot64.p, 8 * t->n, cudaMemcpyDeviceToHost, st));
-    return read_status(t, st);
-  }
-  if (!t->uploaded || t->sysp_dirty) {
-    if ((rc = upload(t, st))) return rc;
-  }
-  if ((rc = t->dev->out.reserve(sizeof(float4) * t->n))) return rc;
-  if ((rc = launch(t, eps, theta, G, static_cast<float4*>(t->dev->out.p), st, false, nullptr, nullptr, nullptr, 0)))
+  // unpermute on the device, copy FP64 results straight into the caller's arrays
+  Device& D = *t->dev;
+  if ((rc = D.acc64.reserve(24 * t->n)) || (rc = D.pot64.reserve(8 * t->n))) return rc;
+  if ((rc = forces_dev64(t, eps, theta, G, static_cast<double*>(D.acc64.p), static_cast<double*>(D.pot64.p), st)))
     return rc;
-  hvec<float4> local;
-  hvec<float4>& h = hbuf ? *hbuf : local;
-  h.resize(t->n);
-  CUDA_TRY(cudaMemcpyAsync(h.data(), t->dev->out.p, sizeof(float4) * t->n, cudaMemcpyDeviceToHost, st));
-  if ((rc = read_status(t, st))) return rc;
-  parallel_for(t->n, 65536, [&](int64_t a, int64_t b) {
-    for (int64_t k = a; k < b; ++k) {
-      const int64_t i = t->perm[k];
-      acc[3 * i] = h[k].x;
-      acc[3 * i + 1] = h[k].y;
-      acc[3 * i + 2] = h[k].z;
-      if (pot) pot[i] = h[k].w;
-    }
-  });
-  return OCTGRAV_OK;
+  CUDA_TRY(cudaMemcpyAsync(acc, D.acc64.p, 24 * t->n, cudaMemcpyDeviceToHost, st));
+  if (pot) CUDA_TRY(cudaMemcpyAsync(pot, D.pot64.p, 8 * t->n, cudaMemcpyDeviceToHost, st));
+  return read_status(t, st);
 }
 
 thread_local Device* tl_cache = nullptr;
@@ -1514,7 +1497,7 @@ int octgrav_forces_ex(const double* pos, const double* mass, int64_t n, double e
   if ((rc = build_common(1, off, pos, mass, n_leaf, n_group, &t, &hcache))) return rc;
   if (!tl_cache) tl_cache = new Device();
   t->dev = tl_cache;
-  rc = forces_host(t, eps, theta, G, acc, pot, static_cast<cudaStream_t>(stream), &hcache.h);
+  rc = forces_host(t, eps, theta, G, acc, pot, static_cast<cudaStream_t>(stream));
   give_back(t, &hcache);
   octgrav_free_tree(t);
   return rc;
