@@ -675,9 +675,10 @@ def main():
     peak, sms, mhz = fp32_peak_tflops(torch)
     achieved = counts["flops"] / (ms_step * 1e-3) / 1e12
 
-    # e2e through the one-shot C-ABI call with pinned host buffers: inputs
-    # copied in, tree built on the GPU, forces, unpermuted on the device,
-    # FP64 results copied out; every step inside the timed region
+    # e2e through the one-shot C-ABI calls with pinned host buffers, every step
+    # inside the timed region: octgrav_forces_ex (tree built on the host, its
+    # arrays copied in) and octgrav_forces_gpu (inputs copied in, tree built on
+    # the GPU); both unpermute on the device and copy the FP64 results out
     pin_x = torch.from_numpy(np.ascontiguousarray(pos)).pin_memory()
     pin_m = torch.from_numpy(np.ascontiguousarray(m)).pin_memory()
     pin_a = torch.empty((a.n, 3), dtype=torch.float64).pin_memory()
@@ -692,7 +693,8 @@ def main():
     for k in range(a.e2e_steps + 1 if a.e2e_steps > 0 else 0):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        G.forces(pos, m, a.eps, a.theta, a.n_leaf, a.n_group, stream=stream)
+        G.forces(pin_x.numpy(), pin_m.numpy(), a.eps, a.theta, a.n_leaf, a.n_group, stream=stream,
+                 out=(pin_a.numpy(), pin_p.numpy()))
         host_t.append(time.perf_counter() - t0)
     e2e_s = statistics.mean(e2e_t[1:]) if len(e2e_t) > 1 else float("nan")
     host_s = statistics.mean(host_t[1:]) if len(host_t) > 1 else float("nan")

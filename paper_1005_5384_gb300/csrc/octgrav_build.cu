@@ -1298,6 +1298,20 @@ cudaError_t gpu_build_items(const GpuBuild& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+__global__ void k_pull(const uint4* __restrict__ src, uint4* __restrict__ dst, int64_t n16) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n16;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    dst[i] = src[i];
+}
+
+cudaError_t pull_host(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  if ((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src) | bytes) & 15u) return cudaErrorInvalidValue;
+  const int64_t n16 = static_cast<int64_t>(bytes / 16);
+  if (n16 == 0) return cudaSuccess;
+  k_pull<<<grid_for(n16, TB * 4), TB, 0, st>>>(static_cast<const uint4*>(src), static_cast<uint4*>(dst), n16);
+  return cudaGetLastError();
+}
+
 cudaError_t gpu_unpermute(const float4* out, const int* perm, int64_t n, double* acc, double* pot, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   k_unpermute<<<grid_for(n, TB), TB, 0, st>>>(out, perm, n, acc, pot);

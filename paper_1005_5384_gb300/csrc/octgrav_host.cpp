@@ -309,8 +309,30 @@ inline int octant_at(uint64_t code, int child_depth) {
   return static_cast<int>((code >> (3 * (kMaxDepth - child_depth))) & 7);
 }
 
+// A particle's two device records: (x_hi, y_hi, z_hi, m) and (x_lo, y_lo, z_lo, 0),
+// hi = fl32(x) and lo = fl32(x - hi).
+inline void particle_records(const double* x, double m, float4* rec) {
+  float hi[3], lo[3];
+  for (int d = 0; d < 3; ++d) {
+    hi[d] = static_cast<float>(x[d]);
+    lo[d] = static_cast<float>(x[d] - static_cast<double>(hi[d]));
+  }
+  rec[0] = make_float4(hi[0], hi[1], hi[2], static_cast<float>(m));
+  rec[1] = make_float4(lo[0], lo[1], lo[2], 0.f);
+}
+
+// Where a one-system build writes its particle images during the gather (tree
+// order), and what to call once they are complete (e.g. to start their upload
+// while the cells are built).
+struct ParticleSink {
+  float4* parts = nullptr;  // 2 records per particle
+  int64_t* perm = nullptr;
+  int32_t* perm32 = nullptr;
+  std::function<int()> ready;
+};
+
 int build_system(const double* pos, const double* mass, int64_t n, int n_leaf, int n_group,
-                 bool parallel, SysTree& T) {
+                 bool parallel, SysTree& T, const ParticleSink* sink = nullptr) {
   T.reset();
   T.n = n;
   const int64_t grain = parallel ? 16384 : (int64_t)1 << 62;
@@ -384,8 +406,17 @@ int build_system(const double* pos, const double* mass, int64_t n, int n_leaf, i
       T.x[3 * t + 1] = pos[3 * i + 1];
       T.x[3 * t + 2] = pos[3 * i + 2];
       T.m[t] = mass[i];
+      if (sink) {
+        particle_records(&T.x[3 * t], T.m[t], sink->parts + 2 * t);
+        sink->perm[t] = i;
+        sink->perm32[t] = static_cast<int32_t>(i);
+      }
     }
   });
+  if (sink && sink->ready) {
+    const int rc = sink->ready();
+    if (rc) return rc;
+  }
 
   // ---- cells, level by level
   auto push_cell = [&](uint64_t key, int depth, int32_t parent, int64_t pf, int64_t pc) {
@@ -632,6 +663,7 @@ struct Device {
   DevBuf perm, key, props, pcount, cfirst, groups, ikey, celloff, result, scratch, in_pos, in_mass, acc64, pot64;
   DevBuf order;  // work-item processing order (octgrav_balance)
   int device = -1;
+  int pageable = -1;     // kernels may read pageable host memory (-1: not asked yet)
   int64_t cell_cap = 0;  // cell capacity that last sufficed for a GPU build
   int level_hint = 0;    // depth of the last GPU build + 2 (0: none yet), caps the next level loop
   // the GPU build's kernels captured as a graph, replayed on gstream while
@@ -704,6 +736,7 @@ struct octgrav_tree {
   bool gpu = false;
   bool host_valid = true;
   bool perm_on_device = false;  // Device::perm holds the permutation (int32)
+  bool parts_on_device = false;  // Device::parts already holds (or receives) the particle records
   int64_t n_groups = 0, n_items = 0;
   bool ordered = false;  // launches take the work items in Device::order (octgrav_balance)
   hvec<int32_t> item_order;  // host image of the default order (host-built trees)
@@ -789,7 +822,8 @@ void make_items(octgrav_tree* t) {
 }
 
 // Concatenate the systems' trees into the device-array images.
-int assemble(octgrav_tree* t, std::vector<SysTree>& sys) {
+// particles_done: a one-system build already wrote perm, perm32 and parts.
+int assemble(octgrav_tree* t, std::vector<SysTree>& sys, bool particles_done = false) {
   const int ns = static_cast<int>(sys.size());
   t->cell_off.assign(ns + 1, 0);
   for (int s = 0; s < ns; ++s) t->cell_off[s + 1] = t->cell_off[s] + static_cast<int64_t>(sys[s].key.size());
@@ -798,9 +832,11 @@ int assemble(octgrav_tree* t, std::vector<SysTree>& sys) {
   t->n_cells = nc;
   // one system: its FP64 cell arrays are moved, not copied, after the loop below
   const bool single = ns == 1;
-  t->perm.resize(t->n);
-  t->perm32.resize(t->n);
-  t->parts.resize(2 * t->n);
+  if (!particles_done) {
+    t->perm.resize(t->n);
+    t->perm32.resize(t->n);
+    t->parts.resize(2 * t->n);
+  }
   t->geo.resize(nc);
   t->link.resize(nc);
   t->mp.resize(4 * nc);
@@ -824,20 +860,14 @@ int assemble(octgrav_tree* t, std::vector<SysTree>& sys) {
     SysTree& T = sys[s];
     const int64_t p0 = t->sys_off[s], c0 = t->cell_off[s];
     const int64_t n = T.n, ncs = static_cast<int64_t>(T.key.size());
-    parallel_for(n, 16384, [&](int64_t a, int64_t b) {
-      for (int64_t k = a; k < b; ++k) {
-        t->perm[p0 + k] = p0 + T.perm[k];
-        t->perm32[p0 + k] = static_cast<int32_t>(p0 + T.perm[k]);
-        float hi[3], lo[3];
-        for (int d = 0; d < 3; ++d) {
-          const double v = T.x[3 * k + d];
-          hi[d] = static_cast<float>(v);
-          lo[d] = static_cast<float>(v - static_cast<double>(hi[d]));
+    if (!particles_done)
+      parallel_for(n, 16384, [&](int64_t a, int64_t b) {
+        for (int64_t k = a; k < b; ++k) {
+          t->perm[p0 + k] = p0 + T.perm[k];
+          t->perm32[p0 + k] = static_cast<int32_t>(p0 + T.perm[k]);
+          particle_records(&T.x[3 * k], T.m[k], &t->parts[2 * (p0 + k)]);
         }
-        t->parts[2 * (p0 + k)] = make_float4(hi[0], hi[1], hi[2], static_cast<float>(T.m[k]));
-        t->parts[2 * (p0 + k) + 1] = make_float4(lo[0], lo[1], lo[2], 0.f);
-      }
-    });
+      });
     parallel_for(ncs, 8192, [&](int64_t a, int64_t b) {
       for (int64_t c = a; c < b; ++c) {
         const int64_t g = c0 + c;
@@ -962,8 +992,8 @@ void give_back(octgrav_tree* t, HostCache* cache) {
   swap_images(*t, cache->spare);
 }
 
-int build_common(int n_sys, const int64_t* offsets, const double* pos, const double* mass, int n_leaf,
-                 int n_group, octgrav_tree** out, HostCache* cache = nullptr) {
+int check_build_args(int n_sys, const int64_t* offsets, const double* pos, const double* mass, int n_leaf,
+                     int n_group, octgrav_tree** out) {
   if (!out) return fail(OCTGRAV_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (!pos || !mass || !offsets || n_sys < 1) return fail(OCTGRAV_ERR_ARG, "NULL input or n_sys < 1");
@@ -971,10 +1001,15 @@ int build_common(int n_sys, const int64_t* offsets, const double* pos, const dou
   if (offsets[0] != 0) return fail(OCTGRAV_ERR_ARG, "offsets[0] must be 0");
   for (int s = 0; s < n_sys; ++s)
     if (offsets[s + 1] <= offsets[s]) return fail(OCTGRAV_ERR_ARG, "empty or decreasing system %d", s);
-  const int64_t n = offsets[n_sys];
-  if (n >= (1ll << 31) - 64) return fail(OCTGRAV_ERR_ARG, "too many particles");
-  int rc = check_inputs(pos, mass, n);
+  if (offsets[n_sys] >= (1ll << 31) - 64) return fail(OCTGRAV_ERR_ARG, "too many particles");
+  return check_inputs(pos, mass, offsets[n_sys]);
+}
+
+int build_common(int n_sys, const int64_t* offsets, const double* pos, const double* mass, int n_leaf,
+                 int n_group, octgrav_tree** out, HostCache* cache = nullptr) {
+  int rc = check_build_args(n_sys, offsets, pos, mass, n_leaf, n_group, out);
   if (rc) return rc;
+  const int64_t n = offsets[n_sys];
   std::unique_ptr<octgrav_tree> t;
   try {
     t.reset(new octgrav_tree());
@@ -1016,6 +1051,83 @@ int upload_vec(DevBuf& b, const V& v, cudaStream_t st) {
   return OCTGRAV_OK;
 }
 
+// Copy host memory to a device buffer. Where the device reads pageable host
+// memory (NVLink-C2C on Grace systems) a kernel pulls it and the call returns at
+// once; otherwise cudaMemcpyAsync, which returns when the source has been read.
+int enqueue_h2d(Device& D, DevBuf& b, const void* src, size_t bytes, cudaStream_t st, bool* async) {
+  int rc = b.reserve(bytes);
+  if (rc || !bytes) return rc;
+  if (D.pageable < 0) {
+    int v = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&v, cudaDevAttrPageableMemoryAccess, D.device));
+    D.pageable = v ? 1 : 0;
+  }
+  const bool aligned = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(b.p) | bytes) & 15u) == 0;
+  if (D.pageable == 1 && aligned) {
+    cudaError_t e = og::pull_host(b.p, src, bytes, st);
+    if (e != cudaSuccess) return fail(OCTGRAV_ERR_CUDA, "host pull failed: %s", cudaGetErrorString(e));
+    *async = true;
+    return OCTGRAV_OK;
+  }
+  CUDA_TRY(cudaMemcpyAsync(b.p, src, bytes, cudaMemcpyHostToDevice, st));
+  return OCTGRAV_OK;
+}
+
+// The one-shot call's build (one system, cached host arrays): the particle
+// records and the permutation are written during the gather and start their
+// way to the device (on st) while the cells are built. On return with an error
+// nothing is still reading the host arrays.
+int build_oneshot(const double* pos, const double* mass, int64_t n, int n_leaf, int n_group, HostCache& cache,
+                  Device& D, cudaStream_t st, octgrav_tree** out) {
+  const int64_t off[2] = {0, n};
+  int rc = check_build_args(1, off, pos, mass, n_leaf, n_group, out);
+  if (rc) return rc;
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (D.device >= 0 && D.device != dev) D.release();
+  if (D.device != dev) D.pageable = -1;
+  D.device = dev;
+  std::unique_ptr<octgrav_tree> t;
+  bool async = false;
+  try {
+    t.reset(new octgrav_tree());
+    t->n = n;
+    t->n_leaf = n_leaf;
+    t->n_group = n_group;
+    t->n_sys = 1;
+    t->sys_off.assign(off, off + 2);
+    t->dev = &D;
+    cache.sys.resize(1);
+    swap_images(*t, cache.spare);
+    t->perm.resize(n);
+    t->perm32.resize((n + 3) & ~int64_t{3});  // whole 16-byte units for the pull
+    t->parts.resize(2 * n);
+    ParticleSink sink;
+    sink.parts = t->parts.data();
+    sink.perm = t->perm.data();
+    sink.perm32 = t->perm32.data();
+    sink.ready = [&]() -> int {
+      int r = enqueue_h2d(D, D.parts, t->parts.data(), sizeof(float4) * t->parts.size(), st, &async);
+      if (!r) r = enqueue_h2d(D, D.perm, t->perm32.data(), sizeof(int32_t) * t->perm32.size(), st, &async);
+      return r;
+    };
+    rc = build_system(pos, mass, n, n_leaf, n_group, true, cache.sys[0], &sink);
+    if (!rc) rc = assemble(t.get(), cache.sys, true);
+  } catch (const std::bad_alloc&) {
+    rc = fail(OCTGRAV_ERR_OOM, "host allocation failed");
+  }
+  if (rc) {
+    if (async) cudaStreamSynchronize(st);
+    if (t) give_back(t.get(), &cache);
+    return rc;
+  }
+  t->parts_on_device = true;
+  t->perm_on_device = true;
+  *out = t.release();
+  return OCTGRAV_OK;
+}
+
+
 int upload(octgrav_tree* t, cudaStream_t st) {
   int dev = 0;
   CUDA_TRY(cudaGetDevice(&dev));
@@ -1026,10 +1138,14 @@ int upload(octgrav_tree* t, cudaStream_t st) {
   D.device = dev;
   int rc;
   if (!t->gpu) {  // a GPU-built tree already lives in these arrays
-    if ((rc = upload_vec(D.parts, t->parts, st)) || (rc = upload_vec(D.geo, t->geo, st)) ||
+    if (!t->parts_on_device &&
+        ((rc = upload_vec(D.parts, t->parts, st)) || (rc = upload_vec(D.perm, t->perm32, st))))
+      return rc;
+    t->parts_on_device = false;  // a later re-upload copies them again
+    if ((rc = upload_vec(D.geo, t->geo, st)) ||
         (rc = upload_vec(D.link, t->link, st)) || (rc = upload_vec(D.mp, t->mp, st)) ||
         (rc = upload_vec(D.items, t->items, st)) || (rc = upload_vec(D.ibox, t->ibox, st)) ||
-        (rc = upload_vec(D.order, t->item_order, st)) || (rc = upload_vec(D.perm, t->perm32, st)))
+        (rc = upload_vec(D.order, t->item_order, st)))
       return rc;
     t->perm_on_device = true;
   }
@@ -1492,12 +1608,12 @@ int octgrav_forces_ex(const double* pos, const double* mass, int64_t n, double e
   if (rc) return rc;
   if (n < 1) return fail(OCTGRAV_ERR_ARG, "n must be >= 1");
   thread_local HostCache hcache;
-  const int64_t off[2] = {0, n};
-  octgrav_tree* t = nullptr;
-  if ((rc = build_common(1, off, pos, mass, n_leaf, n_group, &t, &hcache))) return rc;
   if (!tl_cache) tl_cache = new Device();
-  t->dev = tl_cache;
-  rc = forces_host(t, eps, theta, G, acc, pot, static_cast<cudaStream_t>(stream));
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  octgrav_tree* t = nullptr;
+  if ((rc = build_oneshot(pos, mass, n, n_leaf, n_group, hcache, *tl_cache, st, &t))) return rc;
+  rc = forces_host(t, eps, theta, G, acc, pot, st);
+  if (rc) cudaStreamSynchronize(st);  // nothing may still read the cached host arrays
   give_back(t, &hcache);
   octgrav_free_tree(t);
   return rc;

@@ -194,6 +194,14 @@ cudaError_t gpu_build_items(const GpuBuild& a, cudaStream_t stream);
 cudaError_t gpu_unpermute(const float4* out, const int* perm, int64_t n, double* acc, double* pot,
                           cudaStream_t stream);
 
+// Copy `bytes` from pageable host memory to the device by a kernel that reads
+// the host memory itself (devices with cudaDevAttrPageableMemoryAccess, e.g.
+// over NVLink-C2C): asynchronous for the host, unlike cudaMemcpyAsync from
+// pageable memory. Both pointers 16-byte aligned and bytes a multiple of 16
+// (else cudaErrorInvalidValue). The source must stay valid and unchanged until
+// the stream passes the copy.
+cudaError_t pull_host(void* dst, const void* src, size_t bytes, cudaStream_t stream);
+
 // ---- time integration (octgrav_sim.cu)
 
 constexpr int SIM_EBLOCKS = 256;  // blocks (and partial-sum pairs) of the energy reduction

@@ -384,14 +384,26 @@ class Tree:
         return [(np.sort(ck[k, :nc[k]]), np.sort(lk[k, :nl[k]])) for k in range(ni)]
 
 
+def _out_arrays(n, out):
+    if out is None:
+        return np.zeros((n, 3)), np.zeros(n)
+    acc, pot = out
+    if acc.dtype != np.float64 or not acc.flags.c_contiguous or acc.size != 3 * n:
+        raise ValueError("acc must be a C-contiguous float64 array of n x 3")
+    if pot is not None and (pot.dtype != np.float64 or not pot.flags.c_contiguous or pot.size != n):
+        raise ValueError("pot must be a C-contiguous float64 array of n")
+    return acc, pot
+
+
 def forces(pos, mass, eps: float, theta: float, n_leaf: int = 16, n_group: int | None = None, G: float = 1.0,
-           stream=None):
-    """One-shot C-ABI call with host buffers: (acc [n,3], pot [n]) in input order."""
+           stream=None, out=None):
+    """One-shot C-ABI call with host buffers and the tree built on the host:
+    (acc [n,3], pot [n]) in input order. ``out`` = (acc, pot) host float64
+    arrays to fill (e.g. views of pinned memory)."""
     lib = load()
     pos, mass = _pm(pos, mass)
     n = mass.shape[0]
-    acc = np.zeros((n, 3))
-    pot = np.zeros(n)
+    acc, pot = _out_arrays(n, out)
     _check(lib.octgrav_forces_ex(pos, mass, n, float(eps), float(theta), float(G), int(n_leaf),
                                  int(n_group if n_group is not None else n_leaf), _p(acc), _p(pot),
                                  _stream_handle(stream)))
@@ -407,14 +419,7 @@ def forces_gpu(pos, mass, eps: float, theta: float, n_leaf: int = 16, n_group: i
     lib = load()
     pos, mass = _pm(pos, mass)
     n = mass.shape[0]
-    if out is None:
-        acc, pot = np.zeros((n, 3)), np.zeros(n)
-    else:
-        acc, pot = out
-        if acc.dtype != np.float64 or not acc.flags.c_contiguous or acc.size != 3 * n:
-            raise ValueError("acc must be a C-contiguous float64 array of n x 3")
-        if pot is not None and (pot.dtype != np.float64 or not pot.flags.c_contiguous or pot.size != n):
-            raise ValueError("pot must be a C-contiguous float64 array of n")
+    acc, pot = _out_arrays(n, out)
     _check(lib.octgrav_forces_gpu(_p(pos), _p(mass), n, float(eps), float(theta), float(G), int(n_leaf),
                                   int(n_group if n_group is not None else n_leaf), _p(acc), _p(pot),
                                   _stream_handle(stream)))
