@@ -168,6 +168,24 @@ def test_one_shot_gpu_call_equals_host_path(torch):
     assert np.array_equal(_bits(acc), _bits(a3)) and np.array_equal(_bits(pot), _bits(p3))
 
 
+def test_one_shot_host_call_across_sizes(torch):
+    """The host-build one-shot call keeps its host arrays between calls and
+    starts the particle upload during the build: calls of growing and
+    shrinking N (ragged, not multiples of 4) equal the tree path bit for bit."""
+    for n, seed in ((50001, 31), (3, 32), (120003, 33), (20000, 34)):
+        pos, m = W.plummer(n, seed=seed)
+        T = G.Tree.build(pos, m, 16, 64)
+        ra, rp = T.forces(0.01, 0.5)
+        pin_x = torch.from_numpy(pos.copy()).pin_memory()
+        pin_m = torch.from_numpy(m.copy()).pin_memory()
+        out_a = torch.zeros((n, 3), dtype=torch.float64).pin_memory()
+        out_p = torch.zeros(n, dtype=torch.float64).pin_memory()
+        a1, p1 = G.forces(pin_x.numpy(), pin_m.numpy(), 0.01, 0.5, 16, 64, out=(out_a.numpy(), out_p.numpy()))
+        a2, p2 = G.forces(pos, m, 0.01, 0.5, 16, 64)  # pageable buffers
+        for a, p in ((a1, p1), (a2, p2)):
+            assert np.array_equal(_bits(a), _bits(ra)) and np.array_equal(_bits(p), _bits(rp))
+
+
 def test_device64_outputs_in_input_order(torch):
     pos, m = W.plummer(30000, seed=15)
     for T in (G.Tree.build(pos, m, 16, 64), G.Tree.build_gpu(pos, m, 16, 64)):
