@@ -329,6 +329,7 @@ struct ParticleSink {
   int64_t* perm = nullptr;
   int32_t* perm32 = nullptr;
   std::function<int()> ready;
+  bool check_inputs = false;  // the bounding-box pass also checks the inputs (finite, masses >= 0)
 };
 
 int build_system(const double* pos, const double* mass, int64_t n, int n_leaf, int n_group,
@@ -342,20 +343,29 @@ int build_system(const double* pos, const double* mass, int64_t n, int n_leaf, i
     const int64_t chunks = parallel ? std::max<int64_t>(1, std::min<int64_t>(64, n / 65536)) : 1;
     std::vector<double> part(chunks * 6);
     const int64_t step = (n + chunks - 1) / chunks;
+    const bool check = sink && sink->check_inputs;
+    std::vector<uint8_t> bad(chunks, 0);
     auto body = [&](int c) {
       double a[3] = {pos[0], pos[1], pos[2]}, b[3] = {pos[0], pos[1], pos[2]};
-      for (int64_t i = c * step; i < std::min(n, (c + 1) * step); ++i)
+      bool ok = true;
+      for (int64_t i = c * step; i < std::min(n, (c + 1) * step); ++i) {
         for (int d = 0; d < 3; ++d) {
           const double v = pos[3 * i + d];
           if (v < a[d]) a[d] = v;
           if (v > b[d]) b[d] = v;
+          if (check) ok = ok && std::isfinite(v);
         }
+        if (check) ok = ok && std::isfinite(mass[i]) && mass[i] >= 0;
+      }
       for (int d = 0; d < 3; ++d) {
         part[6 * c + d] = a[d];
         part[6 * c + 3 + d] = b[d];
       }
+      bad[c] = !ok;
     };
     if (chunks > 1) Pool::get().run(static_cast<int>(chunks), body); else body(0);
+    for (int64_t c = 0; c < chunks; ++c)
+      if (bad[c]) return fail(OCTGRAV_ERR_NONFINITE, "non-finite position/mass or negative mass");
     for (int64_t c = 0; c < chunks; ++c)
       for (int d = 0; d < 3; ++d) {
         mn[d] = std::min(mn[d], part[6 * c + d]);
@@ -737,6 +747,8 @@ struct octgrav_tree {
   bool host_valid = true;
   bool perm_on_device = false;  // Device::perm holds the permutation (int32)
   bool parts_on_device = false;  // Device::parts already holds (or receives) the particle records
+  bool pull_images = false;      // upload may pull the host images by kernel (the one-shot call, whose
+                                 // images stay unchanged until it has waited for the stream)
   int64_t n_groups = 0, n_items = 0;
   bool ordered = false;  // launches take the work items in Device::order (octgrav_balance)
   hvec<int32_t> item_order;  // host image of the default order (host-built trees)
@@ -993,7 +1005,7 @@ void give_back(octgrav_tree* t, HostCache* cache) {
 }
 
 int check_build_args(int n_sys, const int64_t* offsets, const double* pos, const double* mass, int n_leaf,
-                     int n_group, octgrav_tree** out) {
+                     int n_group, octgrav_tree** out, bool values = true) {
   if (!out) return fail(OCTGRAV_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (!pos || !mass || !offsets || n_sys < 1) return fail(OCTGRAV_ERR_ARG, "NULL input or n_sys < 1");
@@ -1002,7 +1014,7 @@ int check_build_args(int n_sys, const int64_t* offsets, const double* pos, const
   for (int s = 0; s < n_sys; ++s)
     if (offsets[s + 1] <= offsets[s]) return fail(OCTGRAV_ERR_ARG, "empty or decreasing system %d", s);
   if (offsets[n_sys] >= (1ll << 31) - 64) return fail(OCTGRAV_ERR_ARG, "too many particles");
-  return check_inputs(pos, mass, offsets[n_sys]);
+  return values ? check_inputs(pos, mass, offsets[n_sys]) : OCTGRAV_OK;
 }
 
 int build_common(int n_sys, const int64_t* offsets, const double* pos, const double* mass, int n_leaf,
@@ -1080,13 +1092,8 @@ int enqueue_h2d(Device& D, DevBuf& b, const void* src, size_t bytes, cudaStream_
 int build_oneshot(const double* pos, const double* mass, int64_t n, int n_leaf, int n_group, HostCache& cache,
                   Device& D, cudaStream_t st, octgrav_tree** out) {
   const int64_t off[2] = {0, n};
-  int rc = check_build_args(1, off, pos, mass, n_leaf, n_group, out);
+  int rc = check_build_args(1, off, pos, mass, n_leaf, n_group, out, false);  // values: in the bbox pass
   if (rc) return rc;
-  int dev = 0;
-  CUDA_TRY(cudaGetDevice(&dev));
-  if (D.device >= 0 && D.device != dev) D.release();
-  if (D.device != dev) D.pageable = -1;
-  D.device = dev;
   std::unique_ptr<octgrav_tree> t;
   bool async = false;
   try {
@@ -1106,7 +1113,13 @@ int build_oneshot(const double* pos, const double* mass, int64_t n, int n_leaf, 
     sink.parts = t->parts.data();
     sink.perm = t->perm.data();
     sink.perm32 = t->perm32.data();
+    sink.check_inputs = true;
     sink.ready = [&]() -> int {
+      int dev = 0;
+      CUDA_TRY(cudaGetDevice(&dev));
+      if (D.device >= 0 && D.device != dev) D.release();
+      if (D.device != dev) D.pageable = -1;
+      D.device = dev;
       int r = enqueue_h2d(D, D.parts, t->parts.data(), sizeof(float4) * t->parts.size(), st, &async);
       if (!r) r = enqueue_h2d(D, D.perm, t->perm32.data(), sizeof(int32_t) * t->perm32.size(), st, &async);
       return r;
@@ -1123,6 +1136,7 @@ int build_oneshot(const double* pos, const double* mass, int64_t n, int n_leaf, 
   }
   t->parts_on_device = true;
   t->perm_on_device = true;
+  t->pull_images = true;
   *out = t.release();
   return OCTGRAV_OK;
 }
@@ -1142,11 +1156,20 @@ int upload(octgrav_tree* t, cudaStream_t st) {
         ((rc = upload_vec(D.parts, t->parts, st)) || (rc = upload_vec(D.perm, t->perm32, st))))
       return rc;
     t->parts_on_device = false;  // a later re-upload copies them again
-    if ((rc = upload_vec(D.geo, t->geo, st)) ||
-        (rc = upload_vec(D.link, t->link, st)) || (rc = upload_vec(D.mp, t->mp, st)) ||
-        (rc = upload_vec(D.items, t->items, st)) || (rc = upload_vec(D.ibox, t->ibox, st)) ||
-        (rc = upload_vec(D.order, t->item_order, st)))
+    if (t->pull_images) {
+      bool async = false;
+      if ((rc = enqueue_h2d(D, D.geo, t->geo.data(), sizeof(float4) * t->geo.size(), st, &async)) ||
+          (rc = enqueue_h2d(D, D.link, t->link.data(), sizeof(int2) * t->link.size(), st, &async)) ||
+          (rc = enqueue_h2d(D, D.mp, t->mp.data(), sizeof(float4) * t->mp.size(), st, &async)) ||
+          (rc = enqueue_h2d(D, D.items, t->items.data(), sizeof(int4) * t->items.size(), st, &async)) ||
+          (rc = enqueue_h2d(D, D.ibox, t->ibox.data(), sizeof(float4) * t->ibox.size(), st, &async)) ||
+          (rc = enqueue_h2d(D, D.order, t->item_order.data(), sizeof(int32_t) * t->item_order.size(), st, &async)))
+        return rc;
+    } else if ((rc = upload_vec(D.geo, t->geo, st)) || (rc = upload_vec(D.link, t->link, st)) ||
+               (rc = upload_vec(D.mp, t->mp, st)) || (rc = upload_vec(D.items, t->items, st)) ||
+               (rc = upload_vec(D.ibox, t->ibox, st)) || (rc = upload_vec(D.order, t->item_order, st))) {
       return rc;
+    }
     t->perm_on_device = true;
   }
   if ((rc = D.counts.reserve(t->n_items * sizeof(int2)))) return rc;

@@ -90,6 +90,15 @@ def test_invalid_arguments_are_rejected_without_a_gpu():
     with pytest.raises(G.OctgravError) as e:
         G.Tree.build(pos, neg, 16)
     assert e.value.code == G.ERR_NONFINITE
+    for args in ((bad, m), (pos, neg)):  # the one-shot call checks the values in its first pass
+        with pytest.raises(G.OctgravError) as e:
+            G.forces(*args, 0.01, 0.5)
+        assert e.value.code == G.ERR_NONFINITE
+    inf = pos.copy()
+    inf[99, 2] = np.inf
+    with pytest.raises(G.OctgravError) as e:
+        G.forces(inf, m, 0.01, 0.5)
+    assert e.value.code == G.ERR_NONFINITE
     for eps, theta in ((0.0, 0.5), (-1.0, 0.5), (0.01, -0.1), (float("nan"), 0.5), (0.01, float("inf"))):
         with pytest.raises(G.OctgravError) as e:
             G.forces(pos, m, eps, theta)
