@@ -152,8 +152,9 @@ def test_device_output_order_and_determinism(_cuda):
 
 
 def test_full_size_plummer_sampled_groups():
-    """1,048,576-particle Plummer sphere at theta = 0.5 in the benchmark's launch
-    configuration; the oracle evaluates a seeded sample of 400 groups."""
+    """1,048,576-particle Plummer sphere at theta = 0.5 with N_group 64 (the
+    benchmark's own configuration is in test_gpu_fullsize.py); the oracle
+    evaluates a seeded sample of 400 groups."""
     pos, m = W.plummer(1 << 20, seed=1)
     T = G.Tree.build(pos, m, 16, 64)
     acc, pot = T.forces(0.01, 0.5)
