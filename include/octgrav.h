@@ -105,9 +105,17 @@ int octgrav_set_system_params(octgrav_tree *t, const double *eps, const double *
 int octgrav_forces_tree(octgrav_tree *t, double eps, double theta, double G, double *acc,
                         double *pot, void *stream);
 
-/* One-shot call: build (n_group = n_leaf), upload, forces, free, on the
- * default stream with G = 1. Device buffers are cached between calls on the
- * calling thread's current device. */
+/* One-shot call (the paper's split, Sec. 2): FP64 tree build on the host
+ * (n_group = n_leaf), upload, forces, free, on the default stream with G = 1.
+ * Outputs in input order: acc[3n], pot[n] (pot may be NULL), unpermuted on the
+ * device and copied into these arrays. Device buffers and the host build's
+ * arrays are cached between calls of the calling thread (on its current
+ * device). Where the device reads pageable host memory
+ * (cudaDevAttrPageableMemoryAccess), the tree arrays are pulled by a copy
+ * kernel, the particle records while the host still builds the cells; the
+ * call returns only after the stream is done. Inputs are read, never written.
+ * Errors: ERR_ARG, ERR_NONFINITE (checked before any device call), ERR_OOM,
+ * ERR_CUDA, and the device statuses of octgrav_forces_tree. */
 int octgrav_forces(const double *pos, const double *mass, int64_t n, double eps, double theta,
                    int n_leaf, double *acc, double *pot);
 
