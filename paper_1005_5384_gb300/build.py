@@ -69,7 +69,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     b_cmd = nv("octgrav_build.cu", bo, "-fmad=false")
     s_cmd = nv("octgrav_sim.cu", so, "-fmad=false")
     d_cmd = nv("octgrav_direct.cu", do)
-    h_cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-fno-fast-math", "-pthread",
+    h_cmd = ["g++", "-O3", "-std=c++17", "-fPIC", "-ffp-contract=off", "-fno-fast-math", "-pthread",
              "-I", os.path.join(cuda, "include"), "-I", INCLUDE,
              "-c", os.path.join(CSRC, "octgrav_host.cpp"), "-o", ho]
     cmds = (k_cmd, m_cmd, b_cmd, s_cmd, d_cmd, h_cmd)
