@@ -1307,7 +1307,20 @@ int forces_host(octgrav_tree* t, double eps, double theta, double G, double* acc
   return read_status(t, st);
 }
 
-thread_local Device* tl_cache = nullptr;
+// The one-shot calls' device buffers, one set per calling thread, released
+// when the thread ends.
+struct ThreadDevice {
+  Device* d = nullptr;
+  Device& get() {
+    if (!d) d = new Device();
+    return *d;
+  }
+  ~ThreadDevice() {
+    if (d) d->release();
+    delete d;
+  }
+};
+thread_local ThreadDevice tl_device;
 
 // ---------------------------------------------------------------- GPU build
 
@@ -1631,10 +1644,9 @@ int octgrav_forces_ex(const double* pos, const double* mass, int64_t n, double e
   if (rc) return rc;
   if (n < 1) return fail(OCTGRAV_ERR_ARG, "n must be >= 1");
   thread_local HostCache hcache;
-  if (!tl_cache) tl_cache = new Device();
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   octgrav_tree* t = nullptr;
-  if ((rc = build_oneshot(pos, mass, n, n_leaf, n_group, hcache, *tl_cache, st, &t))) return rc;
+  if ((rc = build_oneshot(pos, mass, n, n_leaf, n_group, hcache, tl_device.get(), st, &t))) return rc;
   rc = forces_host(t, eps, theta, G, acc, pot, st);
   if (rc) cudaStreamSynchronize(st);  // nothing may still read the cached host arrays
   give_back(t, &hcache);
@@ -1673,8 +1685,7 @@ int octgrav_forces_gpu(const double* pos, const double* mass, int64_t n, double 
   int rc = check_params(eps, theta, G);
   if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (!tl_cache) tl_cache = new Device();
-  Device& D = *tl_cache;
+  Device& D = tl_device.get();
   int cur = 0;
   CUDA_TRY(cudaGetDevice(&cur));
   if (D.device >= 0 && D.device != cur) D.release();

@@ -969,15 +969,15 @@ cudaError_t encode_mp_map(CUtensorMap* map, const void* mp, int n_cells) {
   using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-  static EncodeFn fn = nullptr;
-  if (!fn) {
+  static const EncodeFn fn = []() -> EncodeFn {  // looked up once, thread-safe
     void* f = nullptr;
     cudaDriverEntryPointQueryResult q;
-    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q);
-    if (e != cudaSuccess) return e;
-    if (q != cudaDriverEntryPointSuccess || !f) return cudaErrorNotSupported;
-    fn = reinterpret_cast<EncodeFn>(f);
-  }
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<EncodeFn>(f);
+  }();
+  if (!fn) return cudaErrorNotSupported;
   const cuuint64_t dims[2] = {16, static_cast<cuuint64_t>(n_cells > 0 ? n_cells : 1)};
   const cuuint64_t strides[1] = {64};
   const cuuint32_t box[2] = {16, 1};

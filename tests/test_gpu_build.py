@@ -186,6 +186,42 @@ def test_one_shot_host_call_across_sizes(torch):
             assert np.array_equal(_bits(a), _bits(ra)) and np.array_equal(_bits(p), _bits(rp))
 
 
+def test_one_shot_calls_from_threads(torch):
+    """Each calling thread has its own host arrays and device buffers: four
+    threads calling both one-shot entry points at once get the single-thread
+    results bit for bit, and their device buffers are released when they end."""
+    import threading
+
+    pos, m = W.plummer(40000, seed=41)
+    ra, rp = G.forces(pos, m, 0.01, 0.5, 16, 64)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    results = [None] * 4
+    errors = []
+
+    def work(k):
+        try:
+            torch.cuda.set_device(0)
+            out = []
+            for _ in range(3):
+                out += [G.forces(pos, m, 0.01, 0.5, 16, 64), G.forces_gpu(pos, m, 0.01, 0.5, 16, 64)]
+            results[k] = out
+        except Exception as e:  # reported below, on the main thread
+            errors.append(e)
+
+    threads = [threading.Thread(target=work, args=(k,)) for k in range(4)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    for out in results:
+        for a, p in out:
+            assert np.array_equal(_bits(a), _bits(ra)) and np.array_equal(_bits(p), _bits(rp))
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] >= free0 - (64 << 20)
+
+
 def test_device64_outputs_in_input_order(torch):
     pos, m = W.plummer(30000, seed=15)
     for T in (G.Tree.build(pos, m, 16, 64), G.Tree.build_gpu(pos, m, 16, 64)):
