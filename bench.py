@@ -722,6 +722,10 @@ def main():
                    "l2": "flushed (256 MiB write) before every timed step, outside the events",
                    "parallelism": "replica per GPU" if world > 1 else "1 GPU"},
         "gflops": achieved * 1e3, "frac_fp32_peak": achieved / peak,
+        # the paper's own figures, same flop convention (abstract, Sec. 3.3): context only --
+        # a G80 GPU, another model (Milky Way), N_leaf = N_group = 64
+        "paper_context": {"gflops": 100.0, "seconds_per_million_particles": 1.0, "theta": 0.5,
+                          "hardware": "GeForce 8800 Ultra (G80)"},
         "interactions": {"n_pp": counts["n_pp"], "n_pc": counts["n_pc"], "flops_per_step": counts["flops"],
                          "flops_per_particle": counts["flops"] / a.n},
         "e2e": None if host_s != host_s else {
