@@ -63,6 +63,21 @@ __global__ void k32(float* out, float a, float b) {
 #pragma unroll
       for (int i = 0; i < 8; i++) x[i] = __ffma2_rn(acc[i], A, x[i]);
       y[0].x = rsq(y[0].x + B.x);
+    } else if (MODE == 6) {  // FFMA2 whose repeated operand is a register pair that changes
+#pragma unroll
+      for (int i = 0; i < 8; i++) acc[i] = __ffma2_rn(x[i], y[0], acc[i]);
+#pragma unroll
+      for (int i = 0; i < 8; i++) x[i] = __ffma2_rn(acc[i], y[1], x[i]);
+      y[0] = __ffma2_rn(y[0], y[2], y[3]);
+      y[1] = __ffma2_rn(y[1], y[2], y[3]);
+    } else if (MODE == 7) {  // FFMA2 with one operand a 32-bit register in both halves
+      float* ys = reinterpret_cast<float*>(y);
+#pragma unroll
+      for (int i = 0; i < 8; i++) acc[i] = __ffma2_rn(x[i], make_float2(ys[i], ys[i]), acc[i]);
+#pragma unroll
+      for (int i = 0; i < 8; i++) x[i] = __ffma2_rn(acc[i], make_float2(ys[i + 8], ys[i + 8]), x[i]);
+#pragma unroll
+      for (int i = 0; i < 16; i++) ys[i] = fmaf(ys[i], a, b);
     }
   }
   float t = 0;
@@ -132,6 +147,9 @@ int main() {
     run("fp32 FFMA, three distinct operands", reinterpret_cast<void*>(k32<3>), false, 32, ITERS, w);
     run("MUFU rsqrt", reinterpret_cast<void*>(k32<4>), false, 32, ITERS, w);
     run("fp32 FFMA2 + 1 MUFU per 16 (FMA lane-ops)", reinterpret_cast<void*>(k32<5>), false, 32, ITERS, w);
+    run("fp32 FFMA2, one operand a changing register pair", reinterpret_cast<void*>(k32<6>), false, 36, ITERS, w);
+    run("fp32 FFMA2, one operand one register in both halves (+16 FFMA)", reinterpret_cast<void*>(k32<7>), false, 48,
+        ITERS, w);
     run("fp64 DFMA", reinterpret_cast<void*>(k64<0>), true, 8, ITERS / 8, w);
     run("fp64 DADD/DMUL", reinterpret_cast<void*>(k64<1>), true, 8, ITERS / 8, w);
     run("fp64 division (+ add)", reinterpret_cast<void*>(k64<2>), true, 8, ITERS / 8, w);
