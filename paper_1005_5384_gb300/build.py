@@ -58,7 +58,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     bo = os.path.join(BUILD, "octgrav_build.o")
     so = os.path.join(BUILD, "octgrav_sim.o")
     do = os.path.join(BUILD, "octgrav_direct.o")
-    ho = os.path.join(BUILD, "octgrav_host.o")
+    host_srcs = ("octgrav_host.cpp", "octgrav_host_build.cpp", "octgrav_host_mlp.cpp")
+    host_objs = [os.path.join(BUILD, h.replace(".cpp", ".o")) for h in host_srcs]
 
     def nv(src, obj, *extra):
         return [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xptxas", "-v" if verbose else "-O3",
@@ -69,10 +70,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     b_cmd = nv("octgrav_build.cu", bo, "-fmad=false")
     s_cmd = nv("octgrav_sim.cu", so, "-fmad=false")
     d_cmd = nv("octgrav_direct.cu", do)
-    h_cmd = ["g++", "-O3", "-std=c++17", "-fPIC", "-ffp-contract=off", "-fno-fast-math", "-pthread",
-             "-I", os.path.join(cuda, "include"), "-I", INCLUDE,
-             "-c", os.path.join(CSRC, "octgrav_host.cpp"), "-o", ho]
-    cmds = (k_cmd, m_cmd, b_cmd, s_cmd, d_cmd, h_cmd)
+    h_cmds = [["g++", "-O3", "-std=c++17", "-fPIC", "-ffp-contract=off", "-fno-fast-math", "-pthread",
+               "-I", os.path.join(cuda, "include"), "-I", INCLUDE,
+               "-c", os.path.join(CSRC, h), "-o", o] for h, o in zip(host_srcs, host_objs)]
+    cmds = (k_cmd, m_cmd, b_cmd, s_cmd, d_cmd, *h_cmds)
     procs = [subprocess.Popen(c, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True) for c in cmds]
     outs = [p.communicate()[0] for p in procs]
     for p, o, c in zip(procs, outs, cmds):
@@ -81,7 +82,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if verbose and o:
             print(o)
     tmp = LIB + ".%d.tmp" % os.getpid()
-    link = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, ko, mo, bo, so, do, ho, "-lpthread"]
+    link = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, ko, mo, bo, so, do, *host_objs, "-lpthread"]
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed: %s\n%s" % (" ".join(link), r.stdout))

@@ -1,959 +1,11 @@
-// octgrav_host.cpp -- host side of the GB300 tree-code library: FP64 octree
-// build, cell properties and groups (Sec. 2.1), device-array layout, upload,
-// launch and the C ABI declared in include/octgrav.h.
-//
-// Tree definition (shared with any independent implementation):
-//  - root cube: centre = centre of the bounding box of the system, side =
-//    longest box side * (1 + 2^-20) (1.0 when all particles coincide);
-//  - quantised coordinate q = floor((x - lo) / side * 2^21) clamped to
-//    [0, 2^21 - 1]; the octant of a depth-L cell's child is bit (20 - L) of q
-//    on each axis (x = octant bit 0), so cells are Morton-key prefixes;
-//  - a cell is a leaf when it holds <= n_leaf particles or has depth 21;
-//  - groups are the cells reached first from the root that are leaves or hold
-//    <= n_group particles (Sec. 2.1-2.2);
-//  - per cell: tight box, boundary cube (centre = box centre, half side = half
-//    the longest box side, Fig. 1), mass, centre of mass and second moments.
-// The build sorts particles by Morton key (parallel LSD radix sort), splits
-// key ranges level by level, and combines moments bottom-up with the
-// parallel-axis theorem, all in FP64 (products accumulated with explicit fused
-// multiply-adds). Compile with -ffp-contract=off: the GPU build reproduces
-// these operations one for one.
-#include <algorithm>
-#include <atomic>
-#include <chrono>
-#include <cmath>
-#include <condition_variable>
-#include <cstdarg>
-#include <cstdio>
-#include <cstring>
-#include <functional>
-#include <memory>
-#include <mutex>
-#include <new>
-#include <string>
-#include <thread>
-#include <type_traits>
-#include <utility>
-#include <vector>
+// octgrav_host.cpp -- the device side of a tree on the host: device buffers,
+// upload, launch, the one-shot calls, the GPU build's host glue, the time
+// integration and the C ABI declared in include/octgrav.h (the learned
+// criterion's calls are in octgrav_host_mlp.cpp, the FP64 build in
+// octgrav_host_build.cpp).
+#include "octgrav_host.h"
 
-#include <cuda_runtime.h>
-
-#include "../../include/octgrav.h"
-#include "octgrav_internal.h"
-#include "octgrav_mlp.h"
-
-namespace {
-
-constexpr int kMaxDepth = OCTGRAV_MAX_DEPTH;
-
-// Allocator whose construct() without arguments default-initialises, so that
-// resize() of a vector of plain numbers leaves the new elements unwritten. The
-// build's arrays are all filled completely (in parallel) right after they are
-// sized; value-initialisation would first zero them on one thread (~200 MB per
-// million particles).
-template <class T>
-struct NoInit : std::allocator<T> {
-  template <class U>
-  struct rebind {
-    using other = NoInit<U>;
-  };
-  NoInit() = default;
-  template <class U>
-  NoInit(const NoInit<U>&) noexcept {}
-  template <class U>
-  void construct(U* p) noexcept(std::is_nothrow_default_constructible<U>::value) {
-    ::new (static_cast<void*>(p)) U;
-  }
-  template <class U, class... A>
-  void construct(U* p, A&&... a) {
-    ::new (static_cast<void*>(p)) U(std::forward<A>(a)...);
-  }
-};
-template <class T>
-using hvec = std::vector<T, NoInit<T>>;
-
-// ---------------------------------------------------------------- errors
-
-thread_local std::string g_err;
-
-int fail(int code, const char* fmt, ...) {
-  char buf[512];
-  va_list ap;
-  va_start(ap, fmt);
-  vsnprintf(buf, sizeof buf, fmt, ap);
-  va_end(ap);
-  g_err = buf;
-  return code;
-}
-
-#define CUDA_TRY(call)                                                                   \
-  do {                                                                                   \
-    cudaError_t e_ = (call);                                                             \
-    if (e_ != cudaSuccess)                                                               \
-      return fail(OCTGRAV_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));     \
-  } while (0)
-
-// ---------------------------------------------------------------- thread pool
-
-class Pool {
- public:
-  static Pool& get() {
-    static Pool p;
-    return p;
-  }
-  int size() const { return static_cast<int>(threads_.size()) + 1; }
-
-  // Run fn(chunk) for chunk in [0, nchunks) on all workers and the caller.
-  // Workers spin for a short while after a job before they sleep, so the many
-  // short parallel loops of a build do not each pay a wake-up of every thread.
-  void run(int nchunks, const std::function<void(int)>& fn) {
-    if (nchunks <= 0) return;
-    if (threads_.empty() || nchunks == 1 || in_pool_) {
-      for (int c = 0; c < nchunks; ++c) fn(c);
-      return;
-    }
-    std::lock_guard<std::mutex> one(run_mu_);  // one parallel region at a time
-    job_ = &fn;
-    nchunks_ = nchunks;
-    next_.store(0, std::memory_order_relaxed);
-    pending_.store(static_cast<int>(threads_.size()), std::memory_order_relaxed);
-    gen_.fetch_add(1, std::memory_order_seq_cst);
-    if (sleepers_.load(std::memory_order_seq_cst) > 0) {
-      { std::lock_guard<std::mutex> g(mu_); }
-      cv_.notify_all();
-    }
-    work();
-    if (!spin_until([&] { return pending_.load(std::memory_order_acquire) == 0; })) {
-      std::unique_lock<std::mutex> g(mu_);
-      done_cv_.wait(g, [&] { return pending_.load(std::memory_order_acquire) == 0; });
-    }
-    job_ = nullptr;
-  }
-
- private:
-  Pool() {
-    unsigned hc = std::thread::hardware_concurrency();
-    int n = static_cast<int>(hc ? hc : 1);
-    if (const char* e = getenv("OCTGRAV_THREADS")) n = std::max(1, atoi(e));
-    n = std::min(n, 64);
-    for (int t = 1; t < n; ++t) threads_.emplace_back([this] { loop(); });
-  }
-  ~Pool() {
-    stop_.store(true);
-    gen_.fetch_add(1, std::memory_order_release);
-    {
-      std::lock_guard<std::mutex> g(mu_);
-    }
-    cv_.notify_all();
-    for (auto& t : threads_) t.join();
-  }
-  // Spin until pred() holds or ~50 us have passed; true if it holds.
-  template <class P>
-  static bool spin_until(P pred) {
-    auto t0 = std::chrono::steady_clock::now();
-    for (int k = 0;; ++k) {
-      if (pred()) return true;
-      if ((k & 255) == 255 && std::chrono::steady_clock::now() - t0 > std::chrono::microseconds(50)) return pred();
-    }
-  }
-  void work() {
-    in_pool_ = true;
-    for (;;) {
-      int c = next_.fetch_add(1, std::memory_order_relaxed);
-      if (c >= nchunks_) break;
-      (*job_)(c);
-    }
-    in_pool_ = false;
-  }
-  void loop() {
-    uint64_t seen = 0;
-    for (;;) {
-      if (!spin_until([&] { return gen_.load(std::memory_order_acquire) != seen; })) {
-        std::unique_lock<std::mutex> g(mu_);
-        sleepers_.fetch_add(1, std::memory_order_seq_cst);
-        cv_.wait(g, [&] { return gen_.load(std::memory_order_seq_cst) != seen; });
-        sleepers_.fetch_sub(1, std::memory_order_relaxed);
-      }
-      seen = gen_.load(std::memory_order_acquire);
-      if (stop_.load()) return;
-      work();
-      if (pending_.fetch_sub(1, std::memory_order_acq_rel) == 1) {
-        { std::lock_guard<std::mutex> g(mu_); }
-        done_cv_.notify_all();
-      }
-    }
-  }
-  std::vector<std::thread> threads_;
-  std::mutex mu_, run_mu_;
-  std::condition_variable cv_, done_cv_;
-  const std::function<void(int)>* job_ = nullptr;
-  int nchunks_ = 0;
-  std::atomic<int> next_{0};
-  std::atomic<int> pending_{0};
-  std::atomic<int> sleepers_{0};
-  std::atomic<uint64_t> gen_{0};
-  std::atomic<bool> stop_{false};
-  static thread_local bool in_pool_;
-};
-thread_local bool Pool::in_pool_ = false;
-
-// parallel_for over [0, n) in chunks of at least `grain` elements.
-void parallel_for(int64_t n, int64_t grain, const std::function<void(int64_t, int64_t)>& fn) {
-  if (n <= 0) return;
-  Pool& P = Pool::get();
-  int64_t chunks = std::min<int64_t>((n + grain - 1) / grain, 8 * P.size());
-  if (chunks <= 1) {
-    fn(0, n);
-    return;
-  }
-  const int64_t step = (n + chunks - 1) / chunks;
-  P.run(static_cast<int>(chunks), [&](int c) {
-    int64_t lo = c * step, hi = std::min(n, lo + step);
-    if (lo < hi) fn(lo, hi);
-  });
-}
-
-// ---------------------------------------------------------------- Morton keys
-
-inline uint64_t spread21(uint64_t v) {
-  v &= 0x1fffffull;
-  v = (v | v << 32) & 0x1f00000000ffffull;
-  v = (v | v << 16) & 0x1f0000ff0000ffull;
-  v = (v | v << 8) & 0x100f00f00f00f00full;
-  v = (v | v << 4) & 0x10c30c30c30c30c3ull;
-  v = (v | v << 2) & 0x1249249249249249ull;
-  return v;
-}
-
-// Stable LSD radix sort of (key, val) by key (63 significant bits, 9-bit digits).
-void radix_sort(hvec<uint64_t>& key, hvec<uint32_t>& val, hvec<uint64_t>& k2, hvec<uint32_t>& v2,
-                bool parallel) {
-  const int64_t n = static_cast<int64_t>(key.size());
-  k2.resize(n);
-  v2.resize(n);
-  constexpr int BITS = 9, B = 1 << BITS, PASSES = (63 + BITS - 1) / BITS;
-  const int T = parallel ? std::max(1, std::min<int>(Pool::get().size(), static_cast<int>(n / 65536))) : 1;
-  std::vector<int64_t> hist(static_cast<size_t>(T) * B);
-  const int64_t step = (n + T - 1) / T;
-  for (int pass = 0; pass < PASSES; ++pass) {
-    const int sh = pass * BITS;
-    auto body_hist = [&](int t) {
-      int64_t* h = &hist[static_cast<size_t>(t) * B];
-      std::fill(h, h + B, 0);
-      const int64_t lo = t * step, hi = std::min(n, lo + step);
-      for (int64_t i = lo; i < hi; ++i) ++h[(key[i] >> sh) & (B - 1)];
-    };
-    if (T > 1) Pool::get().run(T, body_hist); else body_hist(0);
-    int64_t off = 0;
-    for (int d = 0; d < B; ++d)
-      for (int t = 0; t < T; ++t) {
-        int64_t c = hist[static_cast<size_t>(t) * B + d];
-        hist[static_cast<size_t>(t) * B + d] = off;
-        off += c;
-      }
-    auto body_scatter = [&](int t) {
-      int64_t* h = &hist[static_cast<size_t>(t) * B];
-      const int64_t lo = t * step, hi = std::min(n, lo + step);
-      for (int64_t i = lo; i < hi; ++i) {
-        int64_t dst = h[(key[i] >> sh) & (B - 1)]++;
-        k2[dst] = key[i];
-        v2[dst] = val[i];
-      }
-    };
-    if (T > 1) Pool::get().run(T, body_scatter); else body_scatter(0);
-    key.swap(k2);
-    val.swap(v2);
-  }
-}
-
-// ---------------------------------------------------------------- one system
-
-struct SysTree {
-  int64_t n = 0;
-  hvec<uint32_t> perm;  // tree position -> index within the system
-  hvec<uint64_t> code;  // Morton code per tree position
-  hvec<double> x;       // 3 per tree position
-  hvec<double> m;
-  // cells in breadth-first order (children of a node are contiguous)
-  hvec<uint64_t> key;
-  hvec<int32_t> depth, parent, first_child, n_child;
-  hvec<int64_t> pfirst, pcount;
-  hvec<double> bmin, bmax, cube, M, com, S;  // 3, 3, 4, 1, 3, 6 per cell
-  hvec<int32_t> groups;                      // cell index, tree (Morton) order
-  int depth_reached = 0;
-  int64_t max_group = 0;
-  int64_t n_leaves = 0;
-  // scratch of the build (kept so that a reused SysTree allocates nothing)
-  hvec<uint64_t> k2;
-  hvec<uint32_t> v2;
-  hvec<int64_t> splits;                      // 9 per cell of the level being split
-  std::vector<int32_t> nch;                  // children per cell of that level
-  std::vector<int64_t> child_base;           // first child per chunk of that level
-  // empty every array but keep its memory, for a new build
-  void reset() {
-    n = 0;
-    for (auto* v : {&perm, &v2}) v->clear();
-    for (auto* v : {&code, &key, &k2}) v->clear();
-    for (auto* v : {&x, &m, &bmin, &bmax, &cube, &M, &com, &S}) v->clear();
-    for (auto* v : {&depth, &parent, &first_child, &n_child, &groups}) v->clear();
-    for (auto* v : {&pfirst, &pcount, &splits}) v->clear();
-    nch.clear();
-    child_base.clear();
-    depth_reached = 0;
-    max_group = 0;
-    n_leaves = 0;
-  }
-};
-
-inline int octant_at(uint64_t code, int child_depth) {
-  return static_cast<int>((code >> (3 * (kMaxDepth - child_depth))) & 7);
-}
-
-// A particle's two device records: (x_hi, y_hi, z_hi, m) and (x_lo, y_lo, z_lo, 0),
-// hi = fl32(x) and lo = fl32(x - hi).
-inline void particle_records(const double* x, double m, float4* rec) {
-  float hi[3], lo[3];
-  for (int d = 0; d < 3; ++d) {
-    hi[d] = static_cast<float>(x[d]);
-    lo[d] = static_cast<float>(x[d] - static_cast<double>(hi[d]));
-  }
-  rec[0] = make_float4(hi[0], hi[1], hi[2], static_cast<float>(m));
-  rec[1] = make_float4(lo[0], lo[1], lo[2], 0.f);
-}
-
-// Where a one-system build writes its particle images during the gather (tree
-// order), and what to call once they are complete (e.g. to start their upload
-// while the cells are built).
-struct ParticleSink {
-  float4* parts = nullptr;  // 2 records per particle
-  int64_t* perm = nullptr;
-  int32_t* perm32 = nullptr;
-  std::function<int()> ready;
-  bool check_inputs = false;  // the bounding-box pass also checks the inputs (finite, masses >= 0)
-};
-
-int build_system(const double* pos, const double* mass, int64_t n, int n_leaf, int n_group,
-                 bool parallel, SysTree& T, const ParticleSink* sink = nullptr) {
-  T.reset();
-  T.n = n;
-  const int64_t grain = parallel ? 16384 : (int64_t)1 << 62;
-  // ---- bounding box and root cube
-  double mn[3] = {pos[0], pos[1], pos[2]}, mx[3] = {pos[0], pos[1], pos[2]};
-  {
-    const int64_t chunks = parallel ? std::max<int64_t>(1, std::min<int64_t>(64, n / 65536)) : 1;
-    std::vector<double> part(chunks * 6);
-    const int64_t step = (n + chunks - 1) / chunks;
-    const bool check = sink && sink->check_inputs;
-    std::vector<uint8_t> bad(chunks, 0);
-    auto body = [&](int c) {
-      double a[3] = {pos[0], pos[1], pos[2]}, b[3] = {pos[0], pos[1], pos[2]};
-      bool ok = true;
-      for (int64_t i = c * step; i < std::min(n, (c + 1) * step); ++i) {
-        for (int d = 0; d < 3; ++d) {
-          const double v = pos[3 * i + d];
-          if (v < a[d]) a[d] = v;
-          if (v > b[d]) b[d] = v;
-          if (check) ok = ok && std::isfinite(v);
-        }
-        if (check) ok = ok && std::isfinite(mass[i]) && mass[i] >= 0;
-      }
-      for (int d = 0; d < 3; ++d) {
-        part[6 * c + d] = a[d];
-        part[6 * c + 3 + d] = b[d];
-      }
-      bad[c] = !ok;
-    };
-    if (chunks > 1) Pool::get().run(static_cast<int>(chunks), body); else body(0);
-    for (int64_t c = 0; c < chunks; ++c)
-      if (bad[c]) return fail(OCTGRAV_ERR_NONFINITE, "non-finite position/mass or negative mass");
-    for (int64_t c = 0; c < chunks; ++c)
-      for (int d = 0; d < 3; ++d) {
-        mn[d] = std::min(mn[d], part[6 * c + d]);
-        mx[d] = std::max(mx[d], part[6 * c + 3 + d]);
-      }
-  }
-  double ext = mx[0] - mn[0];
-  if (mx[1] - mn[1] > ext) ext = mx[1] - mn[1];
-  if (mx[2] - mn[2] > ext) ext = mx[2] - mn[2];
-  if (!(ext > 0)) ext = 1.0;
-  const double side = ext * (1.0 + 1.0 / 1048576.0);
-  double lo[3];
-  for (int d = 0; d < 3; ++d) lo[d] = (mn[d] + mx[d]) * 0.5 - side * 0.5;
-  const double scale = std::ldexp(1.0, kMaxDepth);
-  const uint64_t qmax = (1ull << kMaxDepth) - 1;
-
-  // ---- Morton codes and sort
-  hvec<uint64_t>& code = T.code;
-  hvec<uint32_t>& idx = T.perm;
-  code.resize(n);
-  idx.resize(n);
-  parallel_for(n, grain, [&](int64_t a, int64_t b) {
-    for (int64_t i = a; i < b; ++i) {
-      uint64_t q[3];
-      for (int d = 0; d < 3; ++d) {
-        const double u = (pos[3 * i + d] - lo[d]) / side;
-        const double v = std::floor(u * scale);
-        q[d] = v <= 0 ? 0 : (v >= static_cast<double>(qmax) ? qmax : static_cast<uint64_t>(v));
-      }
-      code[i] = spread21(q[0]) | (spread21(q[1]) << 1) | (spread21(q[2]) << 2);
-      idx[i] = static_cast<uint32_t>(i);
-    }
-  });
-  radix_sort(code, idx, T.k2, T.v2, parallel);
-  T.x.resize(3 * n);
-  T.m.resize(n);
-  parallel_for(n, grain, [&](int64_t a, int64_t b) {
-    constexpr int64_t ahead = 16;  // prefetch distance of the random reads
-    for (int64_t t = a; t < b; ++t) {
-      if (t + ahead < b) {
-        const int64_t j = T.perm[t + ahead];
-        __builtin_prefetch(pos + 3 * j);
-        __builtin_prefetch(pos + 3 * j + 2);
-        __builtin_prefetch(mass + j);
-      }
-      const int64_t i = T.perm[t];
-      T.x[3 * t] = pos[3 * i];
-      T.x[3 * t + 1] = pos[3 * i + 1];
-      T.x[3 * t + 2] = pos[3 * i + 2];
-      T.m[t] = mass[i];
-      if (sink) {
-        particle_records(&T.x[3 * t], T.m[t], sink->parts + 2 * t);
-        sink->perm[t] = i;
-        sink->perm32[t] = static_cast<int32_t>(i);
-      }
-    }
-  });
-  if (sink && sink->ready) {
-    const int rc = sink->ready();
-    if (rc) return rc;
-  }
-
-  // ---- cells, level by level
-  auto push_cell = [&](uint64_t key, int depth, int32_t parent, int64_t pf, int64_t pc) {
-    T.key.push_back(key);
-    T.depth.push_back(depth);
-    T.parent.push_back(parent);
-    T.first_child.push_back(-1);
-    T.n_child.push_back(0);
-    T.pfirst.push_back(pf);
-    T.pcount.push_back(pc);
-  };
-  {  // room for the usual tree size, so that the level loop rarely reallocates
-    const size_t guess = static_cast<size_t>(8 * n / (n_leaf + 1) + 64);
-    for (auto* v : {&T.depth, &T.parent, &T.first_child, &T.n_child}) v->reserve(guess);
-    T.key.reserve(guess);
-    T.pfirst.reserve(guess);
-    T.pcount.reserve(guess);
-  }
-  push_cell(1, 0, -1, 0, n);
-  std::vector<int64_t> level_begin = {0};
-  hvec<int64_t>& splits = T.splits;  // read only where nch > 0
-  std::vector<int32_t>& nch = T.nch;
-  std::vector<int64_t>& child_base = T.child_base;
-  for (int L = 0;; ++L) {
-    const int64_t lb = level_begin.back(), le = static_cast<int64_t>(T.key.size());
-    if (lb == le) break;
-    const int64_t nl = le - lb;
-    splits.resize(9 * nl);
-    nch.resize(nl);
-    // the level in fixed chunks: a first pass counts each chunk's children, a
-    // scan over the chunk totals places them in breadth-first order, and a
-    // second pass writes them
-    const int64_t nchunk = parallel ? std::min<int64_t>(8 * Pool::get().size(), std::max<int64_t>(1, nl / 256)) : 1;
-    const int64_t cstep = (nl + nchunk - 1) / nchunk;
-    child_base.assign(nchunk + 1, 0);
-    auto split_chunk = [&](int q) {
-      int64_t total = 0;
-      for (int64_t k = q * cstep; k < std::min(nl, (q + 1) * cstep); ++k) {
-        const int64_t c = lb + k;
-        const int64_t f = T.pfirst[c], cnt = T.pcount[c];
-        int64_t* sp = &splits[9 * k];
-        nch[k] = 0;
-        if (cnt <= n_leaf || L >= kMaxDepth) continue;
-        sp[0] = f;
-        sp[8] = f + cnt;
-        const uint64_t* base = T.code.data();
-        for (int o = 1; o < 8; ++o) {
-          // first position whose child octant is >= o (octants ascend inside a cell)
-          const uint64_t* it = std::partition_point(base + sp[o - 1], base + f + cnt,
-                                                    [&](uint64_t cd) { return octant_at(cd, L + 1) < o; });
-          sp[o] = it - base;
-        }
-        int k8 = 0;
-        for (int o = 0; o < 8; ++o) k8 += sp[o + 1] > sp[o];
-        nch[k] = k8;
-        total += k8;
-      }
-      child_base[q + 1] = total;
-    };
-    Pool::get().run(static_cast<int>(nchunk), split_chunk);
-    for (int64_t q = 0; q < nchunk; ++q) child_base[q + 1] += child_base[q];
-    const int64_t next = le + child_base[nchunk];
-    if (next == le) break;
-    level_begin.push_back(le);
-    if (next >= (1ll << 28)) return fail(OCTGRAV_ERR_ARG, "tree too large (%lld cells)", (long long)next);
-    T.key.resize(next);
-    T.depth.resize(next);
-    T.parent.resize(next);
-    T.first_child.resize(next);
-    T.n_child.resize(next);
-    T.pfirst.resize(next);
-    T.pcount.resize(next);
-    auto emit_chunk = [&](int q) {
-      int64_t w = le + child_base[q];
-      for (int64_t k = q * cstep; k < std::min(nl, (q + 1) * cstep); ++k) {
-        if (!nch[k]) continue;
-        const int64_t c = lb + k;
-        T.first_child[c] = static_cast<int32_t>(w);
-        T.n_child[c] = nch[k];
-        const int64_t* sp = &splits[9 * k];
-        for (int o = 0; o < 8; ++o) {
-          if (sp[o + 1] <= sp[o]) continue;
-          T.key[w] = (T.key[c] << 3) | static_cast<uint64_t>(o);
-          T.depth[w] = L + 1;
-          T.parent[w] = static_cast<int32_t>(c);
-          T.first_child[w] = -1;
-          T.n_child[w] = 0;
-          T.pfirst[w] = sp[o];
-          T.pcount[w] = sp[o + 1] - sp[o];
-          ++w;
-        }
-      }
-    };
-    Pool::get().run(static_cast<int>(nchunk), emit_chunk);
-  }
-  const int64_t nc = static_cast<int64_t>(T.key.size());
-  T.depth_reached = static_cast<int>(level_begin.size()) - 1;
-
-  // ---- cell properties, deepest level first
-  T.bmin.resize(3 * nc);
-  T.bmax.resize(3 * nc);
-  T.cube.resize(4 * nc);
-  T.M.resize(nc);
-  T.com.resize(3 * nc);
-  T.S.resize(6 * nc);
-  level_begin.push_back(nc);
-  for (int L = static_cast<int>(level_begin.size()) - 2; L >= 0; --L) {
-    const int64_t lb = level_begin[L], le = level_begin[L + 1];
-    parallel_for(le - lb, parallel ? 1024 : (int64_t)1 << 62, [&](int64_t a, int64_t b) {
-      for (int64_t c = lb + a; c < lb + b; ++c) {
-        double* bn = &T.bmin[3 * c];
-        double* bx = &T.bmax[3 * c];
-        double* cm = &T.com[3 * c];
-        double* s6 = &T.S[6 * c];
-        double Mc = 0, sx = 0, sy = 0, sz = 0;
-        for (int d = 0; d < 3; ++d) {
-          bn[d] = INFINITY;
-          bx[d] = -INFINITY;
-        }
-        const int64_t f = T.pfirst[c], cnt = T.pcount[c];
-        if (T.n_child[c] == 0) {
-          for (int64_t t = f; t < f + cnt; ++t) {
-            const double* xp = &T.x[3 * t];
-            for (int d = 0; d < 3; ++d) {
-              bn[d] = std::min(bn[d], xp[d]);
-              bx[d] = std::max(bx[d], xp[d]);
-            }
-            Mc += T.m[t];
-            sx = std::fma(T.m[t], xp[0], sx);
-            sy = std::fma(T.m[t], xp[1], sy);
-            sz = std::fma(T.m[t], xp[2], sz);
-          }
-        } else {
-          for (int j = T.first_child[c]; j < T.first_child[c] + T.n_child[c]; ++j) {
-            for (int d = 0; d < 3; ++d) {
-              bn[d] = std::min(bn[d], T.bmin[3 * j + d]);
-              bx[d] = std::max(bx[d], T.bmax[3 * j + d]);
-            }
-            Mc += T.M[j];
-            sx = std::fma(T.M[j], T.com[3 * j], sx);
-            sy = std::fma(T.M[j], T.com[3 * j + 1], sy);
-            sz = std::fma(T.M[j], T.com[3 * j + 2], sz);
-          }
-        }
-        double* cu = &T.cube[4 * c];
-        for (int d = 0; d < 3; ++d) cu[d] = (bn[d] + bx[d]) * 0.5;
-        double e = bx[0] - bn[0];
-        if (bx[1] - bn[1] > e) e = bx[1] - bn[1];
-        if (bx[2] - bn[2] > e) e = bx[2] - bn[2];
-        cu[3] = 0.5 * e;
-        T.M[c] = Mc;
-        if (Mc > 0) {
-          cm[0] = sx / Mc;
-          cm[1] = sy / Mc;
-          cm[2] = sz / Mc;
-        } else {
-          cm[0] = cu[0];
-          cm[1] = cu[1];
-          cm[2] = cu[2];
-        }
-        for (int q = 0; q < 6; ++q) s6[q] = 0;
-        auto add_outer = [&](double w, double y0, double y1, double y2) {
-          const double w0 = w * y0, w1 = w * y1, w2 = w * y2;
-          s6[0] = std::fma(w0, y0, s6[0]);
-          s6[1] = std::fma(w1, y1, s6[1]);
-          s6[2] = std::fma(w2, y2, s6[2]);
-          s6[3] = std::fma(w0, y1, s6[3]);
-          s6[4] = std::fma(w0, y2, s6[4]);
-          s6[5] = std::fma(w1, y2, s6[5]);
-        };
-        if (T.n_child[c] == 0) {
-          for (int64_t t = f; t < f + cnt; ++t)
-            add_outer(T.m[t], T.x[3 * t] - cm[0], T.x[3 * t + 1] - cm[1], T.x[3 * t + 2] - cm[2]);
-        } else {
-          for (int j = T.first_child[c]; j < T.first_child[c] + T.n_child[c]; ++j) {
-            for (int q = 0; q < 6; ++q) s6[q] += T.S[6 * j + q];
-            add_outer(T.M[j], T.com[3 * j] - cm[0], T.com[3 * j + 1] - cm[1], T.com[3 * j + 2] - cm[2]);
-          }
-        }
-      }
-    });
-  }
-
-  // ---- groups: first cells from the root that are leaves or hold <= n_group.
-  // Such eligibility passes from a cell to its children (a child of a leaf does
-  // not exist, and a child never holds more particles than its parent), so the
-  // first eligible cells on the paths from the root are the eligible cells
-  // whose parent is not eligible.
-  auto eligible = [&](int64_t c) { return T.n_child[c] == 0 || T.pcount[c] <= n_group; };
-  {
-    const int64_t chunks = parallel ? std::min<int64_t>(64, std::max<int64_t>(1, nc / 8192)) : 1;
-    const int64_t step = (nc + chunks - 1) / chunks;
-    std::vector<std::vector<int32_t>> found(chunks);
-    std::vector<int64_t> leaves(chunks, 0);
-    auto body = [&](int k) {
-      for (int64_t c = k * step; c < std::min(nc, (k + 1) * step); ++c) {
-        leaves[k] += T.n_child[c] == 0;
-        if (eligible(c) && (c == 0 || !eligible(T.parent[c]))) found[k].push_back(static_cast<int32_t>(c));
-      }
-    };
-    if (chunks > 1) Pool::get().run(static_cast<int>(chunks), body); else body(0);
-    T.n_leaves = 0;
-    for (int64_t k = 0; k < chunks; ++k) {
-      T.n_leaves += leaves[k];
-      T.groups.insert(T.groups.end(), found[k].begin(), found[k].end());
-    }
-  }
-  std::sort(T.groups.begin(), T.groups.end(),
-            [&](int32_t a, int32_t b) { return T.pfirst[a] < T.pfirst[b]; });
-  for (int32_t g : T.groups) T.max_group = std::max(T.max_group, T.pcount[g]);
-  return OCTGRAV_OK;
-}
-
-// ---------------------------------------------------------------- device buffers
-
-struct DevBuf {
-  void* p = nullptr;
-  size_t cap = 0;
-  int reserve(size_t bytes) {
-    if (bytes <= cap && p) return OCTGRAV_OK;
-    if (p) cudaFree(p);
-    p = nullptr;
-    cap = 0;
-    size_t want = std::max<size_t>(bytes, 256);
-    cudaError_t e = cudaMalloc(&p, want);
-    if (e != cudaSuccess) {
-      p = nullptr;
-      return fail(e == cudaErrorMemoryAllocation ? OCTGRAV_ERR_OOM : OCTGRAV_ERR_CUDA,
-                  "cudaMalloc(%zu) failed: %s", want, cudaGetErrorString(e));
-    }
-    cap = want;
-    return OCTGRAV_OK;
-  }
-  void release() {
-    if (p) cudaFree(p);
-    p = nullptr;
-    cap = 0;
-  }
-};
-
-struct Device {
-  DevBuf parts, geo, link, mp, items, ibox, sysp, out, counts, ctl, dbg, mlp;
-  // GPU build: tree arrays beyond the walk's, scratch, inputs and FP64 outputs
-  DevBuf perm, key, props, pcount, cfirst, groups, ikey, celloff, result, scratch, in_pos, in_mass, acc64, pot64;
-  DevBuf order;  // work-item processing order (octgrav_balance)
-  int device = -1;
-  int pageable = -1;     // kernels may read pageable host memory (-1: not asked yet)
-  int64_t cell_cap = 0;  // cell capacity that last sufficed for a GPU build
-  int level_hint = 0;    // depth of the last GPU build + 2 (0: none yet), caps the next level loop
-  // the GPU build's kernels captured as a graph, replayed on gstream while
-  // build_key (every argument, pointers included) stays the same
-  cudaGraphExec_t build_exec = nullptr;
-  std::vector<int64_t> build_key;
-  cudaStream_t gstream = nullptr;
-  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-  void release_graph() {
-    if (build_exec) cudaGraphExecDestroy(build_exec);
-    build_exec = nullptr;
-    build_key.clear();
-  }
-  void release() {
-    release_graph();
-    if (gstream) cudaStreamDestroy(gstream);
-    if (ev_in) cudaEventDestroy(ev_in);
-    if (ev_out) cudaEventDestroy(ev_out);
-    gstream = nullptr;
-    ev_in = ev_out = nullptr;
-    for (DevBuf* b : {&parts, &geo, &link, &mp, &items, &ibox, &sysp, &out, &counts, &ctl, &dbg, &mlp, &perm, &key,
-                      &props, &pcount, &cfirst, &groups, &ikey, &celloff, &result, &scratch, &in_pos, &in_mass,
-                      &acc64, &pot64, &order})
-      b->release();
-    cell_cap = 0;
-  }
-};
-
-}  // namespace
-
-// ---------------------------------------------------------------- the tree object
-
-struct octgrav_tree {
-  int64_t n = 0;
-  int n_leaf = 0, n_group = 0, n_sys = 0;
-  int ppl = 2, ctas_per_sm = 0;
-  int stage = og::STAGING_ASYNC;
-  bool learned = false;             // learned opening criterion active
-  float theta_lo = 0, theta_hi = 0, theta_fb = 0;
-  CUtensorMap mp_map;
-  std::vector<int64_t> sys_off;   // particle offsets per system (n_sys + 1)
-  std::vector<int64_t> cell_off;  // cell offsets per system (n_sys + 1)
-  hvec<int64_t> perm;             // tree position -> input index
-  hvec<int32_t> perm32;           // the same as int32, the device image
-  hvec<uint64_t> key;             // per global cell
-  std::vector<int32_t> group_cell;  // per group, global cell index
-  std::vector<int32_t> group_sys;
-  int64_t n_cells = 0, n_leaves = 0, max_group = 0;
-  int depth_reached = 0;
-  // host images of the device arrays
-  hvec<float4> parts, geo, mp, ibox;
-  hvec<int2> link;
-  hvec<int4> items;
-  hvec<uint64_t> item_key;
-  // host FP64 cell properties (tests / introspection)
-  hvec<double> bmin, bmax, cube, M, com, S;
-  hvec<int64_t> pcount;
-  hvec<int32_t> cfirst;           // first particle (tree position) of every cell
-  std::vector<int32_t> group_item;  // first work item of every group
-  // per-system parameters (optional)
-  std::vector<float4> sysp;
-  bool sysp_dirty = false;
-  // device state
-  Device own;
-  Device* dev = &own;
-  bool uploaded = false;
-  bool launched = false;
-  // built on the GPU: the device arrays are the tree; the host images above
-  // are filled on demand (host_valid)
-  bool gpu = false;
-  bool host_valid = true;
-  bool perm_on_device = false;  // Device::perm holds the permutation (int32)
-  bool parts_on_device = false;  // Device::parts already holds (or receives) the particle records
-  bool pull_images = false;      // upload may pull the host images by kernel (the one-shot call, whose
-                                 // images stay unchanged until it has waited for the stream)
-  int64_t n_groups = 0, n_items = 0;
-  bool ordered = false;  // launches take the work items in Device::order (octgrav_balance)
-  hvec<int32_t> item_order;  // host image of the default order (host-built trees)
-  int64_t cell_cap = 0;  // cell capacity of the device arrays of a GPU-built tree
-  cudaGraphExec_t gexec = nullptr;  // captured memset + kernel (octgrav_graph_capture)
-  std::vector<SysTree> sys_scratch;
-};
-
-// N-body state for the time integration, all on one device.
-struct octgrav_sim {
-  int64_t n = 0;
-  double eps = 0, theta = 0, G = 1;
-  int n_leaf = 16, n_group = 16;
-  Device dev;                        // tree and build buffers, reused every step
-  DevBuf x, v, m, a, phi, epart;     // FP64 state (input order) and energy partials
-  int64_t steps = 0;
-  int rebuild_every = 1;             // full build every k force evaluations, refit in between
-  int since_build = 0;
-  octgrav_tree* tree = nullptr;      // the last built tree (its buffers live in dev)
-  ~octgrav_sim();
-};
-
-namespace {
-
-// Split every group into work items of at most 32 * ppl particles.
-void make_items(octgrav_tree* t) {
-  const int item_max = 32 * t->ppl;
-  const int64_t ng = static_cast<int64_t>(t->group_cell.size());
-  t->group_item.assign(ng, 0);
-  int64_t ni = 0;
-  for (int64_t g = 0; g < ng; ++g) {
-    t->group_item[g] = static_cast<int32_t>(ni);
-    ni += (t->pcount[t->group_cell[g]] + item_max - 1) / item_max;
-  }
-  t->items.resize(ni);
-  t->ibox.resize(4 * ni);
-  t->item_key.resize(ni);
-  parallel_for(ng, 1024, [&](int64_t a, int64_t b) {
-    for (int64_t g = a; g < b; ++g) {
-      const int64_t c = t->group_cell[g];
-      const int s = t->group_sys[g];
-      const int64_t root = t->cell_off[s];
-      const int64_t cnt = t->pcount[c];
-      const int64_t pf = t->cfirst[c];  // first particle of the group (tree position)
-      float4 bx[3];
-      float chi[3], clo[3];
-      for (int d = 0; d < 3; ++d) {
-        const double C = t->cube[4 * c + d];
-        chi[d] = static_cast<float>(C);
-        clo[d] = static_cast<float>(C - static_cast<double>(chi[d]));
-      }
-      bx[0] = make_float4(static_cast<float>(t->bmin[3 * c]), static_cast<float>(t->bmin[3 * c + 1]),
-                          static_cast<float>(t->bmin[3 * c + 2]), chi[0]);
-      bx[1] = make_float4(static_cast<float>(t->bmax[3 * c]), static_cast<float>(t->bmax[3 * c + 1]),
-                          static_cast<float>(t->bmax[3 * c + 2]), chi[1]);
-      bx[2] = make_float4(clo[0], clo[1], clo[2], chi[2]);
-      float4 grange;  // (first particle, count) of the whole group, as int bits
-      const int32_t gr[2] = {static_cast<int32_t>(pf), static_cast<int32_t>(cnt)};
-      std::memcpy(&grange.x, &gr[0], 4);
-      std::memcpy(&grange.y, &gr[1], 4);
-      grange.z = grange.w = 0.f;
-      int64_t k = t->group_item[g];
-      for (int64_t off = 0; off < cnt; off += item_max, ++k) {
-        t->items[k] = make_int4(static_cast<int>(root), static_cast<int>(pf + off),
-                                static_cast<int>(std::min<int64_t>(item_max, cnt - off)), s);
-        t->ibox[4 * k] = bx[0];
-        t->ibox[4 * k + 1] = bx[1];
-        t->ibox[4 * k + 2] = bx[2];
-        t->ibox[4 * k + 3] = grange;
-        t->item_key[k] = t->key[c];
-      }
-    }
-  });
-  t->n_groups = ng;
-  t->n_items = ni;
-  // default processing order: most particles first (a stable counting sort by count)
-  std::vector<int64_t> start(item_max + 2, 0);
-  for (int64_t k = 0; k < ni; ++k) ++start[item_max - t->items[k].z + 1];
-  for (int b = 1; b <= item_max + 1; ++b) start[b] += start[b - 1];
-  t->item_order.resize(ni);
-  for (int64_t k = 0; k < ni; ++k) t->item_order[start[item_max - t->items[k].z]++] = static_cast<int32_t>(k);
-  t->ordered = true;
-}
-
-// Concatenate the systems' trees into the device-array images.
-// particles_done: a one-system build already wrote perm, perm32 and parts.
-int assemble(octgrav_tree* t, std::vector<SysTree>& sys, bool particles_done = false) {
-  const int ns = static_cast<int>(sys.size());
-  t->cell_off.assign(ns + 1, 0);
-  for (int s = 0; s < ns; ++s) t->cell_off[s + 1] = t->cell_off[s] + static_cast<int64_t>(sys[s].key.size());
-  const int64_t nc = t->cell_off[ns];
-  if (nc >= (1ll << 28)) return fail(OCTGRAV_ERR_ARG, "too many cells (%lld)", (long long)nc);
-  t->n_cells = nc;
-  // one system: its FP64 cell arrays are moved, not copied, after the loop below
-  const bool single = ns == 1;
-  if (!particles_done) {
-    t->perm.resize(t->n);
-    t->perm32.resize(t->n);
-    t->parts.resize(2 * t->n);
-  }
-  t->geo.resize(nc);
-  t->link.resize(nc);
-  t->mp.resize(4 * nc);
-  t->cfirst.resize(nc);
-  if (!single) {
-    t->key.resize(nc);
-    t->bmin.resize(3 * nc);
-    t->bmax.resize(3 * nc);
-    t->cube.resize(4 * nc);
-    t->M.resize(nc);
-    t->com.resize(3 * nc);
-    t->S.resize(6 * nc);
-    t->pcount.resize(nc);
-  }
-  t->group_cell.clear();
-  t->group_sys.clear();
-  t->n_leaves = 0;
-  t->max_group = 0;
-  t->depth_reached = 0;
-  for (int s = 0; s < ns; ++s) {
-    SysTree& T = sys[s];
-    const int64_t p0 = t->sys_off[s], c0 = t->cell_off[s];
-    const int64_t n = T.n, ncs = static_cast<int64_t>(T.key.size());
-    if (!particles_done)
-      parallel_for(n, 16384, [&](int64_t a, int64_t b) {
-        for (int64_t k = a; k < b; ++k) {
-          t->perm[p0 + k] = p0 + T.perm[k];
-          t->perm32[p0 + k] = static_cast<int32_t>(p0 + T.perm[k]);
-          particle_records(&T.x[3 * k], T.m[k], &t->parts[2 * (p0 + k)]);
-        }
-      });
-    parallel_for(ncs, 8192, [&](int64_t a, int64_t b) {
-      for (int64_t c = a; c < b; ++c) {
-        const int64_t g = c0 + c;
-        if (!single) t->key[g] = T.key[c];
-        const double* cu = &T.cube[4 * c];
-        t->geo[g] = make_float4(static_cast<float>(cu[0]), static_cast<float>(cu[1]),
-                                static_cast<float>(cu[2]), static_cast<float>(cu[3]));
-        if (T.n_child[c] > 0)
-          t->link[g] = make_int2(static_cast<int>(c0 + T.first_child[c]), T.n_child[c]);
-        else
-          t->link[g] = make_int2(static_cast<int>(p0 + T.pfirst[c]), -static_cast<int>(T.pcount[c]));
-        const double* cm = &T.com[3 * c];
-        const double* s6 = &T.S[6 * c];
-        float chi[3], clo[3];
-        for (int d = 0; d < 3; ++d) {
-          chi[d] = static_cast<float>(cm[d]);
-          clo[d] = static_cast<float>(cm[d] - static_cast<double>(chi[d]));
-        }
-        const double tr = s6[0] + s6[1] + s6[2];
-        t->mp[4 * g] = make_float4(chi[0], chi[1], chi[2], static_cast<float>(T.M[c]));
-        t->mp[4 * g + 1] = make_float4(clo[0], clo[1], clo[2], static_cast<float>(T.pcount[c]));
-        t->mp[4 * g + 2] = make_float4(static_cast<float>(3.0 * s6[0]), static_cast<float>(3.0 * s6[1]),
-                                       static_cast<float>(3.0 * s6[2]), static_cast<float>(3.0 * s6[3]));
-        t->mp[4 * g + 3] = make_float4(static_cast<float>(3.0 * s6[4]), static_cast<float>(3.0 * s6[5]),
-                                       static_cast<float>(1.5 * tr), static_cast<float>(0.5 * tr));
-        if (!single) {
-          for (int d = 0; d < 3; ++d) {
-            t->bmin[3 * g + d] = T.bmin[3 * c + d];
-            t->bmax[3 * g + d] = T.bmax[3 * c + d];
-            t->com[3 * g + d] = cm[d];
-          }
-          for (int d = 0; d < 4; ++d) t->cube[4 * g + d] = cu[d];
-          for (int d = 0; d < 6; ++d) t->S[6 * g + d] = s6[d];
-          t->M[g] = T.M[c];
-          t->pcount[g] = T.pcount[c];
-        }
-        t->cfirst[g] = static_cast<int32_t>(p0 + T.pfirst[c]);
-      }
-    });
-    if (single) {  // the global arrays are this system's
-      t->key = std::move(T.key);
-      t->bmin = std::move(T.bmin);
-      t->bmax = std::move(T.bmax);
-      t->cube = std::move(T.cube);
-      t->M = std::move(T.M);
-      t->com = std::move(T.com);
-      t->S = std::move(T.S);
-      t->pcount = std::move(T.pcount);
-    }
-    for (int32_t gc : T.groups) {
-      t->group_cell.push_back(static_cast<int32_t>(c0 + gc));
-      t->group_sys.push_back(s);
-    }
-    t->n_leaves += T.n_leaves;
-    t->max_group = std::max(t->max_group, T.max_group);
-    t->depth_reached = std::max(t->depth_reached, T.depth_reached);
-  }
-  make_items(t);
-  return OCTGRAV_OK;
-}
-
-int check_inputs(const double* pos, const double* mass, int64_t n) {
-  std::atomic<int> bad{0};
-  parallel_for(n, 65536, [&](int64_t a, int64_t b) {
-    for (int64_t i = a; i < b; ++i) {
-      if (!std::isfinite(pos[3 * i]) || !std::isfinite(pos[3 * i + 1]) || !std::isfinite(pos[3 * i + 2]) ||
-          !std::isfinite(mass[i]) || mass[i] < 0) {
-        bad.store(1);
-        return;
-      }
-    }
-  });
-  return bad.load() ? fail(OCTGRAV_ERR_NONFINITE, "non-finite position/mass or negative mass") : OCTGRAV_OK;
-}
+namespace ogh {
 
 // Host memory reused by a thread's one-shot calls: the per-system build
 // arrays and the tree's host images keep their pages from call to call (at
@@ -1579,7 +631,9 @@ int host_images(octgrav_tree* t) {
   return OCTGRAV_OK;
 }
 
-}  // namespace
+}  // namespace ogh
+
+using namespace ogh;
 
 // ---------------------------------------------------------------- C ABI
 
@@ -2214,301 +1268,6 @@ int octgrav_autotune(int n_sys, const int64_t* offsets, const double* pos, const
   if (best_ms) *best_ms = bms;
   std::lock_guard<std::mutex> g(mu);
   cache.push_back({key, {static_cast<double>(bng), static_cast<double>(bppl), bms}});
-  return OCTGRAV_OK;
-}
-
-// ---- learned opening criterion
-
-static uint16_t to_bf16(float f) {  // round to nearest even
-  uint32_t u;
-  std::memcpy(&u, &f, 4);
-  if ((u & 0x7f800000u) == 0x7f800000u) return static_cast<uint16_t>(u >> 16);
-  u += 0x7fffu + ((u >> 16) & 1u);
-  return static_cast<uint16_t>(u >> 16);
-}
-static uint32_t pack2(float lo, float hi) { return to_bf16(lo) | (static_cast<uint32_t>(to_bf16(hi)) << 16); }
-
-int octgrav_set_criterion(octgrav_tree* t, const float* record, double tau, double theta_lo, double theta_hi,
-                          double theta_fb) {
-  if (!t) return fail(OCTGRAV_ERR_ARG, "tree is NULL");
-  if (!record) {
-    t->learned = false;
-    return OCTGRAV_OK;
-  }
-  if (!(theta_lo >= 0 && theta_hi >= theta_lo && theta_fb >= 0) || !std::isfinite(tau) || !std::isfinite(theta_hi))
-    return fail(OCTGRAV_ERR_ARG, "need 0 <= theta_lo <= theta_hi, theta_fb >= 0 and a finite tau");
-  const float* mu = record;
-  const float* sg = record + 12;
-  const float* xmin = record + 24;
-  const float* xmax = record + 36;
-  const float* w = record + 48;
-  const float* W1 = w;
-  const float* b1 = W1 + og::MLP_NH * og::MLP_NF;
-  const float* W2 = b1 + og::MLP_NH;
-  const float* b2 = W2 + og::MLP_NH * og::MLP_NH;
-  const float* w3 = b2 + og::MLP_NH;
-  og::MlpDevice D;
-  std::memset(&D, 0, sizeof D);
-  auto w1 = [&](int u, int k) { return k < og::MLP_NF ? W1[u * og::MLP_NF + k] : 0.f; };
-  for (int j = 0; j < 8; ++j)
-    for (int L = 0; L < 32; ++L) {  // B fragment of W1^T: rows k = 2(L%4)+{0,1}, +8; column u = 8j + L/4
-      const int u = 8 * j + L / 4, k = 2 * (L % 4);
-      D.w1f[j][L] = make_uint2(pack2(w1(u, k), w1(u, k + 1)), pack2(w1(u, k + 8), w1(u, k + 9)));
-    }
-  for (int kk = 0; kk < 4; ++kk)
-    for (int j = 0; j < 8; ++j)
-      for (int L = 0; L < 32; ++L) {
-        const int u = 8 * j + L / 4, k = 16 * kk + 2 * (L % 4);
-        const float* r = W2 + u * og::MLP_NH;
-        D.w2f[kk][j][L] = make_uint2(pack2(r[k], r[k + 1]), pack2(r[k + 8], r[k + 9]));
-      }
-  for (int j = 0; j < og::MLP_NH; ++j) {
-    D.b1[j] = b1[j];
-    D.b2[j] = b2[j];
-    D.w3[j] = w3[j];
-  }
-  for (int i = 0; i < 16; ++i) {
-    const bool v = i < og::MLP_NF;
-    D.mu[i] = v ? mu[i] : 0.f;
-    D.isig[i] = v ? 1.f / sg[i] : 0.f;
-    D.xmin[i] = v ? xmin[i] : 0.f;
-    D.xmax[i] = v ? xmax[i] : 0.f;
-  }
-  D.b3 = w3[og::MLP_NH];
-  D.tau = static_cast<float>(tau);
-  int rc = t->dev->mlp.reserve(sizeof D);
-  if (rc) return rc;
-  CUDA_TRY(cudaMemcpy(t->dev->mlp.p, &D, sizeof D, cudaMemcpyHostToDevice));
-  t->learned = true;
-  t->theta_lo = static_cast<float>(theta_lo);
-  t->theta_hi = static_cast<float>(theta_hi);
-  t->theta_fb = static_cast<float>(theta_fb);
-  return OCTGRAV_OK;
-}
-
-// Host copy of the walk's FP32 opening test (same operations, no contraction).
-static bool open_f32_host(const float4& g, const float4& b0, const float4& b1, float theta2, float* d2out) {
-  const float h = g.w;
-  const float gmin[3] = {b0.x, b0.y, b0.z}, gmax[3] = {b1.x, b1.y, b1.z}, c[3] = {g.x, g.y, g.z};
-  float d[3];
-  for (int k = 0; k < 3; ++k) {
-    const float below = gmin[k] - (c[k] + h), above = (c[k] - h) - gmax[k];
-    const float tt = below > above ? below : above;
-    d[k] = tt > 0.f ? tt : 0.f;
-  }
-  const float d2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
-  if (d2out) *d2out = d2;
-  return 4.0f * (h * h) >= theta2 * d2;
-}
-
-int octgrav_mlp_samples(octgrav_tree* t, const int64_t* groups, int64_t n_groups, double theta_walk, double eps,
-                        float* features, float* labels, int64_t* pairs, int64_t cap, int64_t* n_out, void* stream) {
-  if (!t || !groups || n_groups < 0 || !n_out) return fail(OCTGRAV_ERR_ARG, "bad argument");
-  int rc = check_params(eps, theta_walk, 1.0);
-  if (rc) return rc;
-  if ((rc = host_images(t))) return rc;
-  const int64_t ngr = static_cast<int64_t>(t->group_cell.size());
-  const float th2 = static_cast<float>(theta_walk * theta_walk);
-  std::vector<int32_t> s_item, s_cell;
-  std::vector<int64_t> s_group;
-  int max_count = 1;
-  for (int64_t q = 0; q < n_groups; ++q) {
-    const int64_t g = groups[q];
-    if (g < 0 || g >= ngr) return fail(OCTGRAV_ERR_ARG, "group index %lld out of range", (long long)g);
-    const int item = t->group_item[g];
-    const int4 it = t->items[item];
-    const float4 b0 = t->ibox[4 * item], b1 = t->ibox[4 * item + 1];
-    max_count = std::max<int>(max_count, static_cast<int>(t->pcount[t->group_cell[g]]));
-    std::vector<int32_t> stack;
-    if (t->link[it.x].y > 0) stack.push_back(it.x);
-    while (!stack.empty()) {
-      const int node = stack.back();
-      stack.pop_back();
-      const int2 lk = t->link[node];
-      for (int c = lk.x; c < lk.x + lk.y; ++c) {
-        float d2 = 0.f;
-        const bool op = open_f32_host(t->geo[c], b0, b1, th2, &d2);
-        if (t->geo[c].w > 0.f && d2 > 0.f) {
-          s_item.push_back(item);
-          s_cell.push_back(c);
-          s_group.push_back(g);
-        }
-        if (op && t->link[c].y > 0) stack.push_back(c);
-      }
-    }
-  }
-  const int64_t ns = static_cast<int64_t>(s_item.size());
-  *n_out = ns;
-  if (!features || !labels || cap <= 0 || ns == 0) return OCTGRAV_OK;
-  const int64_t nw = std::min(ns, cap);
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (!t->uploaded || t->sysp_dirty) {
-    if ((rc = upload(t, st))) return rc;
-  }
-  // reference accelerations: the same walk at theta = 0.3 with the plain test
-  const bool learned = t->learned;
-  t->learned = false;
-  if ((rc = t->dev->out.reserve(sizeof(float4) * t->n))) { t->learned = learned; return rc; }
-  rc = launch(t, eps, 0.3, 1.0, static_cast<float4*>(t->dev->out.p), st, false, nullptr, nullptr, nullptr, 0);
-  t->learned = learned;
-  if (rc) return rc;
-  if ((rc = read_status(t, st))) return rc;
-  // per-cell (first, count) and FP64 moments
-  const int64_t nc = t->n_cells;
-  std::vector<int2> fc(nc);
-  for (int64_t c = 0; c < nc; ++c) fc[c] = make_int2(t->cfirst[c], static_cast<int>(t->pcount[c]));
-  DevBuf b_item, b_cell, b_fc, b_com, b_M, b_S, b_feat, b_lab;
-  if ((rc = b_item.reserve(4 * nw)) || (rc = b_cell.reserve(4 * nw)) || (rc = b_fc.reserve(8 * nc)) ||
-      (rc = b_com.reserve(24 * nc)) || (rc = b_M.reserve(8 * nc)) || (rc = b_S.reserve(48 * nc)) ||
-      (rc = b_feat.reserve(4 * og::MLP_NF * nw)) || (rc = b_lab.reserve(8 * nw)))
-    return rc;
-  CUDA_TRY(cudaMemcpyAsync(b_item.p, s_item.data(), 4 * nw, cudaMemcpyHostToDevice, st));
-  CUDA_TRY(cudaMemcpyAsync(b_cell.p, s_cell.data(), 4 * nw, cudaMemcpyHostToDevice, st));
-  CUDA_TRY(cudaMemcpyAsync(b_fc.p, fc.data(), 8 * nc, cudaMemcpyHostToDevice, st));
-  CUDA_TRY(cudaMemcpyAsync(b_com.p, t->com.data(), 24 * nc, cudaMemcpyHostToDevice, st));
-  CUDA_TRY(cudaMemcpyAsync(b_M.p, t->M.data(), 8 * nc, cudaMemcpyHostToDevice, st));
-  CUDA_TRY(cudaMemcpyAsync(b_S.p, t->S.data(), 48 * nc, cudaMemcpyHostToDevice, st));
-  CUDA_TRY(cudaMemsetAsync(b_lab.p, 0, 8 * nw, st));
-  og::MlpSampleArgs a{};
-  a.n = static_cast<int>(nw);
-  a.chunks = (max_count + 31) / 32;
-  a.item = static_cast<const int*>(b_item.p);
-  a.cell = static_cast<const int*>(b_cell.p);
-  a.items = static_cast<const int4*>(t->dev->items.p);
-  a.ibox = static_cast<const float4*>(t->dev->ibox.p);
-  a.geo = static_cast<const float4*>(t->dev->geo.p);
-  a.mp = static_cast<const float4*>(t->dev->mp.p);
-  a.parts = static_cast<const float4*>(t->dev->parts.p);
-  a.link_first_count = static_cast<const int2*>(b_fc.p);
-  a.com64 = static_cast<const double*>(b_com.p);
-  a.M64 = static_cast<const double*>(b_M.p);
-  a.S64 = static_cast<const double*>(b_S.p);
-  a.aref = static_cast<const float4*>(t->dev->out.p);
-  a.eps2 = eps * eps;
-  a.n_group = t->n_group;
-  a.feat = static_cast<float*>(b_feat.p);
-  a.label64 = static_cast<double*>(b_lab.p);
-  cudaError_t e = og::mlp_sample_features(a, st);
-  if (e == cudaSuccess) e = og::mlp_sample_labels(a, st);
-  if (e != cudaSuccess) return fail(OCTGRAV_ERR_CUDA, "sample kernels failed: %s", cudaGetErrorString(e));
-  std::vector<double> lab(nw);
-  CUDA_TRY(cudaMemcpyAsync(features, b_feat.p, 4 * og::MLP_NF * nw, cudaMemcpyDeviceToHost, st));
-  CUDA_TRY(cudaMemcpyAsync(lab.data(), b_lab.p, 8 * nw, cudaMemcpyDeviceToHost, st));
-  CUDA_TRY(cudaStreamSynchronize(st));
-  for (int64_t k = 0; k < nw; ++k) {
-    labels[k] = static_cast<float>(lab[k]);
-    if (pairs) {
-      pairs[2 * k] = s_group[k];
-      pairs[2 * k + 1] = s_cell[k];
-    }
-  }
-  return OCTGRAV_OK;
-}
-
-static double splitmix_uniform(uint64_t& s) {
-  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  z ^= z >> 31;
-  return static_cast<double>(z >> 11) * (1.0 / 9007199254740992.0);
-}
-
-int octgrav_mlp_grad(const float* params, const float* x, const float* target, int64_t n, float* grad, float* loss,
-                     void* stream) {
-  if (!params || !x || !target || n < 1 || n > (1 << 30) || !grad) return fail(OCTGRAV_ERR_ARG, "bad argument");
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  DevBuf bw, bx, bt, bg, bl;
-  int rc;
-  if ((rc = bw.reserve(4 * og::MLP_NPARAM)) || (rc = bx.reserve(4 * og::MLP_NF * n)) || (rc = bt.reserve(4 * n)) ||
-      (rc = bg.reserve(4 * og::MLP_NPARAM)) || (rc = bl.reserve(4)))
-    return rc;
-  CUDA_TRY(cudaMemcpyAsync(bw.p, params, 4 * og::MLP_NPARAM, cudaMemcpyHostToDevice, st));
-  CUDA_TRY(cudaMemcpyAsync(bx.p, x, 4 * og::MLP_NF * n, cudaMemcpyHostToDevice, st));
-  CUDA_TRY(cudaMemcpyAsync(bt.p, target, 4 * n, cudaMemcpyHostToDevice, st));
-  CUDA_TRY(cudaMemsetAsync(bg.p, 0, 4 * og::MLP_NPARAM, st));
-  CUDA_TRY(cudaMemsetAsync(bl.p, 0, 4, st));
-  cudaError_t e = og::mlp_grad(static_cast<float*>(bw.p), static_cast<float*>(bx.p), static_cast<float*>(bt.p),
-                               static_cast<int>(n), static_cast<int>(n), 0, 0, true, static_cast<float*>(bg.p),
-                               static_cast<float*>(bl.p), st);
-  if (e != cudaSuccess) return fail(OCTGRAV_ERR_CUDA, "gradient kernel failed: %s", cudaGetErrorString(e));
-  CUDA_TRY(cudaMemcpyAsync(grad, bg.p, 4 * og::MLP_NPARAM, cudaMemcpyDeviceToHost, st));
-  float l = 0;
-  CUDA_TRY(cudaMemcpyAsync(&l, bl.p, 4, cudaMemcpyDeviceToHost, st));
-  CUDA_TRY(cudaStreamSynchronize(st));
-  if (loss) *loss = l;
-  return OCTGRAV_OK;
-}
-
-int octgrav_mlp_train(const float* features, const float* labels, int64_t n, int steps, int batch, double lr,
-                      uint64_t seed, float* record, float* final_loss, void* stream) {
-  if (!features || !labels || !record || n < 2 || n > (1 << 30) || steps < 1 || batch < 1 || !(lr > 0))
-    return fail(OCTGRAV_ERR_ARG, "bad argument");
-  const int F = og::MLP_NF;
-  // targets: log10 of the error label; inputs standardised per feature
-  std::vector<float> y(n), X(static_cast<size_t>(n) * F);
-  double mu[og::MLP_NF] = {0}, sd[og::MLP_NF] = {0};
-  for (int64_t k = 0; k < n; ++k)
-    for (int i = 0; i < F; ++i) mu[i] += features[k * F + i];
-  for (int i = 0; i < F; ++i) mu[i] /= static_cast<double>(n);
-  for (int64_t k = 0; k < n; ++k)
-    for (int i = 0; i < F; ++i) sd[i] += (features[k * F + i] - mu[i]) * (features[k * F + i] - mu[i]);
-  for (int i = 0; i < F; ++i) sd[i] = std::max(std::sqrt(sd[i] / static_cast<double>(n)), 1e-6);
-  float xmin[og::MLP_NF], xmax[og::MLP_NF];
-  for (int i = 0; i < F; ++i) { xmin[i] = INFINITY; xmax[i] = -INFINITY; }
-  for (int64_t k = 0; k < n; ++k) {
-    y[k] = static_cast<float>(std::log10(std::max(static_cast<double>(labels[k]), 1e-12)));
-    for (int i = 0; i < F; ++i) {
-      const float v = static_cast<float>((features[k * F + i] - mu[i]) / sd[i]);
-      X[k * F + i] = v;
-      xmin[i] = std::min(xmin[i], v);
-      xmax[i] = std::max(xmax[i], v);
-    }
-  }
-  // He-uniform initialisation from a counter-based generator
-  std::vector<float> w(og::MLP_NPARAM, 0.f);
-  uint64_t rs = seed;
-  const int NH = og::MLP_NH;
-  for (int k = 0; k < NH * F; ++k) w[k] = static_cast<float>((2 * splitmix_uniform(rs) - 1) * std::sqrt(6.0 / F));
-  float* W2 = w.data() + NH * F + NH;
-  for (int k = 0; k < NH * NH; ++k) W2[k] = static_cast<float>((2 * splitmix_uniform(rs) - 1) * std::sqrt(6.0 / NH));
-  float* w3 = W2 + NH * NH + NH;
-  for (int k = 0; k < NH; ++k) w3[k] = static_cast<float>((2 * splitmix_uniform(rs) - 1) * std::sqrt(3.0 / NH));
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  DevBuf bx, by, bw, bm, bv, bg, bl;
-  int rc;
-  if ((rc = bx.reserve(4 * X.size())) || (rc = by.reserve(4 * n)) || (rc = bw.reserve(4 * og::MLP_NPARAM)) ||
-      (rc = bm.reserve(4 * og::MLP_NPARAM)) || (rc = bv.reserve(4 * og::MLP_NPARAM)) ||
-      (rc = bg.reserve(4 * og::MLP_NPARAM)) || (rc = bl.reserve(4)))
-    return rc;
-  CUDA_TRY(cudaMemcpyAsync(bx.p, X.data(), 4 * X.size(), cudaMemcpyHostToDevice, st));
-  CUDA_TRY(cudaMemcpyAsync(by.p, y.data(), 4 * n, cudaMemcpyHostToDevice, st));
-  CUDA_TRY(cudaMemcpyAsync(bw.p, w.data(), 4 * og::MLP_NPARAM, cudaMemcpyHostToDevice, st));
-  CUDA_TRY(cudaMemsetAsync(bm.p, 0, 4 * og::MLP_NPARAM, st));
-  CUDA_TRY(cudaMemsetAsync(bv.p, 0, 4 * og::MLP_NPARAM, st));
-  const int B = static_cast<int>(std::min<int64_t>(batch, n));
-  for (int k = 1; k <= steps; ++k) {
-    CUDA_TRY(cudaMemsetAsync(bg.p, 0, 4 * og::MLP_NPARAM, st));
-    CUDA_TRY(cudaMemsetAsync(bl.p, 0, 4, st));
-    cudaError_t e = og::mlp_grad(static_cast<float*>(bw.p), static_cast<float*>(bx.p), static_cast<float*>(by.p),
-                                 static_cast<int>(n), B, k, seed, false, static_cast<float*>(bg.p),
-                                 static_cast<float*>(bl.p), st);
-    if (e == cudaSuccess)
-      e = og::mlp_adam(static_cast<float*>(bw.p), static_cast<float*>(bm.p), static_cast<float*>(bv.p),
-                       static_cast<float*>(bg.p), static_cast<float>(lr), k, st);
-    if (e != cudaSuccess) return fail(OCTGRAV_ERR_CUDA, "training kernels failed: %s", cudaGetErrorString(e));
-  }
-  float l = 0;
-  CUDA_TRY(cudaMemcpyAsync(w.data(), bw.p, 4 * og::MLP_NPARAM, cudaMemcpyDeviceToHost, st));
-  CUDA_TRY(cudaMemcpyAsync(&l, bl.p, 4, cudaMemcpyDeviceToHost, st));
-  CUDA_TRY(cudaStreamSynchronize(st));
-  for (int i = 0; i < F; ++i) {
-    record[i] = static_cast<float>(mu[i]);
-    record[12 + i] = static_cast<float>(sd[i]);
-    record[24 + i] = xmin[i];
-    record[36 + i] = xmax[i];
-  }
-  std::memcpy(record + 48, w.data(), 4 * og::MLP_NPARAM);
-  if (final_loss) *final_loss = l;
   return OCTGRAV_OK;
 }
 
