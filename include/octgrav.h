@@ -28,7 +28,12 @@
  *    library (cudaMalloc) on the current CUDA device and freed by
  *    octgrav_free_tree.
  *  - Thread safety: distinct trees may be used from distinct threads; one tree
- *    must not be used by two threads at once.
+ *    must not be used by two threads at once. The one-shot calls keep their
+ *    buffers per calling thread and may run concurrently.
+ *  - Environment (read once): OCTGRAV_THREADS = host build threads (default:
+ *    all hardware threads); OCTGRAV_HOST_PULL=0 makes the one-shot host-build
+ *    call upload with cudaMemcpyAsync only (no copy kernel reading pageable
+ *    memory); OCTGRAV_GPU_CELL_CAP = initial cell capacity of a GPU build.
  */
 #ifndef OCTGRAV_H
 #define OCTGRAV_H

@@ -124,6 +124,7 @@ int enqueue_h2d(Device& D, DevBuf& b, const void* src, size_t bytes, cudaStream_
   if (D.pageable < 0) {
     int v = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&v, cudaDevAttrPageableMemoryAccess, D.device));
+    if (const char* e = getenv("OCTGRAV_HOST_PULL")) v = v && atoi(e) != 0;  // 0: always cudaMemcpyAsync
     D.pageable = v ? 1 : 0;
   }
   const bool aligned = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(b.p) | bytes) & 15u) == 0;

@@ -222,6 +222,24 @@ def test_one_shot_calls_from_threads(torch):
     assert torch.cuda.mem_get_info()[0] >= free0 - (64 << 20)
 
 
+def test_one_shot_copy_fallback_equals_pull(torch, monkeypatch):
+    """With OCTGRAV_HOST_PULL=0 the one-shot call uploads with cudaMemcpyAsync
+    instead of pulling pageable memory by kernel: the same results. (The
+    setting is read when a thread's device buffers are first used, so the call
+    runs on a new thread.)"""
+    import threading
+
+    pos, m = W.plummer(30001, seed=42)
+    ra, rp = G.forces(pos, m, 0.01, 0.5, 16, 64)
+    monkeypatch.setenv("OCTGRAV_HOST_PULL", "0")
+    out = {}
+    t = threading.Thread(target=lambda: out.update(r=G.forces(pos, m, 0.01, 0.5, 16, 64)))
+    t.start()
+    t.join()
+    a, p = out["r"]
+    assert np.array_equal(_bits(a), _bits(ra)) and np.array_equal(_bits(p), _bits(rp))
+
+
 def test_device64_outputs_in_input_order(torch):
     pos, m = W.plummer(30000, seed=15)
     for T in (G.Tree.build(pos, m, 16, 64), G.Tree.build_gpu(pos, m, 16, 64)):
