@@ -30,8 +30,8 @@
  *  - Thread safety: distinct trees may be used from distinct threads; one tree
  *    must not be used by two threads at once. The one-shot calls keep their
  *    buffers per calling thread and may run concurrently.
- *  - Environment (read once): OCTGRAV_THREADS = host build threads (default:
- *    all hardware threads); OCTGRAV_HOST_PULL=0 makes the one-shot host-build
+ *  - Environment (read at first use): OCTGRAV_THREADS = host build threads (default:
+ *    all hardware threads); OCTGRAV_HOST_PULL=0 makes a thread's one-shot host-build
  *    call upload with cudaMemcpyAsync only (no copy kernel reading pageable
  *    memory); OCTGRAV_GPU_CELL_CAP = initial cell capacity of a GPU build.
  */
