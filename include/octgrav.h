@@ -377,6 +377,17 @@ int octgrav_set_criterion(octgrav_tree *t, const float *record, double tau, doub
  * All modes compute identical results. Errors: ERR_ARG. */
 int octgrav_set_staging(octgrav_tree *t, int mode);
 
+/* Failure injection for tests (nothing faults or hangs): later launches of t
+ * give each walk only stack_cap node-stack entries (0 = the whole stack), so
+ * that a deep walk reports OCTGRAV_ERR_STACK; and, in staging mode 2, never
+ * request the first tile of cell records of work item drop_item (-1 = none),
+ * so that its bounded wait (~1 s) runs out and the launch reports
+ * OCTGRAV_ERR_TIMEOUT; the warp then waits for its other copies and stops.
+ * The context stays usable; octgrav_set_fault(t, 0, -1) restores normal
+ * launches. A graph captured before the call keeps the old settings.
+ * Errors: ERR_ARG (stack_cap < 0, drop_item outside [-1, n_items)). */
+int octgrav_set_fault(octgrav_tree *t, int stack_cap, int64_t drop_item);
+
 void octgrav_free_tree(octgrav_tree *t);
 
 #define OCTGRAV_NOALLOC_MAX_ITEMS 262144 /* work items accepted by octgrav_forces_noalloc */

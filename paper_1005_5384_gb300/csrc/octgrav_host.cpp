@@ -266,6 +266,8 @@ og::KParams make_params(octgrav_tree* t, float4* out) {
   p.stage = t->stage;
   p.mp_map = t->mp_map;
   p.n_group = t->n_group;
+  p.stack_cap = t->fault_stack_cap;
+  p.drop_item = t->fault_drop_item;
   if (t->learned) {
     p.mlp = static_cast<const og::MlpDevice*>(D.mlp.p);
     p.theta_lo2 = static_cast<float>(static_cast<double>(t->theta_lo) * t->theta_lo);
@@ -1269,6 +1271,15 @@ int octgrav_autotune(int n_sys, const int64_t* offsets, const double* pos, const
   if (best_ms) *best_ms = bms;
   std::lock_guard<std::mutex> g(mu);
   cache.push_back({key, {static_cast<double>(bng), static_cast<double>(bppl), bms}});
+  return OCTGRAV_OK;
+}
+
+int octgrav_set_fault(octgrav_tree* t, int stack_cap, int64_t drop_item) {
+  if (!t) return fail(OCTGRAV_ERR_ARG, "tree is NULL");
+  if (stack_cap < 0 || drop_item < -1 || drop_item >= t->n_items)
+    return fail(OCTGRAV_ERR_ARG, "stack_cap must be >= 0 and drop_item in [-1, n_items)");
+  t->fault_stack_cap = stack_cap;
+  t->fault_drop_item = static_cast<int>(drop_item + 1);
   return OCTGRAV_OK;
 }
 

@@ -319,6 +319,7 @@ struct octgrav_tree {
   int64_t n = 0;
   int n_leaf = 0, n_group = 0, n_sys = 0;
   int ppl = 2, ctas_per_sm = 0;
+  int fault_stack_cap = 0, fault_drop_item = 0;  // failure injection (octgrav_set_fault; 0 = off)
   int stage = og::STAGING_ASYNC;
   bool learned = false;             // learned opening criterion active
   float theta_lo = 0, theta_hi = 0, theta_fb = 0;

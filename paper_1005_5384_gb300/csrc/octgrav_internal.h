@@ -58,6 +58,14 @@ struct KParams {
   const struct MlpDevice* mlp;
   float theta_lo2, theta_hi2, theta_fb2;  // fl32(theta^2) of the band and the fallback
   int n_group;
+  // failure injection (tests; nothing faults; zero = off): stack_cap =
+  // node-stack entries a walk may use (0: all; launches clamp it to the
+  // stack's size), so that a walk overflows and reports ST_STACK; drop_item =
+  // 1 + the index of a work item whose first tile of cell records is never
+  // requested in gather4 staging, so that the bounded wait for it runs out and
+  // reports ST_TIMEOUT
+  int stack_cap;
+  int drop_item;
   // capture mode (tests): per item up to dbg_cap cell indices
   int* dbg_cell;
   int* dbg_leaf;

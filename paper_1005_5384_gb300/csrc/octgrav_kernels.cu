@@ -648,6 +648,8 @@ __global__ void __launch_bounds__(CtaWarps<MLP>::v * 32, MLP ? 1 : 2) walk_eval_
     // ---- walk (Listing 1): root opened; children of up to 4 nodes per step
     int top = 0, nlq = 0, n_pc = 0, n_leafent = 0;
     bool ok = true;
+    // failure injection: the first tile of this item is never requested
+    const uint32_t drop_end = (STAGE == STAGE_GATHER4 && item + 1 == p.drop_item) ? app + TILE : 0u;
     {
       const int2 rl = __ldg(p.link + it.x);
       if (rl.y < 0) {  // the root is a leaf: it is the group itself (own pass above)
@@ -770,7 +772,7 @@ __global__ void __launch_bounds__(CtaWarps<MLP>::v * 32, MLP ? 1 : 2) walk_eval_
       const unsigned m_lq = __ballot_sync(FULL, open && leaf && !own_leaf);
       const unsigned m_node = __ballot_sync(FULL, open && !leaf);
       const int nn = __popc(m_node);
-      if (top + nn > STK) {
+      if (top + nn > p.stack_cap) {
         status |= ST_STACK;
         break;
       }
@@ -813,6 +815,7 @@ __global__ void __launch_bounds__(CtaWarps<MLP>::v * 32, MLP ? 1 : 2) walk_eval_
         const uint32_t upto = app & ~3u;
         if (lane == 0) {
           for (uint32_t k = iss; k < upto; k += 4) {
+            if (k < drop_end) continue;  // failure injection: this tile never arrives
             const uint32_t sk = k % (NTILE * TILE);
             const uint32_t bar = bar0 + 8 * (sk / TILE);
             const int4 r4 = *reinterpret_cast<const int4*>(&S.cidx[sk]);
@@ -840,7 +843,7 @@ __global__ void __launch_bounds__(CtaWarps<MLP>::v * 32, MLP ? 1 : 2) walk_eval_
         if (rem) app += TILE - rem;
       } else if (rem) {
         __syncwarp();
-        if (lane == 0) {
+        if (lane == 0 && app >= drop_end) {
           const uint32_t bar = bar0 + 8 * ((app / TILE) % NTILE);
           if (STAGE == STAGE_GATHER4 && iss < app) {
             // last partial group of 4: pad with the first index; the padded
@@ -959,7 +962,10 @@ cudaError_t launch_t(const KParams& p, int ctas_per_sm, cudaStream_t stream, Lau
     info->smem = smem;
   }
   if (dry) return cudaSuccess;
-  kern<<<grid, NW * 32, smem, stream>>>(p);
+  KParams q = p;
+  constexpr int STK = MLP ? STACK_MLP : STACK;
+  q.stack_cap = (p.stack_cap > 0 && p.stack_cap < STK) ? p.stack_cap : STK;
+  kern<<<grid, NW * 32, smem, stream>>>(q);
   return cudaGetLastError();
 }
 

@@ -71,6 +71,7 @@ _SIGS = {
     "octgrav_set_launch": (C.c_int, [_vp, C.c_int, C.c_int]),
     "octgrav_balance": (C.c_int, [_vp, C.c_int, _vp]),
     "octgrav_set_staging": (C.c_int, [_vp, C.c_int]),
+    "octgrav_set_fault": (C.c_int, [_vp, C.c_int, C.c_int64]),
     "octgrav_mlp_samples": (C.c_int, [_vp, _i64, C.c_int64, C.c_double, C.c_double, _vp, _vp, _vp, C.c_int64,
                                       C.POINTER(C.c_int64), _vp]),
     "octgrav_mlp_train": (C.c_int, [_vp, _vp, C.c_int64, C.c_int, C.c_int, C.c_double, C.c_uint64, _vp, _vp,
@@ -275,6 +276,11 @@ class Tree:
     def set_staging(self, mode: int):
         """0 = cp.async.bulk per record, 1 = 16-byte cp.async (default), 2 = TMA gather4."""
         _check(load().octgrav_set_staging(self._h, int(mode)))
+
+    def set_fault(self, stack_cap: int = 0, drop_item: int = -1):
+        """Failure injection for tests: a node stack of stack_cap entries (0 = all),
+        and (staging 2) a work item whose first tile is never requested (-1 = none)."""
+        _check(load().octgrav_set_fault(self._h, int(stack_cap), int(drop_item)))
 
     def set_system_params(self, eps=None, theta=None):
         if eps is None and theta is None:

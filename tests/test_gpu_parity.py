@@ -223,3 +223,44 @@ def test_longest_first_order_changes_nothing_but_the_order(_cuda):
     torch.cuda.synchronize()
     assert T.status() == G.OK
     T.balance(0)
+
+
+def test_forced_stack_overflow_reports_err_stack(_cuda):
+    """Failure injection without a fault: walks given 8 node-stack entries
+    overflow, the launch reports ERR_STACK through the device status word, and
+    the next launch on the same context is exact again."""
+    pos, m = W.plummer(30000, seed=51)
+    T = G.Tree.build(pos, m, 16, 64)
+    ra, rp = T.forces(0.01, 0.5)
+    T.set_fault(stack_cap=8)
+    with pytest.raises(G.OctgravError) as e:
+        T.forces(0.01, 0.5)
+    assert e.value.code == G.ERR_STACK
+    T.set_fault()
+    a, p = T.forces(0.01, 0.5)
+    assert np.array_equal(a, ra) and np.array_equal(p, rp)
+
+
+def test_forced_wait_timeout_reports_err_timeout(_cuda):
+    """Failure injection without a fault or a hang: in gather4 staging the first
+    tile of one work item is never requested, so its bounded mbarrier wait
+    (~1 s) runs out; the warp waits for its other copies and stops, the launch
+    reports ERR_TIMEOUT, and the context stays usable."""
+    import time
+
+    pos, m = W.plummer(30000, seed=52)
+    T = G.Tree.build(pos, m, 16, 64)
+    T.set_staging(2)
+    ra, rp = T.forces(0.01, 0.5)
+    T.set_fault(drop_item=0)
+    t0 = time.perf_counter()
+    with pytest.raises(G.OctgravError) as e:
+        T.forces(0.01, 0.5)
+    assert e.value.code == G.ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 60
+    T.set_fault()
+    a, p = T.forces(0.01, 0.5)
+    assert np.array_equal(a, ra) and np.array_equal(p, rp)
+    with pytest.raises(G.OctgravError) as e:
+        T.set_fault(drop_item=T.stats["n_items"])
+    assert e.value.code == G.ERR_ARG
