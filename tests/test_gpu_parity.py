@@ -264,3 +264,15 @@ def test_forced_wait_timeout_reports_err_timeout(_cuda):
     with pytest.raises(G.OctgravError) as e:
         T.set_fault(drop_item=T.stats["n_items"])
     assert e.value.code == G.ERR_ARG
+
+
+def test_small_capture_buffer_reports_err_list(_cuda):
+    """The list-capture buffer is bounded on the device: a capacity of 4 entries
+    per work item is exceeded and reported as ERR_LIST (the kernel writes only
+    within the buffer); a large enough buffer then captures normally."""
+    pos, m = W.plummer(8192, seed=53)
+    T = G.Tree.build(pos, m, 16, 64)
+    with pytest.raises(G.OctgravError) as e:
+        T.debug_lists(0.5, cap=4)
+    assert e.value.code == G.ERR_LIST
+    assert len(T.debug_lists(0.5, cap=8192)) == T.stats["n_items"]
