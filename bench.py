@@ -696,6 +696,7 @@ def main():
         G.forces(pin_x.numpy(), pin_m.numpy(), a.eps, a.theta, a.n_leaf, a.n_group, stream=stream,
                  out=(pin_a.numpy(), pin_p.numpy()))
         host_t.append(time.perf_counter() - t0)
+    host_phases = G.oneshot_phases() if host_t else None  # the last call's breakdown (ms)
     e2e_s = statistics.mean(e2e_t[1:]) if len(e2e_t) > 1 else float("nan")
     host_s = statistics.mean(host_t[1:]) if len(host_t) > 1 else float("nan")
     s = T.stats
@@ -733,6 +734,7 @@ def main():
             "d2h_bytes_per_step": d2h, "seconds_per_step": host_s,
             "path": "octgrav_forces_ex (the paper's split, Sec. 2: host FP64 tree build, upload, kernel, device "
                     "unpermute, FP64 download)",
+            "phases_ms": host_phases,
             "gpu_build_path": None if e2e_s != e2e_s else {
                 "value": world * a.n / e2e_s, "unit": "forces/s", "h2d_bytes_per_step": h2d_gpu,
                 "d2h_bytes_per_step": d2h_gpu, "seconds_per_step": e2e_s,

@@ -128,6 +128,18 @@ int octgrav_forces(const double *pos, const double *mass, int64_t n, double eps,
 int octgrav_forces_ex(const double *pos, const double *mass, int64_t n, double eps, double theta,
                       double G, int n_leaf, int n_group, double *acc, double *pot, void *stream);
 
+/* Where the calling thread's last successful octgrav_forces_ex call spent its
+ * time, in ms: host build phases 0 bounding box with the input check, 1 Morton
+ * keys, 2 radix sort, 3 gather with the particle records (and the start of
+ * their upload), 4 levels, 5 cell properties, 6 groups, 7 cell records and
+ * work items, 8 the whole host build; device time between CUDA events on the
+ * call's stream: 9 the remaining upload, 10 the walk-and-evaluate launch,
+ * 11 unpermute and the FP64 copies out; 12 the whole call (host clock).
+ * Writes min(n_out, OCTGRAV_ONESHOT_PHASES) values and returns that count.
+ * Errors: ERR_ARG, ERR_STATE (no completed call on this thread). */
+#define OCTGRAV_ONESHOT_PHASES 13
+int octgrav_oneshot_phases(double *ms, int n_out);
+
 /* ---- Tree build on the GPU (Sec. 2.1 run as CUDA kernels).
  *
  * The same tree as octgrav_build_tree / octgrav_build_batch of the same data,

@@ -143,7 +143,7 @@ int enqueue_h2d(Device& D, DevBuf& b, const void* src, size_t bytes, cudaStream_
 // way to the device (on st) while the cells are built. On return with an error
 // nothing is still reading the host arrays.
 int build_oneshot(const double* pos, const double* mass, int64_t n, int n_leaf, int n_group, HostCache& cache,
-                  Device& D, cudaStream_t st, octgrav_tree** out) {
+                  Device& D, cudaStream_t st, octgrav_tree** out, double* phase_ms = nullptr) {
   const int64_t off[2] = {0, n};
   int rc = check_build_args(1, off, pos, mass, n_leaf, n_group, out, false);  // values: in the bbox pass
   if (rc) return rc;
@@ -167,6 +167,7 @@ int build_oneshot(const double* pos, const double* mass, int64_t n, int n_leaf, 
     sink.perm = t->perm.data();
     sink.perm32 = t->perm32.data();
     sink.check_inputs = true;
+    sink.phase_ms = phase_ms;
     sink.ready = [&]() -> int {
       int dev = 0;
       CUDA_TRY(cudaGetDevice(&dev));
@@ -178,7 +179,9 @@ int build_oneshot(const double* pos, const double* mass, int64_t n, int n_leaf, 
       return r;
     };
     rc = build_system(pos, mass, n, n_leaf, n_group, true, cache.sys[0], &sink);
+    const auto ta = std::chrono::steady_clock::now();
     if (!rc) rc = assemble(t.get(), cache.sys, true);
+    if (phase_ms) phase_ms[7] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ta).count();
   } catch (const std::bad_alloc&) {
     rc = fail(OCTGRAV_ERR_OOM, "host allocation failed");
   }
@@ -331,34 +334,42 @@ int device_perm(octgrav_tree* t, cudaStream_t st) {
 }
 
 // Forces into device FP64 arrays in input order (enqueued, not waited for).
-int forces_dev64(octgrav_tree* t, double eps, double theta, double G, double* acc, double* pot, cudaStream_t st) {
+// ev (optional, 3 events): recorded before the upload, before the launch and after it.
+int forces_dev64(octgrav_tree* t, double eps, double theta, double G, double* acc, double* pot, cudaStream_t st,
+                 cudaEvent_t* ev = nullptr) {
   int rc = check_params(eps, theta, G);
   if (rc) return rc;
+  if (ev) CUDA_TRY(cudaEventRecord(ev[0], st));
   if (!t->uploaded || t->sysp_dirty) {
     if ((rc = upload(t, st))) return rc;
   }
   if ((rc = t->dev->out.reserve(sizeof(float4) * t->n))) return rc;
   if ((rc = device_perm(t, st))) return rc;
+  if (ev) CUDA_TRY(cudaEventRecord(ev[1], st));
   if ((rc = launch(t, eps, theta, G, static_cast<float4*>(t->dev->out.p), st, false, nullptr, nullptr, nullptr, 0)))
     return rc;
+  if (ev) CUDA_TRY(cudaEventRecord(ev[2], st));
   cudaError_t e = og::gpu_unpermute(static_cast<const float4*>(t->dev->out.p), static_cast<const int*>(t->dev->perm.p),
                                     t->n, acc, pot, st);
   if (e != cudaSuccess) return fail(OCTGRAV_ERR_CUDA, "unpermute launch failed: %s", cudaGetErrorString(e));
   return OCTGRAV_OK;
 }
 
+// ev (optional, 4 events): those of forces_dev64, then one after the copies out.
 int forces_host(octgrav_tree* t, double eps, double theta, double G, double* acc, double* pot,
-                cudaStream_t st) {
+                cudaStream_t st, cudaEvent_t* ev = nullptr) {
   if (!acc) return fail(OCTGRAV_ERR_ARG, "acc is NULL");
   int rc = check_params(eps, theta, G);
   if (rc) return rc;
   // unpermute on the device, copy FP64 results straight into the caller's arrays
   Device& D = *t->dev;
   if ((rc = D.acc64.reserve(24 * t->n)) || (rc = D.pot64.reserve(8 * t->n))) return rc;
-  if ((rc = forces_dev64(t, eps, theta, G, static_cast<double*>(D.acc64.p), static_cast<double*>(D.pot64.p), st)))
+  if ((rc = forces_dev64(t, eps, theta, G, static_cast<double*>(D.acc64.p), static_cast<double*>(D.pot64.p), st,
+                         ev)))
     return rc;
   CUDA_TRY(cudaMemcpyAsync(acc, D.acc64.p, 24 * t->n, cudaMemcpyDeviceToHost, st));
   if (pot) CUDA_TRY(cudaMemcpyAsync(pot, D.pot64.p, 8 * t->n, cudaMemcpyDeviceToHost, st));
+  if (ev) CUDA_TRY(cudaEventRecord(ev[3], st));
   return read_status(t, st);
 }
 
@@ -366,11 +377,21 @@ int forces_host(octgrav_tree* t, double eps, double theta, double G, double* acc
 // when the thread ends.
 struct ThreadDevice {
   Device* d = nullptr;
+  cudaEvent_t ev[4] = {};  // phase events of the last one-shot host-build call
+  double phase_ms[OCTGRAV_ONESHOT_PHASES] = {};
+  bool timed = false;
   Device& get() {
     if (!d) d = new Device();
     return *d;
   }
+  cudaEvent_t* events() {
+    for (cudaEvent_t& e : ev)
+      if (!e && cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return ev;
+  }
   ~ThreadDevice() {
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
     if (d) d->release();
     delete d;
   }
@@ -702,13 +723,42 @@ int octgrav_forces_ex(const double* pos, const double* mass, int64_t n, double e
   if (n < 1) return fail(OCTGRAV_ERR_ARG, "n must be >= 1");
   thread_local HostCache hcache;
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ThreadDevice& TD = tl_device;
+  double* ph = TD.phase_ms;
+  TD.timed = false;
+  const auto t0 = std::chrono::steady_clock::now();
   octgrav_tree* t = nullptr;
-  if ((rc = build_oneshot(pos, mass, n, n_leaf, n_group, hcache, tl_device.get(), st, &t))) return rc;
-  rc = forces_host(t, eps, theta, G, acc, pot, st);
+  if ((rc = build_oneshot(pos, mass, n, n_leaf, n_group, hcache, TD.get(), st, &t, ph))) return rc;
+  const auto t1 = std::chrono::steady_clock::now();
+  cudaEvent_t* ev = TD.events();
+  rc = forces_host(t, eps, theta, G, acc, pot, st, ev);
   if (rc) cudaStreamSynchronize(st);  // nothing may still read the cached host arrays
   give_back(t, &hcache);
   octgrav_free_tree(t);
+  if (!rc) {
+    const auto t2 = std::chrono::steady_clock::now();
+    ph[8] = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    float e01 = 0.f, e12 = 0.f, e23 = 0.f;
+    if (ev && cudaEventElapsedTime(&e01, ev[0], ev[1]) == cudaSuccess &&
+        cudaEventElapsedTime(&e12, ev[1], ev[2]) == cudaSuccess && cudaEventElapsedTime(&e23, ev[2], ev[3]) == cudaSuccess) {
+      ph[9] = e01;
+      ph[10] = e12;
+      ph[11] = e23;
+    } else {
+      ph[9] = ph[10] = ph[11] = -1.0;
+    }
+    ph[12] = std::chrono::duration<double, std::milli>(t2 - t0).count();
+    TD.timed = true;
+  }
   return rc;
+}
+
+int octgrav_oneshot_phases(double* ms, int n_out) {
+  if (!ms || n_out < 0) return fail(OCTGRAV_ERR_ARG, "NULL output or n_out < 0");
+  if (!tl_device.timed) return fail(OCTGRAV_ERR_STATE, "no completed octgrav_forces_ex call on this thread");
+  const int k = std::min(n_out, static_cast<int>(OCTGRAV_ONESHOT_PHASES));
+  for (int i = 0; i < k; ++i) ms[i] = tl_device.phase_ms[i];
+  return k;
 }
 
 int octgrav_forces(const double* pos, const double* mass, int64_t n, double eps, double theta, int n_leaf,

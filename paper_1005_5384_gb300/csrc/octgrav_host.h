@@ -242,6 +242,7 @@ struct ParticleSink {
   int64_t* perm = nullptr;
   int32_t* perm32 = nullptr;
   std::function<int()> ready;
+  double* phase_ms = nullptr;  // if set: durations of the build's phases 0..6 (octgrav_oneshot_phases)
   bool check_inputs = false;  // the bounding-box pass also checks the inputs (finite, masses >= 0)
 };
 

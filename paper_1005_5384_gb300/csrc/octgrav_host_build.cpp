@@ -112,6 +112,13 @@ int build_system(const double* pos, const double* mass, int64_t n, int n_leaf, i
   T.reset();
   T.n = n;
   const int64_t grain = parallel ? 16384 : (int64_t)1 << 62;
+  auto clock0 = std::chrono::steady_clock::now();
+  auto mark = [&](int k) {  // phase durations for octgrav_oneshot_phases
+    if (!sink || !sink->phase_ms) return;
+    const auto now = std::chrono::steady_clock::now();
+    sink->phase_ms[k] = std::chrono::duration<double, std::milli>(now - clock0).count();
+    clock0 = now;
+  };
   // ---- bounding box and root cube
   double mn[3] = {pos[0], pos[1], pos[2]}, mx[3] = {pos[0], pos[1], pos[2]};
   {
@@ -157,6 +164,7 @@ int build_system(const double* pos, const double* mass, int64_t n, int n_leaf, i
   const double scale = std::ldexp(1.0, kMaxDepth);
   const uint64_t qmax = (1ull << kMaxDepth) - 1;
 
+  mark(0);
   // ---- Morton codes and sort
   hvec<uint64_t>& code = T.code;
   hvec<uint32_t>& idx = T.perm;
@@ -174,7 +182,9 @@ int build_system(const double* pos, const double* mass, int64_t n, int n_leaf, i
       idx[i] = static_cast<uint32_t>(i);
     }
   });
+  mark(1);
   radix_sort(code, idx, T.k2, T.v2, parallel);
+  mark(2);
   T.x.resize(3 * n);
   T.m.resize(n);
   parallel_for(n, grain, [&](int64_t a, int64_t b) {
@@ -203,6 +213,7 @@ int build_system(const double* pos, const double* mass, int64_t n, int n_leaf, i
     if (rc) return rc;
   }
 
+  mark(3);
   // ---- cells, level by level
   auto push_cell = [&](uint64_t key, int depth, int32_t parent, int64_t pf, int64_t pc) {
     T.key.push_back(key);
@@ -300,6 +311,7 @@ int build_system(const double* pos, const double* mass, int64_t n, int n_leaf, i
   const int64_t nc = static_cast<int64_t>(T.key.size());
   T.depth_reached = static_cast<int>(level_begin.size()) - 1;
 
+  mark(4);
   // ---- cell properties, deepest level first
   T.bmin.resize(3 * nc);
   T.bmax.resize(3 * nc);
@@ -385,6 +397,7 @@ int build_system(const double* pos, const double* mass, int64_t n, int n_leaf, i
     });
   }
 
+  mark(5);
   // ---- groups: first cells from the root that are leaves or hold <= n_group.
   // Such eligibility passes from a cell to its children (a child of a leaf does
   // not exist, and a child never holds more particles than its parent), so the
@@ -412,6 +425,7 @@ int build_system(const double* pos, const double* mass, int64_t n, int n_leaf, i
   std::sort(T.groups.begin(), T.groups.end(),
             [&](int32_t a, int32_t b) { return T.pfirst[a] < T.pfirst[b]; });
   for (int32_t g : T.groups) T.max_group = std::max(T.max_group, T.pcount[g]);
+  mark(6);
   return OCTGRAV_OK;
 }
 

@@ -72,6 +72,7 @@ _SIGS = {
     "octgrav_balance": (C.c_int, [_vp, C.c_int, _vp]),
     "octgrav_set_staging": (C.c_int, [_vp, C.c_int]),
     "octgrav_set_fault": (C.c_int, [_vp, C.c_int, C.c_int64]),
+    "octgrav_oneshot_phases": (C.c_int, [_vp, C.c_int]),
     "octgrav_mlp_samples": (C.c_int, [_vp, _i64, C.c_int64, C.c_double, C.c_double, _vp, _vp, _vp, C.c_int64,
                                       C.POINTER(C.c_int64), _vp]),
     "octgrav_mlp_train": (C.c_int, [_vp, _vp, C.c_int64, C.c_int, C.c_int, C.c_double, C.c_uint64, _vp, _vp,
@@ -414,6 +415,20 @@ def forces(pos, mass, eps: float, theta: float, n_leaf: int = 16, n_group: int |
                                  int(n_group if n_group is not None else n_leaf), _p(acc), _p(pot),
                                  _stream_handle(stream)))
     return acc, pot
+
+
+ONESHOT_PHASES = ("bbox_check", "morton", "sort", "gather_records", "levels", "cell_props", "groups",
+                  "records_items", "host_build", "device_upload", "device_walk_eval", "device_unpermute_copy_out",
+                  "call")
+
+
+def oneshot_phases() -> dict:
+    """Where the calling thread's last forces() call spent its time (ms)."""
+    ms = np.zeros(len(ONESHOT_PHASES))
+    k = load().octgrav_oneshot_phases(_p(ms), len(ms))
+    if k < 0:
+        _check(k)
+    return {name: float(ms[i]) for i, name in enumerate(ONESHOT_PHASES[:k])}
 
 
 def forces_gpu(pos, mass, eps: float, theta: float, n_leaf: int = 16, n_group: int | None = None, G: float = 1.0,

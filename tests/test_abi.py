@@ -114,6 +114,12 @@ def test_invalid_arguments_are_rejected_without_a_gpu():
     assert T.status() == G.ERR_STATE          # no launch yet
 
 
+def test_oneshot_phases_need_a_completed_call():
+    with pytest.raises(G.OctgravError) as e:
+        G.oneshot_phases()
+    assert e.value.code == G.ERR_STATE
+
+
 def test_item_split_for_large_groups():
     pos = np.zeros((150, 3))
     pos[:140] = [0.5, 0.5, 0.5]          # 140 coincident particles: one max-depth leaf

@@ -240,6 +240,20 @@ def test_one_shot_copy_fallback_equals_pull(torch, monkeypatch):
     assert np.array_equal(_bits(a), _bits(ra)) and np.array_equal(_bits(p), _bits(rp))
 
 
+def test_oneshot_phases(torch):
+    """The one-shot host-build call reports where its time went: every phase
+    measured, the host phases adding up to the host build, the device phases
+    and the build within the whole call."""
+    pos, m = W.plummer(200000, seed=43)
+    G.forces(pos, m, 0.01, 0.5, 16, 64)
+    ph = G.oneshot_phases()
+    assert list(ph) == list(G.ONESHOT_PHASES)
+    assert all(v >= 0 for v in ph.values())
+    host = sum(ph[k] for k in G.ONESHOT_PHASES[:8])
+    assert host <= ph["host_build"] * 1.05 + 0.05
+    assert ph["device_walk_eval"] > 0 and ph["host_build"] + ph["device_walk_eval"] <= ph["call"] * 1.05 + 0.05
+
+
 def test_device64_outputs_in_input_order(torch):
     pos, m = W.plummer(30000, seed=15)
     for T in (G.Tree.build(pos, m, 16, 64), G.Tree.build_gpu(pos, m, 16, 64)):
