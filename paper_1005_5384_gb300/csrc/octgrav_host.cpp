@@ -71,6 +71,7 @@ int check_build_args(int n_sys, const int64_t* offsets, const double* pos, const
 
 int build_common(int n_sys, const int64_t* offsets, const double* pos, const double* mass, int n_leaf,
                  int n_group, octgrav_tree** out, HostCache* cache = nullptr) {
+  Range range("octgrav:host_build");
   int rc = check_build_args(n_sys, offsets, pos, mass, n_leaf, n_group, out);
   if (rc) return rc;
   const int64_t n = offsets[n_sys];
@@ -522,6 +523,7 @@ int gpu_result(octgrav_tree* t, cudaStream_t st, int64_t* res) {
 
 int build_gpu_common(int n_sys, const int64_t* offsets, const double* pos, const double* mass, int n_leaf,
                      int n_group, cudaStream_t st, Device* dev, octgrav_tree** out) {
+  Range range("octgrav:gpu_build");
   if (!out) return fail(OCTGRAV_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (!pos || !mass || !offsets || n_sys < 1) return fail(OCTGRAV_ERR_ARG, "NULL input or n_sys < 1");
@@ -728,10 +730,16 @@ int octgrav_forces_ex(const double* pos, const double* mass, int64_t n, double e
   TD.timed = false;
   const auto t0 = std::chrono::steady_clock::now();
   octgrav_tree* t = nullptr;
-  if ((rc = build_oneshot(pos, mass, n, n_leaf, n_group, hcache, TD.get(), st, &t, ph))) return rc;
+  {
+    Range r("octgrav:host_build");
+    if ((rc = build_oneshot(pos, mass, n, n_leaf, n_group, hcache, TD.get(), st, &t, ph))) return rc;
+  }
   const auto t1 = std::chrono::steady_clock::now();
   cudaEvent_t* ev = TD.events();
-  rc = forces_host(t, eps, theta, G, acc, pot, st, ev);
+  {
+    Range r("octgrav:forces");
+    rc = forces_host(t, eps, theta, G, acc, pot, st, ev);
+  }
   if (rc) cudaStreamSynchronize(st);  // nothing may still read the cached host arrays
   give_back(t, &hcache);
   octgrav_free_tree(t);
@@ -912,6 +920,7 @@ int octgrav_sim_create(const double* pos, const double* vel, const double* mass,
 }
 
 int octgrav_sim_step(octgrav_sim* s, double dt, int n_steps, void* stream) {
+  Range range("octgrav:sim_step");
   if (!s) return fail(OCTGRAV_ERR_ARG, "sim is NULL");
   if (!std::isfinite(dt) || n_steps < 0) return fail(OCTGRAV_ERR_ARG, "need a finite dt and n_steps >= 0");
   cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -24,6 +24,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/octgrav.h"
 #include "octgrav_internal.h"
@@ -68,6 +69,14 @@ extern thread_local std::string g_err;  // the calling thread's last message
     if (e_ != cudaSuccess)                                                               \
       return fail(OCTGRAV_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));     \
   } while (0)
+
+// An NVTX range for profilers (no cost without one attached): "octgrav:<name>".
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 // ---------------------------------------------------------------- thread pool
 
