@@ -328,7 +328,19 @@ def extras(torch, G, a, pos, m, T, out, flush, stream, peak, steps):
         c = T.interaction_counts()
         res["plummer_median_1e-3"] = {"theta": th, "median_rel_err": md, "forces_per_s": a.n / (ms * 1e-3),
                                       "ms": ms, "frac_fp32_peak": c["flops"] / ms / 1e9 / peak,
-                                      "flops_per_particle": c["flops"] / a.n}
+                                      "flops_per_particle": c["flops"] / a.n, "n_group": a.n_group}
+        # the group size is part of the operating point: the same search at N_group 256
+        T2 = G.Tree.build(pos, m, a.n_leaf, 256)
+        T2.forces_device(a.eps, th, out, stream=stream)
+        T2.balance(stream=stream)
+        th2, md2 = theta_for_median(torch, G, T2, out, a.eps, samp, ad)
+        if th2 is not None:
+            ms2 = time_kernel(torch, lambda: T2.forces_device(a.eps, th2, out, stream=stream), flush, steps, stream)
+            c2 = T2.interaction_counts()
+            res["plummer_median_1e-3"]["at_n_group_256"] = {
+                "theta": th2, "median_rel_err": md2, "forces_per_s": a.n / (ms2 * 1e-3), "ms": ms2,
+                "frac_fp32_peak": c2["flops"] / ms2 / 1e9 / peak, "flops_per_particle": c2["flops"] / a.n}
+        del T2
     # C3: clustered, 4,194,304 particles, theta 0.5, eps 0.001
     cpos, cm = W.clustered(4_194_304, 64, seed=3)
     CT = G.Tree.build(cpos, cm, a.n_leaf, a.n_group)
