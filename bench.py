@@ -313,6 +313,17 @@ def extras(torch, G, a, pos, m, T, out, flush, stream, peak, steps):
                                                       "particle_steps_per_s": a.n * nsteps / dt_refit,
                                                       "rel_energy_change_21_steps": (e2 - e0) / abs(e0)}}
     del S
+    # C1: the 16,384-particle Plummer sphere (the parity workload), theta 0.5
+    spos, sm = W.plummer(16384, seed=1)
+    ST = G.Tree.build(spos, sm, a.n_leaf, 64)
+    sout = torch.empty((ST.n, 4), dtype=torch.float32, device="cuda")
+    ST.forces_device(a.eps, 0.5, sout, stream=stream)
+    ST.balance(stream=stream)
+    ms = time_kernel(torch, lambda: ST.forces_device(a.eps, 0.5, sout, stream=stream), flush, steps, stream)
+    c = ST.interaction_counts()
+    res["plummer_16k"] = {"n_group": 64, "forces_per_s": ST.n / (ms * 1e-3), "ms": ms,
+                          "frac_fp32_peak": c["flops"] / ms / 1e9 / peak, "flops_per_particle": c["flops"] / ST.n}
+    del ST, sout
     # C2 at theta = 0.75
     T.forces_device(a.eps, 0.75, out, stream=stream)
     ms = time_kernel(torch, lambda: T.forces_device(a.eps, 0.75, out, stream=stream), flush, steps, stream)
