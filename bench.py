@@ -315,13 +315,16 @@ def extras(torch, G, a, pos, m, T, out, flush, stream, peak, steps):
     del S
     # C1: the 16,384-particle Plummer sphere (the parity workload), theta 0.5
     spos, sm = W.plummer(16384, seed=1)
-    ST = G.Tree.build(spos, sm, a.n_leaf, 64)
+    stuned = G.autotune([(spos, sm)], n_leaf=a.n_leaf, eps=a.eps, theta=0.5, candidates=(16, 32, 64, 128),
+                        stream=stream)
+    ST = G.Tree.build(spos, sm, a.n_leaf, stuned["n_group"])
+    ST.set_launch(stuned["particles_per_lane"])
     sout = torch.empty((ST.n, 4), dtype=torch.float32, device="cuda")
     ST.forces_device(a.eps, 0.5, sout, stream=stream)
     ST.balance(stream=stream)
     ms = time_kernel(torch, lambda: ST.forces_device(a.eps, 0.5, sout, stream=stream), flush, steps, stream)
     c = ST.interaction_counts()
-    res["plummer_16k"] = {"n_group": 64, "forces_per_s": ST.n / (ms * 1e-3), "ms": ms,
+    res["plummer_16k"] = {"autotuned": stuned, "forces_per_s": ST.n / (ms * 1e-3), "ms": ms,
                           "frac_fp32_peak": c["flops"] / ms / 1e9 / peak, "flops_per_particle": c["flops"] / ST.n}
     del ST, sout
     # C2 at theta = 0.75
