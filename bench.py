@@ -776,11 +776,13 @@ def main():
     }
     acc = np.empty((a.n, 3))
     acc[T.perm()] = out.cpu().numpy()[:, :3]
-    if not a.no_cpu_baseline and rank == 0:
+    # the oracle baseline, the accuracy check and the extra workloads run at N = 1 only: at N > 1
+    # the GPUs are held for the headline line alone
+    if not a.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(pos, m, a, a.cpu_seconds, acc)
-    if not a.no_accuracy:
+    if not a.no_accuracy and world == 1:
         line["accuracy"] = accuracy(G, acc, pos, m, a)
-    if not a.no_extras:
+    if not a.no_extras and world == 1:
         line["extras"] = extras(torch, G, a, pos, m, T, out, flush, stream, peak, min(a.steps, 10))
     print(json.dumps(line), flush=True)
     if dist:
