@@ -725,6 +725,9 @@ def main():
     host_phases = G.oneshot_phases() if host_t else None  # the last call's breakdown (ms)
     e2e_s = statistics.mean(e2e_t[1:]) if len(e2e_t) > 1 else float("nan")
     host_s = statistics.mean(host_t[1:]) if len(host_t) > 1 else float("nan")
+    if dist and len(e2e_t) > 1:  # the slowest rank's time, as for the headline
+        e2e_s = RK.max_over_ranks(dist, e2e_s, device="cuda")
+        host_s = RK.max_over_ranks(dist, host_s, device="cuda")
     s = T.stats
     # host-build path: the tree's device arrays go up (particles 32 B + the int32 permutation,
     # cells 16 + 8 + 64 B, items 16 + 64 B + the 4-byte processing order) and the FP64
