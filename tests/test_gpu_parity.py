@@ -278,12 +278,16 @@ def test_small_capture_buffer_reports_err_list(_cuda):
     assert len(T.debug_lists(0.5, cap=8192)) == T.stats["n_items"]
 
 
-@pytest.mark.parametrize("shape", ["plane", "line", "two_points_and_a_cloud"])
+@pytest.mark.parametrize("shape", ["plane", "line", "two_points_and_a_cloud", "zero_masses", "far_offset"])
 def test_degenerate_geometries(_cuda, shape):
     """Flat and one-dimensional systems (zero extent on some axes: boxes and
-    cubes of zero thickness, distances along a single axis) and a cloud with
-    two heavy coincident pairs: lists bit-exact and forces within 1e-5 of the
-    oracle, GPU build identical to the host build."""
+    cubes of zero thickness, distances along a single axis), a cloud with two
+    heavy coincident pairs, a third of the particles massless (cells of zero
+    mass take the cube centre as centre of mass), and a cloud of unit size
+    10^4 away from the origin (FP32 absolute coordinates would keep ~1e-3 of
+    its structure; the group-relative hi/lo coordinates keep it all): lists
+    bit-exact and forces within 1e-5 of the oracle, GPU build identical to the
+    host build."""
     rng = np.random.default_rng(60)
     n = 40000
     pos = rng.standard_normal((n, 3))
@@ -292,12 +296,16 @@ def test_degenerate_geometries(_cuda, shape):
     elif shape == "line":
         pos[:, 1] = 0.0
         pos[:, 2] = 0.0
-    else:
+    elif shape == "two_points_and_a_cloud":
         pos[:2] = [0.3, 0.3, 0.3]
         pos[2:4] = [-1.0, 0.5, 2.0]
+    elif shape == "far_offset":
+        pos += np.array([1.0e4, -1.0e4, 3.0e3])
     m = np.full(n, 1.0 / n)
     if shape == "two_points_and_a_cloud":
         m[:4] = 0.05
+    elif shape == "zero_masses":
+        m[::3] = 0.0
     T, R = _list_parity(pos, m, 16, 64, 0.6)
     acc, pot = T.forces(0.01, 0.6)
     ra, rp, _, _, _ = R.forces(0.01, 0.6)
