@@ -319,6 +319,7 @@ def extras(torch, G, a, pos, m, T, out, flush, stream, peak, steps):
                         stream=stream)
     ST = G.Tree.build(spos, sm, a.n_leaf, stuned["n_group"])
     ST.set_launch(stuned["particles_per_lane"])
+    ST.set_split(stuned["split"])
     sout = torch.empty((ST.n, 4), dtype=torch.float32, device="cuda")
     ST.forces_device(a.eps, 0.5, sout, stream=stream)
     ST.balance(stream=stream)

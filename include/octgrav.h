@@ -326,9 +326,11 @@ int octgrav_graph_launch(octgrav_tree *t, void *stream);
 
 /* Autotuner: for the given systems (layout as octgrav_build_batch) times the
  * fused kernel for every group size in n_group_cand[0..n_cand) (values below
- * n_leaf are skipped) and particles-per-lane 1 and 2, and returns the fastest
- * in best[0] = n_group, best[1] = particles per lane, best[2] = 0 (CTAs/SM:
- * occupancy maximum), with its median time in *best_ms (may be NULL).
+ * n_leaf are skipped), particles-per-lane 1 and 2 and, where the work items
+ * are too few to fill the GPU (fewer than 4 per warp slot), list splits of
+ * 1, 2 and 4 (octgrav_set_split), and returns the fastest in best[0] =
+ * n_group, best[1] = particles per lane, best[2] = list split, with its
+ * median time in *best_ms (may be NULL).
  * Results are cached in-process per (n_sys, log2 N, theta, eps, n_leaf,
  * candidates). Builds temporary trees and device buffers. Synchronous.
  * Errors: as octgrav_build_batch and octgrav_forces_device. */
@@ -399,6 +401,16 @@ int octgrav_set_staging(octgrav_tree *t, int mode);
  * launches. A graph captured before the call keeps the old settings.
  * Errors: ERR_ARG (stack_cap < 0, drop_item outside [-1, n_items)). */
 int octgrav_set_fault(octgrav_tree *t, int stack_cap, int64_t drop_item);
+
+/* List split for systems too small to fill the GPU: later launches of t walk
+ * every work item with nparts warps (1 = off, up to 16); part j evaluates the
+ * accepted cells and queued leaves whose sequence numbers are j modulo nparts
+ * (part 0 also the group's own particles), and the parts' results are summed
+ * in part order by a second kernel, so a launch is deterministic but rounds
+ * differently from an unsplit one (FP32 sums of nparts partial results).
+ * Applies to launches with the plain opening test and staging mode 1 that
+ * capture no lists; others run unsplit. Errors: ERR_ARG. */
+int octgrav_set_split(octgrav_tree *t, int nparts);
 
 void octgrav_free_tree(octgrav_tree *t);
 

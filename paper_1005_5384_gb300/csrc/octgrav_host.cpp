@@ -281,6 +281,12 @@ og::KParams make_params(octgrav_tree* t, float4* out) {
   return p;
 }
 
+// Parts of a list-split launch of t (1: no split): only plain-criterion,
+// cp.async-staged launches that capture no lists split.
+int split_parts(const octgrav_tree* t, bool capture) {
+  return (t->nparts > 1 && !capture && !t->learned && t->stage == og::STAGING_ASYNC) ? t->nparts : 1;
+}
+
 int launch(octgrav_tree* t, double eps, double theta, double G, float4* out, cudaStream_t st,
            bool capture, int* dbg_cell, int* dbg_leaf, int2* dbg_n, int dbg_cap) {
   int rc = check_params(eps, theta, G);
@@ -301,9 +307,19 @@ int launch(octgrav_tree* t, double eps, double theta, double G, float4* out, cud
     p.dbg_cap = dbg_cap;
   }
   CUDA_TRY(cudaMemsetAsync(t->dev->ctl.p, 0, 8, st));
+  const int nparts = split_parts(t, capture);
+  if (nparts > 1) {  // the parts' outputs are summed into out below; counts are accumulated
+    if ((rc = t->dev->split.reserve(sizeof(float4) * nparts * static_cast<size_t>(t->n)))) return rc;
+    p.nparts = nparts;
+    p.n = static_cast<int>(t->n);
+    p.part_out = static_cast<float4*>(t->dev->split.p);
+    CUDA_TRY(cudaMemsetAsync(t->dev->counts.p, 0, sizeof(int2) * t->n_items, st));
+  }
   if (p.n_items > 0) {
     cudaError_t e = og::launch_walk_eval(p, t->ppl, t->ctas_per_sm, capture, st, nullptr);
     if (e != cudaSuccess) return fail(OCTGRAV_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+    if (nparts > 1 && (e = og::split_sum(p.part_out, nparts, p.n, out, st)) != cudaSuccess)
+      return fail(OCTGRAV_ERR_CUDA, "split sum launch failed: %s", cudaGetErrorString(e));
   }
   t->launched = true;
   return OCTGRAV_OK;
@@ -1228,6 +1244,9 @@ int octgrav_graph_capture(octgrav_tree* t, double eps, double theta, double G, f
     if ((rc = upload(t, st))) return rc;
   }
   CUDA_TRY(cudaStreamSynchronize(st));  // uploads from pageable memory cannot be captured
+  if (const int np = split_parts(t, false); np > 1) {  // allocate outside the capture
+    if ((rc = t->dev->split.reserve(sizeof(float4) * np * static_cast<size_t>(t->n)))) return rc;
+  }
   og::LaunchInfo li;
   cudaError_t e = og::prepare_walk_eval(t->ppl, t->stage, t->ctas_per_sm, &li);
   if (e != cudaSuccess) return fail(OCTGRAV_ERR_CUDA, "kernel preparation failed: %s", cudaGetErrorString(e));
@@ -1276,7 +1295,7 @@ int octgrav_autotune(int n_sys, const int64_t* offsets, const double* pos, const
       if (kv.first == key) {
         best[0] = static_cast<int>(kv.second[0]);
         best[1] = static_cast<int>(kv.second[1]);
-        best[2] = 0;
+        best[2] = static_cast<int>(kv.second[3]);
         if (best_ms) *best_ms = kv.second[2];
         return OCTGRAV_OK;
       }
@@ -1288,13 +1307,17 @@ int octgrav_autotune(int n_sys, const int64_t* offsets, const double* pos, const
   CUDA_TRY(cudaEventCreate(&e0));
   CUDA_TRY(cudaEventCreate(&e1));
   double bms = 1e300;
-  int bng = -1, bppl = 2;
+  int bng = -1, bppl = 2, bsplit = 1;
   for (int c = 0; c < n_cand && rc == OCTGRAV_OK; ++c) {
     if (n_group_cand[c] < n_leaf) continue;
     octgrav_tree* t = nullptr;
     if ((rc = build_common(n_sys, offsets, pos, mass, n_leaf, n_group_cand[c], &t))) break;
-    for (int ppl = 1; ppl <= 2 && rc == OCTGRAV_OK; ++ppl) {
-      if ((rc = octgrav_set_launch(t, ppl, 0))) break;
+    // list splits only where the work items are too few to fill the GPU
+    const int max_split = t->n_items < 4 * 152 * 16 ? 4 : 1;
+    for (int trial = 0; trial < 2 * 3 && rc == OCTGRAV_OK; ++trial) {
+      const int ppl = 1 + trial % 2, split = 1 << (trial / 2);
+      if (split > max_split) break;
+      if ((rc = octgrav_set_launch(t, ppl, 0)) || (rc = octgrav_set_split(t, split))) break;
       float4* out = static_cast<float4*>(outb.p);
       if ((rc = launch(t, eps, theta, 1.0, out, st, false, nullptr, nullptr, nullptr, 0))) break;
       if ((rc = octgrav_balance(t, 1, st))) break;  // time the longest-first order
@@ -1315,6 +1338,7 @@ int octgrav_autotune(int n_sys, const int64_t* offsets, const double* pos, const
         bms = ms[1];
         bng = n_group_cand[c];
         bppl = ppl;
+        bsplit = split;
       }
     }
     octgrav_free_tree(t);
@@ -1326,10 +1350,19 @@ int octgrav_autotune(int n_sys, const int64_t* offsets, const double* pos, const
   if (bng < 0) return fail(OCTGRAV_ERR_ARG, "no candidate n_group >= n_leaf");
   best[0] = bng;
   best[1] = bppl;
-  best[2] = 0;
+  best[2] = bsplit;
   if (best_ms) *best_ms = bms;
   std::lock_guard<std::mutex> g(mu);
-  cache.push_back({key, {static_cast<double>(bng), static_cast<double>(bppl), bms}});
+  cache.push_back({key, {static_cast<double>(bng), static_cast<double>(bppl), bms, static_cast<double>(bsplit)}});
+  return OCTGRAV_OK;
+}
+
+int octgrav_set_split(octgrav_tree* t, int nparts) {
+  if (!t) return fail(OCTGRAV_ERR_ARG, "tree is NULL");
+  if (nparts < 1 || nparts > 16) return fail(OCTGRAV_ERR_ARG, "nparts must be in [1, 16]");
+  if (static_cast<int64_t>(nparts) * t->n_items >= (1ll << 31))
+    return fail(OCTGRAV_ERR_ARG, "too many work items to split %d ways", nparts);
+  t->nparts = nparts;
   return OCTGRAV_OK;
 }
 

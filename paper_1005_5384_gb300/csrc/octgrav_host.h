@@ -291,6 +291,7 @@ struct Device {
   // GPU build: tree arrays beyond the walk's, scratch, inputs and FP64 outputs
   DevBuf perm, key, props, pcount, cfirst, groups, ikey, celloff, result, scratch, in_pos, in_mass, acc64, pot64;
   DevBuf order;  // work-item processing order (octgrav_balance)
+  DevBuf split;  // per-part outputs of a list-split launch (octgrav_set_split)
   int device = -1;
   int pageable = -1;     // kernels may read pageable host memory (-1: not asked yet)
   int64_t cell_cap = 0;  // cell capacity that last sufficed for a GPU build
@@ -315,7 +316,7 @@ struct Device {
     ev_in = ev_out = nullptr;
     for (DevBuf* b : {&parts, &geo, &link, &mp, &items, &ibox, &sysp, &out, &counts, &ctl, &dbg, &mlp, &perm, &key,
                       &props, &pcount, &cfirst, &groups, &ikey, &celloff, &result, &scratch, &in_pos, &in_mass,
-                      &acc64, &pot64, &order})
+                      &acc64, &pot64, &order, &split})
       b->release();
     cell_cap = 0;
   }
@@ -330,6 +331,7 @@ struct octgrav_tree {
   int n_leaf = 0, n_group = 0, n_sys = 0;
   int ppl = 2, ctas_per_sm = 0;
   int fault_stack_cap = 0, fault_drop_item = 0;  // failure injection (octgrav_set_fault; 0 = off)
+  int nparts = 1;  // list split of every work item over this many warps (octgrav_set_split)
   int stage = og::STAGING_ASYNC;
   bool learned = false;             // learned opening criterion active
   float theta_lo = 0, theta_hi = 0, theta_fb = 0;

@@ -66,6 +66,13 @@ struct KParams {
   // reports ST_TIMEOUT
   int stack_cap;
   int drop_item;
+  // list split (small systems; 1 = off): work item k is walked by nparts warps,
+  // part j evaluating the accepted cells and queued leaves whose sequence
+  // number is j modulo nparts (part 0 also the group's own particles) into
+  // part_out[j * n + particle]; counts are accumulated with atomics
+  int nparts;
+  int n;                 // particles (rows of one part_out slice)
+  float4* part_out;
   // capture mode (tests): per item up to dbg_cap cell indices
   int* dbg_cell;
   int* dbg_leaf;
@@ -87,6 +94,9 @@ cudaError_t launch_walk_eval(const KParams& p, int ppl, int ctas_per_sm, bool ca
 // Compute (and cache) the launch configuration of a kernel variant without
 // launching it; call before stream capture.
 cudaError_t prepare_walk_eval(int ppl, int stage, int ctas_per_sm, LaunchInfo* info);
+// out[i] = sum over k of part_out[k * n + i], k = 0 .. nparts - 1 in order
+// (the parts of a list-split launch).
+cudaError_t split_sum(const float4* part_out, int nparts, int n, float4* out, cudaStream_t stream);
 
 // Shared memory per CTA of the fused kernel.
 size_t walk_eval_smem_bytes();

@@ -382,7 +382,7 @@ struct CtaWarps {
   static constexpr int v = MLP ? WARPS_MLP : WARPS;
 };
 
-template <int R, int STAGE, bool CAPTURE, bool MLP>
+template <int R, int STAGE, bool CAPTURE, bool MLP, bool SPLIT = false>
 __global__ void __launch_bounds__(CtaWarps<MLP>::v * 32, MLP ? 1 : 2) walk_eval_kernel(const __grid_constant__ KParams p) {
   constexpr int REC = RingStride<STAGE>::v;
   using WarpSmem = WarpSmemT<STAGE == STAGE_GATHER4, MLP>;
@@ -416,12 +416,17 @@ __global__ void __launch_bounds__(CtaWarps<MLP>::v * 32, MLP ? 1 : 2) walk_eval_
   int status = 0;
 
   for (;;) {
-    int item = 0;
+    int item = 0, part = 0;
     if (lane == 0) {
       item = static_cast<int>(atomicAdd(p.work, 1u));
+      if (SPLIT) {  // the parts of one item are consecutive work indices
+        part = item % p.nparts;
+        item /= p.nparts;
+      }
       if (p.order && item < p.n_items) item = __ldg(p.order + item);  // longest first
     }
     item = __shfl_sync(FULL, item, 0);
+    if (SPLIT) part = __shfl_sync(FULL, part, 0);
     if (item >= p.n_items) break;
 
     const int4 it = __ldg(p.items + item);
@@ -642,11 +647,14 @@ __global__ void __launch_bounds__(CtaWarps<MLP>::v * 32, MLP ? 1 : 2) walk_eval_
     // The group's own particles: they sit in the group's own leaves, which are
     // always opened (distance 0) and are evaluated here, with the self term
     // left out, instead of through the leaf queue.
-    n_pp += gcount;
-    pp_pass(gcount, 0, true);
+    if (!SPLIT || part == 0) {
+      n_pp += gcount;
+      pp_pass(gcount, 0, true);
+    }
 
     // ---- walk (Listing 1): root opened; children of up to 4 nodes per step
     int top = 0, nlq = 0, n_pc = 0, n_leafent = 0;
+    int nlq_all = 0;  // leaves queued by every part (SPLIT: their sequence numbers)
     bool ok = true;
     // failure injection: the first tile of this item is never requested
     const uint32_t drop_end = (STAGE == STAGE_GATHER4 && item + 1 == p.drop_item) ? app + TILE : 0u;
@@ -778,13 +786,21 @@ __global__ void __launch_bounds__(CtaWarps<MLP>::v * 32, MLP ? 1 : 2) walk_eval_
       }
       if (open && !leaf) S.stack[top + __popc(m_node & lt)] = (lk.x << 3) | (lk.y - 1);
       top += nn;
-      if (open && leaf && !own_leaf) S.leafq[nlq + __popc(m_lq & lt)] = make_int2(lk.x, -lk.y);
+      unsigned m_lq_use = m_lq;  // the queued leaves this warp evaluates
+      if (SPLIT) {
+        const bool mine = (nlq_all + __popc(m_lq & lt)) % p.nparts == part;
+        m_lq_use = __ballot_sync(FULL, open && leaf && !own_leaf && mine);
+        nlq_all += __popc(m_lq);
+      }
+      if ((m_lq_use >> lane) & 1u) S.leafq[nlq + __popc(m_lq_use & lt)] = make_int2(lk.x, -lk.y);
       if (CAPTURE && open && leaf && n_leafent + __popc(m_leaf & lt) < p.dbg_cap)
         p.dbg_leaf[(size_t)item * p.dbg_cap + n_leafent + __popc(m_leaf & lt)] = c;
-      nlq += __popc(m_lq);
+      nlq += __popc(m_lq_use);
       n_leafent += __popc(m_leaf);
-      if (valid && !open) {
-        const uint32_t e = app + __popc(m_acc & lt);
+      unsigned m_stage = m_acc;  // the accepted cells this warp evaluates
+      if (SPLIT) m_stage = __ballot_sync(FULL, valid && !open && (n_pc + __popc(m_acc & lt)) % p.nparts == part);
+      if ((m_stage >> lane) & 1u) {
+        const uint32_t e = app + __popc(m_stage & lt);
         const uint32_t se = e % (NTILE * TILE);
         if (STAGE == STAGE_BULK) {
           const uint32_t bar = bar0 + 8 * (se / TILE);
@@ -801,10 +817,10 @@ __global__ void __launch_bounds__(CtaWarps<MLP>::v * 32, MLP ? 1 : 2) walk_eval_
         if (CAPTURE && n_pc + __popc(m_acc & lt) < p.dbg_cap)
           p.dbg_cell[(size_t)item * p.dbg_cap + n_pc + __popc(m_acc & lt)] = c;
       }
-      const int na = __popc(m_acc);
+      const int na = __popc(m_stage);
       const uint32_t old = app;
       app += na;
-      n_pc += na;
+      n_pc += __popc(m_acc);
       if (STAGE == STAGE_ASYNC) cp_async_commit();
       __syncwarp();  // all expect_tx / index writes of this step are done
       if (STAGE == STAGE_BULK && lane == 0) {
@@ -905,13 +921,22 @@ __global__ void __launch_bounds__(CtaWarps<MLP>::v * 32, MLP ? 1 : 2) walk_eval_
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         if (P.idx[r] >= 0) {
-          p.out[P.idx[r]] = make_float4(G * (P.hi[r].x + P.lo[r].x), G * (P.hi[r].y + P.lo[r].y),
-                                        G * (P.hi[r].z + P.lo[r].z), G * (P.hi[r].p + P.lo[r].p));
+          const float4 v = make_float4(G * (P.hi[r].x + P.lo[r].x), G * (P.hi[r].y + P.lo[r].y),
+                                       G * (P.hi[r].z + P.lo[r].z), G * (P.hi[r].p + P.lo[r].p));
+          if (SPLIT)
+            p.part_out[static_cast<size_t>(part) * p.n + P.idx[r]] = v;
+          else
+            p.out[P.idx[r]] = v;
         }
       }
     }
     if (lane == 0) {
-      p.counts[item] = make_int2(n_pc, n_pp);
+      if (SPLIT) {  // zeroed before the launch; every part walked all of the lists
+        if (part == 0) atomicAdd(&p.counts[item].x, n_pc);
+        atomicAdd(&p.counts[item].y, n_pp);
+      } else {
+        p.counts[item] = make_int2(n_pc, n_pp);
+      }
       if (CAPTURE) p.dbg_n[item] = make_int2(n_pc, n_leafent);
     }
     if (status & ST_STACK) break;
@@ -928,11 +953,11 @@ struct LaunchCache {
   int sms[64] = {};
 };
 
-template <int R, int STAGE, bool CAPTURE, bool MLP = false>
+template <int R, int STAGE, bool CAPTURE, bool MLP = false, bool SPLIT = false>
 cudaError_t launch_t(const KParams& p, int ctas_per_sm, cudaStream_t stream, LaunchInfo* info, bool dry) {
   constexpr int NW = CtaWarps<MLP>::v;
   const size_t smem = sizeof(WarpSmemT<STAGE == STAGE_GATHER4, MLP>) * NW + (MLP ? sizeof(MlpDevice) : 0) + 128;
-  auto kern = walk_eval_kernel<R, STAGE, CAPTURE, MLP>;
+  auto kern = walk_eval_kernel<R, STAGE, CAPTURE, MLP, SPLIT>;
   static LaunchCache cache;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -1013,6 +1038,10 @@ cudaError_t launch_dispatch(const KParams& p, int ppl, int ctas_per_sm, bool cap
     return capture ? launch_t<2, STAGE_ASYNC, true, true>(p, ctas_per_sm, stream, info, dry)
                    : launch_t<2, STAGE_ASYNC, false, true>(p, ctas_per_sm, stream, info, dry);
   }
+  if (p.nparts > 1 && !capture && p.stage == STAGE_ASYNC) {  // list split (small systems)
+    return ppl == 1 ? launch_t<1, STAGE_ASYNC, false, false, true>(p, ctas_per_sm, stream, info, dry)
+                    : launch_t<2, STAGE_ASYNC, false, false, true>(p, ctas_per_sm, stream, info, dry);
+  }
   switch (p.stage) {
     case STAGE_BULK: return launch_s<STAGE_BULK>(p, ppl, ctas_per_sm, capture, stream, info, dry);
     case STAGE_ASYNC: return launch_s<STAGE_ASYNC>(p, ppl, ctas_per_sm, capture, stream, info, dry);
@@ -1023,6 +1052,29 @@ cudaError_t launch_dispatch(const KParams& p, int ppl, int ctas_per_sm, bool cap
 cudaError_t launch_walk_eval(const KParams& p, int ppl, int ctas_per_sm, bool capture,
                              cudaStream_t stream, LaunchInfo* info) {
   return launch_dispatch(p, ppl, ctas_per_sm, capture, stream, info, false);
+}
+
+namespace {
+__global__ void k_split_sum(const float4* __restrict__ part_out, int nparts, int n, float4* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    float4 s = part_out[i];
+    for (int k = 1; k < nparts; ++k) {  // in part order: the same sum on every launch
+      const float4 v = part_out[static_cast<size_t>(k) * n + i];
+      s.x += v.x;
+      s.y += v.y;
+      s.z += v.z;
+      s.w += v.w;
+    }
+    out[i] = s;
+  }
+}
+}  // namespace
+
+cudaError_t split_sum(const float4* part_out, int nparts, int n, float4* out, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  const int grid = min((n + 255) / 256, 152 * 8);
+  k_split_sum<<<grid, 256, 0, stream>>>(part_out, nparts, n, out);
+  return cudaGetLastError();
 }
 
 cudaError_t prepare_walk_eval(int ppl, int stage, int ctas_per_sm, LaunchInfo* info) {

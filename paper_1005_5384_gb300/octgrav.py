@@ -72,6 +72,7 @@ _SIGS = {
     "octgrav_balance": (C.c_int, [_vp, C.c_int, _vp]),
     "octgrav_set_staging": (C.c_int, [_vp, C.c_int]),
     "octgrav_set_fault": (C.c_int, [_vp, C.c_int, C.c_int64]),
+    "octgrav_set_split": (C.c_int, [_vp, C.c_int]),
     "octgrav_oneshot_phases": (C.c_int, [_vp, C.c_int]),
     "octgrav_mlp_samples": (C.c_int, [_vp, _i64, C.c_int64, C.c_double, C.c_double, _vp, _vp, _vp, C.c_int64,
                                       C.POINTER(C.c_int64), _vp]),
@@ -277,6 +278,11 @@ class Tree:
     def set_staging(self, mode: int):
         """0 = cp.async.bulk per record, 1 = 16-byte cp.async (default), 2 = TMA gather4."""
         _check(load().octgrav_set_staging(self._h, int(mode)))
+
+    def set_split(self, nparts: int = 1):
+        """Walk every work item with nparts warps, each evaluating a share of the
+        lists (small systems; 1 = off)."""
+        _check(load().octgrav_set_split(self._h, int(nparts)))
 
     def set_fault(self, stack_cap: int = 0, drop_item: int = -1):
         """Failure injection for tests: a node stack of stack_cap entries (0 = all),
@@ -557,7 +563,7 @@ def autotune(systems, n_leaf: int = 16, eps: float = 0.01, theta: float = 0.5, c
     ms = np.zeros(1)
     _check(lib.octgrav_autotune(len(systems), off, pos.reshape(-1), mass, int(n_leaf), float(eps), float(theta),
                                 _p(cand), len(cand), _p(best), _p(ms), _stream_handle(stream)))
-    return dict(n_group=int(best[0]), particles_per_lane=int(best[1]), ms=float(ms[0]))
+    return dict(n_group=int(best[0]), particles_per_lane=int(best[1]), split=int(best[2]), ms=float(ms[0]))
 
 
 def version() -> int:

@@ -313,3 +313,40 @@ def test_degenerate_geometries(_cuda, shape):
     assert float(np.linalg.norm(pot - rp) / np.linalg.norm(rp)) <= TOL_RMS
     acc_g, _ = G.forces_gpu(pos, m, 0.01, 0.6, 16, 64)
     assert np.array_equal(acc_g, acc)
+
+
+@pytest.mark.parametrize("nparts", [2, 4])
+def test_list_split_matches_unsplit_and_oracle(_cuda, nparts):
+    """List split (a small system's work items walked by several warps, each
+    evaluating a share of the lists): the same interaction counts as the
+    unsplit launch, forces within FP32 rounding of it and within 1e-5 of the
+    oracle, bitwise reproducible, and the same through a captured graph."""
+    torch = _cuda
+    pos, m = W.plummer(16384, seed=1)
+    T = G.Tree.build(pos, m, 16, 16)
+    a1, p1 = T.forces(0.01, 0.5)
+    c1 = T.interaction_counts()
+    T.set_split(nparts)
+    a2, p2 = T.forces(0.01, 0.5)
+    c2 = T.interaction_counts()
+    assert c1["n_pc"] == c2["n_pc"] and c1["n_pp"] == c2["n_pp"]
+    assert O.rel_rms(a2, a1) <= 1e-6
+    R = O.Tree(pos, m, 16, 16)
+    ra, rp, _, _, _ = R.forces(0.01, 0.5)
+    assert O.rel_rms(a2, ra) <= TOL_RMS
+    assert float(np.linalg.norm(p2 - rp) / np.linalg.norm(rp)) <= TOL_RMS
+    a3, _ = T.forces(0.01, 0.5)
+    assert np.array_equal(a2, a3)
+    out = torch.empty((T.n, 4), dtype=torch.float32, device="cuda")
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        T.forces_device(0.01, 0.5, out, stream=st)
+        st.synchronize()
+        ref = out.clone()
+        T.capture_graph(0.01, 0.5, out, stream=st)
+        out.zero_()
+        T.launch_graph(stream=st)
+        st.synchronize()
+    assert torch.equal(out, ref)
+    with pytest.raises(G.OctgravError):
+        T.set_split(0)
