@@ -131,3 +131,34 @@ def test_item_split_for_large_groups():
     assert T.stats["max_group"] == 140
     T.set_launch(1)
     assert T.item_info()["count"].max() <= 32
+
+
+def test_host_builds_from_threads_agree():
+    """Host builds started from four threads at once share the library's thread
+    pool (one parallel region at a time) and give the single-thread tree: the
+    same permutation, cell keys and FP64 cell properties."""
+    import threading
+
+    pos, m = W.plummer(120000, seed=71)
+    ref = G.Tree.build(pos, m, 16, 64)
+    ref_perm, ref_keys = ref.perm(), ref.cell_keys()
+    ref_props = ref.cell_props()
+    out, errors = [None] * 4, []
+
+    def work(k):
+        try:
+            t = G.Tree.build(pos, m, 16, 64)
+            out[k] = (t.perm(), t.cell_keys(), t.cell_props())
+        except Exception as e:  # reported on the main thread
+            errors.append(e)
+
+    threads = [threading.Thread(target=work, args=(k,)) for k in range(4)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    for perm, keys, props in out:
+        assert np.array_equal(perm, ref_perm) and np.array_equal(keys, ref_keys)
+        for name in ref_props:
+            assert np.array_equal(props[name], ref_props[name]), name
