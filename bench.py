@@ -151,6 +151,15 @@ def fp32_peak_tflops(torch):
     return sms * 128 * 2 * mhz * 1e6 / 1e12, sms, mhz
 
 
+def hbm_peak_gbs():
+    """Measured copy bandwidth of this GPU (MEASURED_PEAKS.json), else the profiling fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
 def measured_traffic(a):
     """DRAM bytes per launch from the committed ncu summary, if it matches this kernel and workload."""
     import hashlib
@@ -742,6 +751,8 @@ def main():
         if dist:
             dist.destroy_process_group()
         return
+    traffic = measured_traffic(a)
+    hbm_peak, hbm_src = hbm_peak_gbs()
     line = {
         "metric": METRIC, "value": value, "unit": "forces/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -771,9 +782,13 @@ def main():
                 "path": "octgrav_forces_gpu: pinned H2D + GPU tree build + kernel + device unpermute + pinned D2H"}},
         "gpu_launches": a.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": measured_traffic(a),
+                     "frac": achieved / peak, "traffic": traffic,
                      "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz" % (sms, mhz),
-                     "kernel": "walk_eval_kernel (fused walk + evaluation)"},
+                     "kernel": "walk_eval_kernel (fused walk + evaluation)",
+                     # the tree sits in L2: DRAM sees each array about once per launch
+                     "hbm": None if traffic is None else {
+                         "achieved_gbs": traffic / (ms_step * 1e-3) / 1e9, "peak_gbs": hbm_peak,
+                         "frac": traffic / (ms_step * 1e-3) / 1e9 / hbm_peak, "peak_source": hbm_src}},
         "clocks": clk,
         "wall_s_timed_loop_incl_flush": wall,
         "tree": s,
