@@ -10,7 +10,6 @@
 * the gain: at an equal median relative force error of 1e-3 the learned walk
   needs fewer interactions and less time than the plain theta walk.
 """
-import time
 
 import numpy as np
 import pytest
@@ -150,33 +149,44 @@ def _bisect(f, lo, hi, target=1e-3, iters=10, increasing=True):
     return lo
 
 
-def _time(T, torch, out, eps, theta, reps=7):
+def _time_events(T, torch, out, eps, theta, reps=9):
+    """Median launch time (ms) between CUDA events on the current stream."""
+    T.forces_device(eps, theta, out)
     ts = []
     for _ in range(reps):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
         T.forces_device(eps, theta, out)
+        b.record()
         torch.cuda.synchronize()
-        ts.append(time.perf_counter() - t0)
+        ts.append(a.elapsed_time(b))
     return float(np.median(ts))
 
 
 def test_learned_criterion_beats_theta_at_equal_median_error(torch):
-    # the network is trained on a system of the same size and kind, another seed
-    tpos, tm = W.sphere_disc(262144, seed=6)
-    TT = G.Tree.build(tpos, tm, 16, 64)
-    groups = np.sort(np.random.default_rng(0).choice(TT.stats["n_groups"], 128, replace=False))
+    """C5 as the benchmark runs it: the network trained on another seed of the
+    same kind of system (64 groups), N_group 256; the plain walk and the learned
+    walk each tuned to a median Delta a/a of 1e-3 against FP64 direct sums at
+    1024 particles; both timed with CUDA events after ordering their items
+    longest first. The learned walk needs at least 20 % fewer flops and runs
+    at least 5 % faster (measured: 35 % and ~15 %)."""
+    tpos, tm = W.sphere_disc(1 << 20, seed=6)
+    TT = G.Tree.build(tpos, tm, 16, 256)
+    groups = np.sort(np.random.default_rng(0).choice(TT.stats["n_groups"], 64, replace=False))
     f, lab, _ = TT.mlp_samples(groups, 0.35, 0.01)
     rec, _ = G.mlp_train(f, lab, steps=3000, batch=4096, lr=2e-3, seed=3)
-    pos, m = W.sphere_disc(262144, seed=5)
-    T = G.Tree.build(pos, m, 16, 64)
+    del TT
+    pos, m = W.sphere_disc(1 << 20, seed=5)
+    T = G.Tree.build(pos, m, 16, 256)
     out = torch.empty((T.n, 4), dtype=torch.float32, device="cuda")
-    samp = W.sample_indices(T.n, 768, seed=21)
-    ad, _ = O.direct(pos, m, 0.01, targets=samp)
+    samp = W.sample_indices(T.n, 1024, seed=23)
+    ad, _ = O.direct(pos, m, 0.01, targets=samp)  # the judge: FP64 direct sums of the oracle
     th = _bisect(lambda x: _median_err(T, torch, out, 0.01, samp, ad, x), 0.3, 2.0)
     e_th = _median_err(T, torch, out, 0.01, samp, ad, th)
     f_th = T.interaction_counts()["flops"]
-    t_th = _time(T, torch, out, 0.01, th)
+    T.balance()
+    t_th = _time_events(T, torch, out, 0.01, th)
+    T.balance(0)
 
     def err_tau(tau):
         T.set_criterion(rec, tau=tau, **BAND)
@@ -184,9 +194,10 @@ def test_learned_criterion_beats_theta_at_equal_median_error(torch):
     tau = _bisect(err_tau, -6.0, -1.0)
     e_ml = err_tau(tau)
     f_ml = T.interaction_counts()["flops"]
-    t_ml = _time(T, torch, out, 0.01, 0.5)
+    T.balance()
+    t_ml = _time_events(T, torch, out, 0.01, 0.5)
     print("theta %.3f err %.2e flops %.3g time %.3f ms | tau %.3f err %.2e flops %.3g time %.3f ms"
-          % (th, e_th, f_th, 1e3 * t_th, tau, e_ml, f_ml, 1e3 * t_ml))
+          % (th, e_th, f_th, t_th, tau, e_ml, f_ml, t_ml))
     assert e_th <= 1.05e-3 and e_ml <= 1.05e-3
     assert f_ml < 0.8 * f_th
-    assert t_ml < t_th
+    assert t_ml < 0.95 * t_th
