@@ -100,7 +100,10 @@ def _load():
         lib.ora_forces_on_lists.argtypes = [C.c_void_p, C.c_int64, _i64p, C.c_int64, _i64p, C.c_int64,
                                             C.c_double, C.c_double, _f64p, _f64p]
         lib.ora_forces_on_lists.restype = None
-        lib.ora_mlp_label_mode.argtypes = [C.c_int]
+        lib.ora_mlp_decide.argtypes = [C.c_void_p, C.c_int64, C.c_int64, _f64p, _f64p, _f64p, _f64p, _f64p,
+                                       C.c_double, C.c_double, C.c_double, C.c_double, C.POINTER(C.c_int),
+                                       C.POINTER(C.c_double)]
+        lib.ora_mlp_decide.restype = C.c_int
         _lib = lib
         return lib
 
@@ -319,6 +322,24 @@ class Tree:
         if nm < 0:
             raise RuntimeError("oracle MLP forces failed")
         return acc, pot, npp, npc, int(nm)
+
+    def mlp_decide(self, g: int, c: int, net: dict, tau: float, theta_lo: float, theta_hi: float,
+                   theta_fb: float):
+        """One decision of the learned criterion for group g and cell c: (open, branch, y).
+
+        branch: 0 the theta_hi test opens, 1 the theta_lo test accepts, 2 a
+        point cell (h = 0) is accepted, 3 a standardised input is out of the
+        training range and the theta_fb test decides, 4 the network decides
+        (y = its FP64 prediction, accept iff y < tau)."""
+        w = np.ascontiguousarray(net["w"], dtype=np.float64)
+        args = [np.ascontiguousarray(net[k], dtype=np.float64) for k in ("mu", "sigma", "fmin", "fmax")]
+        br = C.c_int(0)
+        y = C.c_double(0.0)
+        op = _load().ora_mlp_decide(self._h, int(g), int(c), w, *args, float(tau), float(theta_lo),
+                                    float(theta_hi), float(theta_fb), C.byref(br), C.byref(y))
+        if op < 0:
+            raise ValueError("group or cell index out of range")
+        return bool(op), int(br.value), float(y.value)
 
     def forces_on_lists(self, g: int, cells, leaves, eps: float, G: float = 1.0):
         """O6 for group g's particles (member order) from given cell and leaf lists (cell indices)."""

@@ -69,24 +69,3 @@ def loss_and_grad(w, X, t):
     g["W1"] = dz1.T @ X
     g["b1"] = dz1.sum(0)
     return L, pack(g)
-
-
-def standardise(F):
-    """Per-feature mean and standard deviation of a training set (std floored at 1e-6)."""
-    mu = F.mean(0)
-    sd = np.maximum(F.std(0), 1e-6)
-    return mu, sd
-
-
-def adam_train(w, X, t, steps=2000, batch=4096, lr=3e-3, seed=1, beta1=0.9, beta2=0.999):
-    """Reference Adam training loop (FP64); the product trains on the GPU."""
-    rng = np.random.Generator(np.random.PCG64(seed))
-    m = np.zeros_like(w)
-    v = np.zeros_like(w)
-    for k in range(1, steps + 1):
-        idx = np.floor(rng.random(min(batch, len(t))) * len(t)).astype(np.int64)
-        L, g = loss_and_grad(w, X[idx], t[idx])
-        m = beta1 * m + (1 - beta1) * g
-        v = beta2 * v + (1 - beta2) * g * g
-        w = w - lr * (m / (1 - beta1 ** k)) / (np.sqrt(v / (1 - beta2 ** k)) + 1e-8)
-    return w

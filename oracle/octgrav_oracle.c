@@ -662,14 +662,13 @@ void ora_mlp_features(const ora_tree *T, int64_t g, int64_t c, double *f)
 
 /* Error label of accepting cell c for group g: the largest, over the group's
  * particles i, of |a_multipole(c, i) - a_direct(members of c, i)| / |a_ref(i)|,
- * a_ref the particle's total acceleration (input order, 3 per particle). */
-static int g_label_mean = 0; /* prototype switch: 0 = max over the group, 1 = mean */
-void ora_mlp_label_mode(int mean) { g_label_mean = mean; }
-
+ * a_ref the particle's total acceleration (input order, 3 per particle). The
+ * direct part follows O1: the self term and coincident pairs at eps = 0
+ * (r^2 = 0) are left out. */
 static double mlp_label(const ora_tree *T, int64_t g, int64_t c, double eps2, const double *aref)
 {
     const int64_t gc = T->group[g];
-    double emax = 0, esum = 0;
+    double emax = 0;
     for (int64_t a = T->first[gc]; a < T->first[gc] + T->count[gc]; ++a) {
         const int64_t i = T->idx[a];
         const double *xi = T->pos + 3 * i;
@@ -682,6 +681,7 @@ static double mlp_label(const ora_tree *T, int64_t g, int64_t c, double eps2, co
             const double *xj = T->pos + 3 * j;
             double dx = xj[0] - xi[0], dy = xj[1] - xi[1], dz = xj[2] - xi[2];
             double r2 = dx * dx + dy * dy + dz * dz + eps2;
+            if (r2 == 0.0) continue;
             double rinv = 1.0 / sqrt(r2);
             double mr3 = T->mass[j] * rinv * rinv * rinv;
             ad[0] += mr3 * dx; ad[1] += mr3 * dy; ad[2] += mr3 * dz;
@@ -691,9 +691,8 @@ static double mlp_label(const ora_tree *T, int64_t g, int64_t c, double eps2, co
         double na = sqrt(ar[0] * ar[0] + ar[1] * ar[1] + ar[2] * ar[2]);
         double e = na > 0 ? ea / na : 0;
         if (e > emax) emax = e;
-        esum += e;
     }
-    return g_label_mean ? esum / (double)T->count[gc] : emax;
+    return emax;
 }
 
 /* Training samples: for each listed group, every child tested by a walk with
@@ -786,24 +785,47 @@ double ora_mlp_forward(const double *w, const double *x)
  * accept; otherwise (between the two) a cell with h = 0 is accepted (its
  * monopole is exact), a cell whose standardised features leave [fmin, fmax]
  * uses the FP32 test with theta_fb, and any other is accepted iff the network
- * predicts log10 error < tau. Standardisation: x = (f - mu) / sigma. */
+ * predicts log10 error < tau (a prediction equal to tau opens).
+ * Standardisation: x = (f - mu) / sigma. */
 typedef struct {
     const double *w, *mu, *sigma, *fmin, *fmax; double tau, theta_lo, theta_hi, theta_fb;
 } mlp_rule;
 
-static int mlp_open(const ora_tree *T, int64_t g, int64_t c, const mlp_rule *R, int64_t *n_mlp)
+/* Which rule decided a pair (ora_mlp_decide's *branch). */
+enum { ORA_BR_HI_OPEN = 0, ORA_BR_LO_ACCEPT = 1, ORA_BR_POINT = 2, ORA_BR_FALLBACK = 3, ORA_BR_NETWORK = 4 };
+
+static int mlp_open(const ora_tree *T, int64_t g, int64_t c, const mlp_rule *R, int *branch, double *y)
 {
-    if (open_cell(T, g, c, (float)(R->theta_hi * R->theta_hi))) return 1;
-    if (!open_cell(T, g, c, (float)(R->theta_lo * R->theta_lo))) return 0;
-    if (T->cube[4 * c + 3] == 0) return 0;
+    *y = 0.0;
+    if (open_cell(T, g, c, (float)(R->theta_hi * R->theta_hi))) { *branch = ORA_BR_HI_OPEN; return 1; }
+    if (!open_cell(T, g, c, (float)(R->theta_lo * R->theta_lo))) { *branch = ORA_BR_LO_ACCEPT; return 0; }
+    if (T->cube[4 * c + 3] == 0) { *branch = ORA_BR_POINT; return 0; }
     double f[ORA_NF], x[ORA_NF];
     ora_mlp_features(T, g, c, f);
     for (int i = 0; i < ORA_NF; ++i) {
         x[i] = (f[i] - R->mu[i]) / R->sigma[i];
-        if (!(x[i] >= R->fmin[i] && x[i] <= R->fmax[i])) return open_cell(T, g, c, (float)(R->theta_fb * R->theta_fb));
+        if (!(x[i] >= R->fmin[i] && x[i] <= R->fmax[i])) {
+            *branch = ORA_BR_FALLBACK;
+            return open_cell(T, g, c, (float)(R->theta_fb * R->theta_fb));
+        }
     }
-    if (n_mlp) ++*n_mlp;
-    return !(ora_mlp_forward(R->w, x) < R->tau);
+    *branch = ORA_BR_NETWORK;
+    *y = ora_mlp_forward(R->w, x);
+    return !(*y < R->tau);
+}
+
+/* One decision of the learned criterion, exported for pair-by-pair checks:
+ * returns 1 (open) or 0 (accept), or -1 for a bad group/cell index; *branch
+ * receives the rule that decided (0 theta_hi opens, 1 theta_lo accepts,
+ * 2 point cell h = 0, 3 out of the training range: theta_fb test, 4 network)
+ * and *y the network's prediction (branch 4 only, else 0). */
+int ora_mlp_decide(const ora_tree *T, int64_t g, int64_t c, const double *w, const double *mu,
+                   const double *sigma, const double *fmin, const double *fmax, double tau, double theta_lo,
+                   double theta_hi, double theta_fb, int *branch, double *y)
+{
+    if (g < 0 || g >= T->n_groups || c < 0 || c >= T->n_cells) return -1;
+    mlp_rule R = {w, mu, sigma, fmin, fmax, tau, theta_lo, theta_hi, theta_fb};
+    return mlp_open(T, g, c, &R, branch, y);
 }
 
 typedef struct {
@@ -816,6 +838,7 @@ static void *mlpf_worker(void *arg)
     mlpf_job *J = (mlpf_job *)arg;
     const ora_tree *T = J->T;
     vec cells = {0, 0, 0}, leaves = {0, 0, 0}, stack = {0, 0, 0};
+    int64_t *tmp = NULL; int64_t tcap = 0;
     int64_t nm = 0;
     for (;;) {
         int64_t k = __atomic_fetch_add(&J->next, 1, __ATOMIC_RELAXED);
@@ -828,11 +851,18 @@ static void *mlpf_worker(void *arg)
             for (int o = 0; o < 8; ++o) {
                 int64_t ch = T->child[8 * node + o];
                 if (ch < 0) continue;
-                if (mlp_open(T, g, ch, J->R, &nm)) {
+                int br; double y;
+                if (mlp_open(T, g, ch, J->R, &br, &y)) {
                     if (T->leaf[ch]) vpush(&leaves, ch); else vpush(&stack, ch);
                 } else vpush(&cells, ch);
+                if (br == ORA_BR_NETWORK) ++nm;
             }
         }
+        /* O6 summation order: cell list, then leaf list, each in key order */
+        int64_t need = cells.n > leaves.n ? cells.n : leaves.n;
+        if (need > tcap) { free(tmp); tcap = need; tmp = (int64_t *)malloc(sizeof(int64_t) * (size_t)tcap); }
+        sort_by_key(cells.v, cells.n, T->key, tmp);
+        sort_by_key(leaves.v, leaves.n, T->key, tmp);
         int64_t pp_src = 0;
         for (int64_t l = 0; l < leaves.n; ++l) pp_src += T->count[leaves.v[l]];
         for (int64_t a = T->first[gc]; a < T->first[gc] + T->count[gc]; ++a) {
@@ -851,7 +881,9 @@ static void *mlpf_worker(void *arg)
                     if (j == i) continue;
                     const double *xj = T->pos + 3 * j;
                     double dx = xj[0] - xi[0], dy = xj[1] - xi[1], dz = xj[2] - xi[2];
-                    double rinv = 1.0 / sqrt(dx * dx + dy * dy + dz * dz + J->eps2);
+                    double r2 = dx * dx + dy * dy + dz * dz + J->eps2;
+                    if (r2 == 0.0) continue;
+                    double rinv = 1.0 / sqrt(r2);
                     double mr3 = T->mass[j] * rinv * rinv * rinv;
                     ax += mr3 * dx; ay += mr3 * dy; az += mr3 * dz;
                     phi -= T->mass[j] * rinv;
@@ -864,7 +896,7 @@ static void *mlpf_worker(void *arg)
         }
     }
     __atomic_fetch_add(&J->n_mlp, nm, __ATOMIC_RELAXED);
-    free(cells.v); free(leaves.v); free(stack.v);
+    free(cells.v); free(leaves.v); free(stack.v); free(tmp);
     return NULL;
 }
 
@@ -911,7 +943,9 @@ void ora_forces_on_lists(const ora_tree *T, int64_t g, const int64_t *cells, int
                 if (j == i) continue;
                 const double *xj = T->pos + 3 * j;
                 double dx = xj[0] - xi[0], dy = xj[1] - xi[1], dz = xj[2] - xi[2];
-                double rinv = 1.0 / sqrt(dx * dx + dy * dy + dz * dz + eps2);
+                double r2 = dx * dx + dy * dy + dz * dz + eps2;
+                if (r2 == 0.0) continue;
+                double rinv = 1.0 / sqrt(r2);
                 double mr3 = T->mass[j] * rinv * rinv * rinv;
                 ax += mr3 * dx; ay += mr3 * dy; az += mr3 * dz;
                 phi -= T->mass[j] * rinv;
