@@ -93,17 +93,23 @@ def _load():
         lib.ora_mlp_samples.restype = C.c_int64
         lib.ora_mlp_forward.argtypes = [_f64p, _f64p]
         lib.ora_mlp_forward.restype = C.c_double
+        lib.ora_mlp_forward_bf16.argtypes = [_f64p, _f64p]
+        lib.ora_mlp_forward_bf16.restype = C.c_double
         lib.ora_forces_mlp.argtypes = [C.c_void_p, C.c_double, C.c_double, _f64p, _f64p, _f64p, _f64p, _f64p,
-                                       C.c_double, C.c_double, C.c_double, C.c_double, C.c_void_p, C.c_int64,
-                                       _f64p, _f64p, C.c_void_p, C.c_void_p, C.c_int]
+                                       C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, C.c_void_p,
+                                       C.c_int64, _f64p, _f64p, C.c_void_p, C.c_void_p, C.c_int]
         lib.ora_forces_mlp.restype = C.c_int64
         lib.ora_forces_on_lists.argtypes = [C.c_void_p, C.c_int64, _i64p, C.c_int64, _i64p, C.c_int64,
                                             C.c_double, C.c_double, _f64p, _f64p]
         lib.ora_forces_on_lists.restype = None
         lib.ora_mlp_decide.argtypes = [C.c_void_p, C.c_int64, C.c_int64, _f64p, _f64p, _f64p, _f64p, _f64p,
-                                       C.c_double, C.c_double, C.c_double, C.c_double, C.POINTER(C.c_int),
-                                       C.POINTER(C.c_double)]
+                                       C.c_double, C.c_double, C.c_double, C.c_double, C.c_int,
+                                       C.POINTER(C.c_int), C.POINTER(C.c_double)]
         lib.ora_mlp_decide.restype = C.c_int
+        lib.ora_mlp_decide_many.argtypes = [C.c_void_p, C.c_int64, _i64p, _i64p, _f64p, _f64p, _f64p, _f64p,
+                                            _f64p, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int,
+                                            _i32p, _i32p, _f64p, C.c_void_p]
+        lib.ora_mlp_decide_many.restype = C.c_int
         _lib = lib
         return lib
 
@@ -302,8 +308,9 @@ class Tree:
         return feat, lab, pair
 
     def forces_mlp(self, eps: float, net: dict, tau: float, theta_lo: float, theta_hi: float, theta_fb: float,
-                   G: float = 1.0, groups=None, nthreads: int | None = None):
-        """O6 with the learned criterion: acc, pot, n_pp, n_pc, number of network evaluations."""
+                   G: float = 1.0, groups=None, nthreads: int | None = None, bf16: bool = False):
+        """O6 with the learned criterion: acc, pot, n_pp, n_pc, number of network evaluations.
+        bf16: evaluate the network with BF16 operands (mlp_forward_bf16)."""
         lib = _load()
         acc = np.zeros((self.n, 3))
         pot = np.zeros(self.n)
@@ -317,29 +324,50 @@ class Tree:
         w = np.ascontiguousarray(net["w"], dtype=np.float64)
         args = [np.ascontiguousarray(net[k], dtype=np.float64) for k in ("mu", "sigma", "fmin", "fmax")]
         nm = lib.ora_forces_mlp(self._h, float(eps), float(G), w, *args, float(tau), float(theta_lo),
-                                float(theta_hi), float(theta_fb), gp, ng, acc.reshape(-1), pot, _ptr(npp),
+                                float(theta_hi), float(theta_fb), int(bf16), gp, ng, acc.reshape(-1), pot, _ptr(npp),
                                 _ptr(npc), int(nthreads or default_threads()))
         if nm < 0:
             raise RuntimeError("oracle MLP forces failed")
         return acc, pot, npp, npc, int(nm)
 
     def mlp_decide(self, g: int, c: int, net: dict, tau: float, theta_lo: float, theta_hi: float,
-                   theta_fb: float):
+                   theta_fb: float, bf16: bool = False):
         """One decision of the learned criterion for group g and cell c: (open, branch, y).
 
         branch: 0 the theta_hi test opens, 1 the theta_lo test accepts, 2 a
         point cell (h = 0) is accepted, 3 a standardised input is out of the
         training range and the theta_fb test decides, 4 the network decides
-        (y = its FP64 prediction, accept iff y < tau)."""
+        (y = its prediction, accept iff y < tau; FP64, or with BF16 operands when bf16)."""
         w = np.ascontiguousarray(net["w"], dtype=np.float64)
         args = [np.ascontiguousarray(net[k], dtype=np.float64) for k in ("mu", "sigma", "fmin", "fmax")]
         br = C.c_int(0)
         y = C.c_double(0.0)
         op = _load().ora_mlp_decide(self._h, int(g), int(c), w, *args, float(tau), float(theta_lo),
-                                    float(theta_hi), float(theta_fb), C.byref(br), C.byref(y))
+                                    float(theta_hi), float(theta_fb), int(bf16), C.byref(br), C.byref(y))
         if op < 0:
             raise ValueError("group or cell index out of range")
         return bool(op), int(br.value), float(y.value)
+
+    def mlp_decide_many(self, groups, cells, net: dict, tau: float, theta_lo: float, theta_hi: float,
+                        theta_fb: float, features: bool = False, bf16: bool = False):
+        """mlp_decide for pairs (groups[k], cells[k]): open [n] bool, branch [n], y [n] and, with
+        ``features``, each pair's 12 inputs [n,12] (branches 3 and 4; zeros elsewhere)."""
+        g = np.ascontiguousarray(groups, dtype=np.int64)
+        c = np.ascontiguousarray(cells, dtype=np.int64)
+        n = len(g)
+        if len(c) != n:
+            raise ValueError("groups and cells differ in length")
+        w = np.ascontiguousarray(net["w"], dtype=np.float64)
+        args = [np.ascontiguousarray(net[k], dtype=np.float64) for k in ("mu", "sigma", "fmin", "fmax")]
+        op = np.zeros(n, np.int32)
+        br = np.zeros(n, np.int32)
+        y = np.zeros(n)
+        f = np.zeros((n, 12)) if features else None
+        rc = _load().ora_mlp_decide_many(self._h, n, g, c, w, *args, float(tau), float(theta_lo),
+                                         float(theta_hi), float(theta_fb), int(bf16), op, br, y, _ptr(f))
+        if rc < 0:
+            raise ValueError("group or cell index out of range")
+        return (op.astype(bool), br, y, f) if features else (op.astype(bool), br, y)
 
     def forces_on_lists(self, g: int, cells, leaves, eps: float, G: float = 1.0):
         """O6 for group g's particles (member order) from given cell and leaf lists (cell indices)."""
@@ -362,6 +390,13 @@ class Tree:
 def mlp_forward_c(w, x) -> float:
     """O8 FP64 forward pass (C) of the packed 12-64-64-1 network on one input."""
     return float(_load().ora_mlp_forward(np.ascontiguousarray(w, np.float64), np.ascontiguousarray(x, np.float64)))
+
+
+def mlp_forward_bf16_c(w, x) -> float:
+    """O8 forward pass with BF16 operands (inputs and first hidden layer rounded
+    to BF16 by way of FP32; w must hold BF16 values where they multiply)."""
+    return float(_load().ora_mlp_forward_bf16(np.ascontiguousarray(w, np.float64),
+                                              np.ascontiguousarray(x, np.float64)))
 
 
 def rel_err(a, a_ref):

@@ -366,8 +366,7 @@ void ora_tree_groups(const ora_tree *T, int64_t *group /* n_groups */)
 /* Distance between the group's tight box [gmin, gmax] and the cell's boundary
  * cube (centre c, half side h); the cell is opened iff its side 2h is at least
  * theta times that distance. Returns 1 = open, 0 = accept. */
-int ora_open_f32(const float gmin[3], const float gmax[3], const float c[3], float h,
-                 float theta2)
+static float gap2_f32(const float gmin[3], const float gmax[3], const float c[3], float h)
 {
     float d[3];
     for (int k = 0; k < 3; ++k) {
@@ -376,7 +375,13 @@ int ora_open_f32(const float gmin[3], const float gmax[3], const float c[3], flo
         float t = below > above ? below : above;
         d[k] = t > 0.0f ? t : 0.0f;
     }
-    float d2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
+    return (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
+}
+
+int ora_open_f32(const float gmin[3], const float gmax[3], const float c[3], float h,
+                 float theta2)
+{
+    float d2 = gap2_f32(gmin, gmax, c, h);
     float lhs = 4.0f * (h * h);
     return lhs >= theta2 * d2;
 }
@@ -403,6 +408,19 @@ static int open_cell(const ora_tree *T, int64_t g, int64_t c, float theta2)
         cc[k] = (float)T->cube[4 * c + k];
     }
     return ora_open_f32(gmin, gmax, cc, (float)T->cube[4 * c + 3], theta2);
+}
+
+/* The squared box-to-cube distance exactly as the opening test sees it (FP32). */
+static float cell_gap2_f32(const ora_tree *T, int64_t g, int64_t c)
+{
+    const int64_t gc = T->group[g];
+    float gmin[3], gmax[3], cc[3];
+    for (int k = 0; k < 3; ++k) {
+        gmin[k] = (float)T->bmin[3 * gc + k];
+        gmax[k] = (float)T->bmax[3 * gc + k];
+        cc[k] = (float)T->cube[4 * c + k];
+    }
+    return gap2_f32(gmin, gmax, cc, (float)T->cube[4 * c + 3]);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -697,8 +715,9 @@ static double mlp_label(const ora_tree *T, int64_t g, int64_t c, double eps2, co
 
 /* Training samples: for each listed group, every child tested by a walk with
  * opening parameter theta_walk whose cube has h > 0 and lies at d > 0 from the
- * group box yields (features, label, group, cell). Returns the number of
- * samples (at most cap are written). */
+ * group box yields (features, label, group, cell). h and d are taken as the
+ * FP32 opening test sees them (the only pairs the criterion can be asked
+ * about). Returns the number of samples (at most cap are written). */
 typedef struct {
     const ora_tree *T; const int64_t *groups; int64_t ng; double theta, eps2; const double *aref;
     double *feat, *label; int64_t *pair; int64_t cap; int64_t *offs; int pass; int64_t next;
@@ -713,7 +732,7 @@ static void *samp_worker(void *arg)
     for (;;) {
         int64_t k = __atomic_fetch_add(&J->next, 1, __ATOMIC_RELAXED);
         if (k >= J->ng) break;
-        const int64_t g = J->groups[k], gc = T->group[g];
+        const int64_t g = J->groups[k];
         int64_t cnt = 0, base = J->pass ? J->offs[k] : 0;
         stack.n = 0;
         if (!T->leaf[0]) vpush(&stack, 0);
@@ -723,8 +742,7 @@ static void *samp_worker(void *arg)
                 int64_t ch = T->child[8 * node + o];
                 if (ch < 0) continue;
                 int op = open_cell(T, g, ch, theta2);
-                double d = box_cube_dist(T->bmin + 3 * gc, T->bmax + 3 * gc, T->cube + 4 * ch);
-                if (T->cube[4 * ch + 3] > 0 && d > 0) {
+                if ((float)T->cube[4 * ch + 3] > 0.0f && cell_gap2_f32(T, g, ch) > 0.0f) {
                     if (J->pass) {
                         int64_t s = base + cnt;
                         if (s < J->cap) {
@@ -780,6 +798,45 @@ double ora_mlp_forward(const double *w, const double *x)
     return y;
 }
 
+/* Round to the nearest BF16 value (8 significant bits, ties to even) by way of
+ * FP32, as a tensor core's BF16 operand is made from an FP32 value. */
+static double bf16_round(double v)
+{
+    float f = (float)v;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    if ((u & 0x7f800000u) != 0x7f800000u) { /* finite: round the low 16 bits away */
+        u += 0x7fffu + ((u >> 16) & 1u);
+        u &= 0xffff0000u;
+    }
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+
+/* The network with BF16 operands, the precision of a tensor-core evaluation
+ * with BF16 weights: the inputs and the first hidden layer are rounded to
+ * BF16 before they are multiplied (the weights w must already be BF16
+ * values); sums, biases, the second hidden layer and the output stay exact
+ * up to FP64. */
+double ora_mlp_forward_bf16(const double *w, const double *x)
+{
+    const double *W1 = w, *b1 = w + ORA_NH * ORA_NF, *W2 = b1 + ORA_NH, *b2 = W2 + ORA_NH * ORA_NH;
+    const double *w3 = b2 + ORA_NH, *b3 = w3 + ORA_NH;
+    double xr[ORA_NF], h1[ORA_NH], y = *b3;
+    for (int i = 0; i < ORA_NF; ++i) xr[i] = bf16_round(x[i]);
+    for (int j = 0; j < ORA_NH; ++j) {
+        double s = b1[j];
+        for (int i = 0; i < ORA_NF; ++i) s += W1[j * ORA_NF + i] * xr[i];
+        h1[j] = bf16_round(s > 0 ? s : 0);
+    }
+    for (int j = 0; j < ORA_NH; ++j) {
+        double s = b2[j];
+        for (int i = 0; i < ORA_NH; ++i) s += W2[j * ORA_NH + i] * h1[i];
+        y += w3[j] * (s > 0 ? s : 0);
+    }
+    return y;
+}
+
 /* The learned criterion's decision for group g and child c (1 = open):
  * the FP32 opening test with theta_hi opens -> open; with theta_lo accepts ->
  * accept; otherwise (between the two) a cell with h = 0 is accepted (its
@@ -789,6 +846,7 @@ double ora_mlp_forward(const double *w, const double *x)
  * Standardisation: x = (f - mu) / sigma. */
 typedef struct {
     const double *w, *mu, *sigma, *fmin, *fmax; double tau, theta_lo, theta_hi, theta_fb;
+    int bf16; /* 1: the network with BF16 operands (ora_mlp_forward_bf16) */
 } mlp_rule;
 
 /* Which rule decided a pair (ora_mlp_decide's *branch). */
@@ -799,7 +857,7 @@ static int mlp_open(const ora_tree *T, int64_t g, int64_t c, const mlp_rule *R, 
     *y = 0.0;
     if (open_cell(T, g, c, (float)(R->theta_hi * R->theta_hi))) { *branch = ORA_BR_HI_OPEN; return 1; }
     if (!open_cell(T, g, c, (float)(R->theta_lo * R->theta_lo))) { *branch = ORA_BR_LO_ACCEPT; return 0; }
-    if (T->cube[4 * c + 3] == 0) { *branch = ORA_BR_POINT; return 0; }
+    if ((float)T->cube[4 * c + 3] == 0.0f) { *branch = ORA_BR_POINT; return 0; }
     double f[ORA_NF], x[ORA_NF];
     ora_mlp_features(T, g, c, f);
     for (int i = 0; i < ORA_NF; ++i) {
@@ -810,7 +868,7 @@ static int mlp_open(const ora_tree *T, int64_t g, int64_t c, const mlp_rule *R, 
         }
     }
     *branch = ORA_BR_NETWORK;
-    *y = ora_mlp_forward(R->w, x);
+    *y = R->bf16 ? ora_mlp_forward_bf16(R->w, x) : ora_mlp_forward(R->w, x);
     return !(*y < R->tau);
 }
 
@@ -818,14 +876,37 @@ static int mlp_open(const ora_tree *T, int64_t g, int64_t c, const mlp_rule *R, 
  * returns 1 (open) or 0 (accept), or -1 for a bad group/cell index; *branch
  * receives the rule that decided (0 theta_hi opens, 1 theta_lo accepts,
  * 2 point cell h = 0, 3 out of the training range: theta_fb test, 4 network)
- * and *y the network's prediction (branch 4 only, else 0). */
+ * and *y the network's prediction (branch 4 only, else 0); bf16 = 1 evaluates
+ * the network with BF16 operands (ora_mlp_forward_bf16). */
 int ora_mlp_decide(const ora_tree *T, int64_t g, int64_t c, const double *w, const double *mu,
                    const double *sigma, const double *fmin, const double *fmax, double tau, double theta_lo,
-                   double theta_hi, double theta_fb, int *branch, double *y)
+                   double theta_hi, double theta_fb, int bf16, int *branch, double *y)
 {
     if (g < 0 || g >= T->n_groups || c < 0 || c >= T->n_cells) return -1;
-    mlp_rule R = {w, mu, sigma, fmin, fmax, tau, theta_lo, theta_hi, theta_fb};
+    mlp_rule R = {w, mu, sigma, fmin, fmax, tau, theta_lo, theta_hi, theta_fb, bf16};
     return mlp_open(T, g, c, &R, branch, y);
+}
+
+/* ora_mlp_decide for n pairs (groups[k], cells[k]): open[k], branch[k], y[k];
+ * feat (n x 12, may be NULL) receives each pair's inputs where the rule
+ * computed them (branches 3 and 4; zeros elsewhere). Returns 0, or -1 for a
+ * bad index (outputs of later pairs are then unset). */
+int ora_mlp_decide_many(const ora_tree *T, int64_t n, const int64_t *groups, const int64_t *cells,
+                        const double *w, const double *mu, const double *sigma, const double *fmin,
+                        const double *fmax, double tau, double theta_lo, double theta_hi, double theta_fb,
+                        int bf16, int *open, int *branch, double *y, double *feat)
+{
+    mlp_rule R = {w, mu, sigma, fmin, fmax, tau, theta_lo, theta_hi, theta_fb, bf16};
+    for (int64_t k = 0; k < n; ++k) {
+        const int64_t g = groups[k], c = cells[k];
+        if (g < 0 || g >= T->n_groups || c < 0 || c >= T->n_cells) return -1;
+        open[k] = mlp_open(T, g, c, &R, &branch[k], &y[k]);
+        if (feat) {
+            if (branch[k] >= ORA_BR_FALLBACK) ora_mlp_features(T, g, c, feat + ORA_NF * k);
+            else memset(feat + ORA_NF * k, 0, sizeof(double) * ORA_NF);
+        }
+    }
+    return 0;
 }
 
 typedef struct {
@@ -901,14 +982,14 @@ static void *mlpf_worker(void *arg)
 }
 
 /* Tree forces with the learned criterion (see mlp_open); arguments as
- * ora_forces plus the network and its thresholds. Returns the number of
- * network evaluations, or -1. */
+ * ora_forces plus the network, its thresholds and its precision (bf16 as for
+ * ora_mlp_decide). Returns the number of network evaluations, or -1. */
 int64_t ora_forces_mlp(const ora_tree *T, double eps, double G, const double *w, const double *mu,
                        const double *sigma, const double *fmin, const double *fmax, double tau, double theta_lo,
-                       double theta_hi, double theta_fb, const int64_t *groups, int64_t ng, double *acc,
-                       double *pot, int64_t *npp, int64_t *npc, int nthreads)
+                       double theta_hi, double theta_fb, int bf16, const int64_t *groups, int64_t ng,
+                       double *acc, double *pot, int64_t *npp, int64_t *npc, int nthreads)
 {
-    mlp_rule R = {w, mu, sigma, fmin, fmax, tau, theta_lo, theta_hi, theta_fb};
+    mlp_rule R = {w, mu, sigma, fmin, fmax, tau, theta_lo, theta_hi, theta_fb, bf16};
     mlpf_job J;
     memset(&J, 0, sizeof J);
     J.T = T; J.eps2 = eps * eps; J.G = G; J.R = &R;

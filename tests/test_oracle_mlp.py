@@ -95,3 +95,43 @@ def test_labels_fall_with_distance_as_expansion_error():
         labels.append(L[list(P[:, 1]).index(c)])
     slope = np.polyfit(np.log(ds), np.log(labels), 1)[0]
     assert -5.4 < slope < -4.6               # (l/d)^3 * M/d^2 -> d^-5 absolute
+
+
+def _one_unit(w1, b1, w2, b2, w3, b3):
+    """Network with one active unit per layer: unit 5 of layer 1 reads input 2,
+    unit 9 of layer 2 reads unit 5, the output reads unit 9."""
+    p = {k: np.zeros(s) for k, s in M.SIZES}
+    p["W1"][5, 2], p["b1"][5] = w1, b1
+    p["W2"][9, 5], p["b2"][9] = w2, b2
+    p["w3"][9], p["b3"][0] = w3, b3
+    return M.pack(p)
+
+
+def test_bf16_forward_equals_fp64_on_bf16_values():
+    """Where every operand is a BF16 value the rounding changes nothing."""
+    w = _one_unit(2.0, -1.0, 3.0, 0.5, -4.0, 0.25)
+    for xv, y in ((1.5, -25.75), (0.25, -1.75)):
+        x = np.zeros(12)
+        x[2] = xv
+        assert O.mlp_forward_bf16_c(w, x) == y == O.mlp_forward_c(w, x)
+
+
+def test_bf16_forward_rounds_inputs_and_hidden_layer_by_hand():
+    """BF16 keeps 8 significant bits: near 1 the spacing is 2^-7, so
+    1 + 2^-9 rounds to 1, the midpoint 1 + 2^-8 rounds to the even 1, and the
+    midpoint 1 + 3 * 2^-8 rounds to the even 1 + 2^-6."""
+    w = _one_unit(1.0, 0.0, 1.0, 0.0, 1.0, 0.0)    # y = relu(relu(x))
+    x = np.zeros(12)
+    for xv, y in ((1 + 2.0 ** -9, 1.0), (1 + 2.0 ** -8, 1.0), (1 + 3 * 2.0 ** -8, 1 + 2.0 ** -6),
+                  (1 + 2.0 ** -7, 1 + 2.0 ** -7)):
+        x[2] = xv
+        assert O.mlp_forward_bf16_c(w, x) == y, xv
+        assert O.mlp_forward_c(w, x) == xv
+    # the first hidden layer is rounded: z1 = 1 + 2^-9 -> 1; the second is not:
+    # z2 = 1 + 2^-9 stays
+    x[2] = 1.0
+    assert O.mlp_forward_bf16_c(_one_unit(1.0, 2.0 ** -9, 1.0, 0.0, 1.0, 0.0), x) == 1.0
+    assert O.mlp_forward_bf16_c(_one_unit(1.0, 0.0, 1.0, 2.0 ** -9, 1.0, 0.0), x) == 1 + 2.0 ** -9
+    # 1/3 = 1.0101010|101... * 2^-2 rounds up to 1.0101011 * 2^-2 = 171 / 512
+    x[2] = 1.0 / 3.0
+    assert O.mlp_forward_bf16_c(w, x) == 171.0 / 512.0

@@ -278,3 +278,20 @@ def test_mlp_decide_reports_its_branches(tree):
     assert seen == {0, 1, 2, 3, 4}
     with pytest.raises(ValueError):
         T.mlp_decide(0, T.n_cells, net, tau, 0.45, 1.2, 0.7)
+
+
+def test_mlp_decide_many_equals_single_decisions(tree):
+    """The batched decision call gives each pair's single-call result, and the
+    inputs it reports are the pair's features."""
+    T = tree
+    net = _open_net(6)
+    net["fmax"][3] = 0.8
+    rng = np.random.default_rng(1)
+    g = rng.integers(0, T.n_groups, 400)
+    c = rng.integers(1, T.n_cells, 400)
+    op, br, y, f = T.mlp_decide_many(g, c, net, 0.0, 0.45, 1.2, 0.7, features=True)
+    for k in range(400):
+        assert (op[k], br[k], y[k]) == T.mlp_decide(int(g[k]), int(c[k]), net, 0.0, 0.45, 1.2, 0.7)
+        if br[k] >= 3:
+            np.testing.assert_array_equal(f[k], T.mlp_features(int(g[k]), int(c[k])))
+    assert set(br.tolist()) >= {0, 1, 3, 4}
