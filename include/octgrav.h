@@ -196,6 +196,29 @@ int octgrav_forces_tree_device64(octgrav_tree *t, double eps, double theta, doub
 int octgrav_forces_gpu(const double *pos, const double *mass, int64_t n, double eps, double theta,
                        double G, int n_leaf, int n_group, double *acc, double *pot, void *stream);
 
+/* One-shot call for many independent systems (the paper's "convenient user
+ * interface", Sec. 1 and the abstract, in its batched form): HOST arrays in,
+ * HOST FP64 results out, both in input order. System s owns particles
+ * offsets[s] .. offsets[s+1]-1 of pos (n x 3) and mass (n), n = offsets[n_sys]
+ * (offsets: n_sys + 1 entries, offsets[0] = 0, strictly increasing), and is
+ * evaluated with its own softening eps[s] > 0 and opening parameter
+ * theta[s] >= 0 (arrays of n_sys entries). acc (n x 3) and pot (n, may be NULL)
+ * receive the results. The systems are copied to the device, their octrees
+ * built on the GPU (octgrav_build_batch_gpu), walked and evaluated by one
+ * persistent launch, unpermuted on the device and copied back; the call
+ * returns after the copies. Device buffers are cached per calling thread (its
+ * current device), as in octgrav_forces_gpu. Defaults: G = 1, N_leaf = 16,
+ * N_group = 256 (the group size the autotuner picks for systems of 10^3 to
+ * 10^5 particles); octgrav_forces_batched_ex takes every knob. Errors: ERR_ARG
+ * (NULL, offsets, a bad eps/theta), ERR_NONFINITE (found on the device),
+ * ERR_OOM, ERR_CUDA and the launch statuses. */
+int octgrav_forces_batched(int n_sys, const int64_t *offsets, const double *pos, const double *mass,
+                           const double *eps, const double *theta, double *acc, double *pot,
+                           void *stream);
+int octgrav_forces_batched_ex(int n_sys, const int64_t *offsets, const double *pos,
+                              const double *mass, const double *eps, const double *theta, double G,
+                              int n_leaf, int n_group, double *acc, double *pot, void *stream);
+
 /* Direct Plummer-softened summation in FP64 on the GPU at nt target
  * particles (the exact reference of the error measure Delta a / a, Sec. 3.1):
  * targets[k] indexes pos/mass (HOST arrays, n particles); NULL targets means
@@ -294,6 +317,23 @@ int octgrav_interaction_counts(octgrav_tree *t, int64_t *out, void *stream);
 int octgrav_debug_lists(octgrav_tree *t, double theta, int cap, uint64_t *cell_keys,
                         int32_t *n_cell, uint64_t *leaf_keys, int32_t *n_leaf, void *stream);
 
+/* Test hook with a choice of work items, for trees too large to capture whole:
+ * like octgrav_debug_lists, but row r of every output belongs to work item
+ * items[r] (n_sel distinct indices in [0, n_items); items == NULL captures
+ * every item, row = item). With the learned criterion (octgrav_set_criterion)
+ * and net_cap > 0 it also records, per row, every candidate that reached the
+ * network step (Sec. 2.2's opening test replaced by the network inside the
+ * band): net_keys[r*net_cap + e] = the cell's key, net_y[...] = the network's
+ * FP32 prediction, or NaN where a standardised input left the training range
+ * and the theta_fb test decided; n_net[r] = their number. Candidates are
+ * recorded in the order the walk met them. net_cap = 0 records none (net_*
+ * may then be NULL). Truncation (a list or a candidate record longer than its
+ * cap) returns ERR_LIST after filling what fits. Synchronous. Errors: ERR_ARG,
+ * ERR_LIST, ERR_OOM, ERR_CUDA and the launch statuses. */
+int octgrav_debug_walk(octgrav_tree *t, double theta, int64_t n_sel, const int64_t *items, int cap,
+                       uint64_t *cell_keys, int32_t *n_cell, uint64_t *leaf_keys, int32_t *n_leaf,
+                       int net_cap, uint64_t *net_keys, float *net_y, int32_t *n_net, void *stream);
+
 /* Order in which later launches on this tree take the work items (the
  * persistent kernel's tail is shorter when the biggest items go first).
  * Every new tree (and every octgrav_set_launch that rebuilds the items)
@@ -364,7 +404,10 @@ int octgrav_mlp_samples(octgrav_tree *t, const int64_t *groups, int64_t n_groups
 /* Train the criterion's network on the GPU (FP32 forward/backward, Adam, mini-
  * batches drawn by a counter-based generator from seed) on log10 of the
  * labels, with inputs standardised over the samples. Writes the record
- * (OCTGRAV_MLP_RECORD floats) and the last mini-batch loss. Synchronous. */
+ * (OCTGRAV_MLP_RECORD floats; its input range is that of the standardised
+ * samples widened by 1e-3 on each side, so that inputs equal to a training
+ * extreme count as in range however they are rounded) and the last
+ * mini-batch loss. Synchronous. */
 int octgrav_mlp_train(const float *features, const float *labels, int64_t n, int steps, int batch,
                       double lr, uint64_t seed, float *record, float *final_loss, void *stream);
 
@@ -422,11 +465,18 @@ void octgrav_free_tree(octgrav_tree *t);
  * allocator) owns every device byte, or a time-step loop that must not suffer
  * the device-wide synchronisation that cudaMalloc/cudaFree can cause. The
  * call makes no cudaMalloc, cudaFree or other allocating call.
- *   arena: caller-allocated device memory that receives the tree's device
- *     arrays (copied from the tree's host images on stream). Call once with
- *     arena = NULL to get the size needed in *arena_bytes; otherwise
- *     *arena_bytes is the arena's size and must be at least that.
+ *   arena: caller-allocated device memory (256-byte aligned) that receives the
+ *     tree's device arrays, copied on stream: device to device from a
+ *     GPU-built tree (which must live on the current device), from the host
+ *     images of a host-built one. Call once with arena = NULL to get the size
+ *     needed in *arena_bytes; otherwise *arena_bytes is the arena's size and
+ *     must be at least that.
  *   acc4_dev, eps, theta, G, stream: as octgrav_forces_device (tree order).
+ * The tree's settings apply as in octgrav_forces_device -- staging mode,
+ * particles per lane, per-system parameters and the learned criterion (whose
+ * network stays in the tree's device memory; set it on the current device) --
+ * except the list split of octgrav_set_split, which needs a per-part output
+ * buffer: these launches run unsplit and round like an unsplit launch.
  * The status word, work-queue counter and per-item counts live in a
  * fixed-size array inside the library (2 MiB + 256 B per GPU, kept until the
  * process exits), so the tree may have at most OCTGRAV_NOALLOC_MAX_ITEMS work

@@ -288,7 +288,8 @@ int split_parts(const octgrav_tree* t, bool capture) {
 }
 
 int launch(octgrav_tree* t, double eps, double theta, double G, float4* out, cudaStream_t st,
-           bool capture, int* dbg_cell, int* dbg_leaf, int2* dbg_n, int dbg_cap) {
+           const CaptureArgs* cap) {
+  const bool capture = cap != nullptr;
   int rc = check_params(eps, theta, G);
   if (rc) return rc;
   if (!t->uploaded || t->sysp_dirty) {
@@ -301,10 +302,14 @@ int launch(octgrav_tree* t, double eps, double theta, double G, float4* out, cud
   og::KParams p = make_params(t, out);
   p.sys0 = make_float4(static_cast<float>(theta * theta), static_cast<float>(eps * eps), static_cast<float>(G), 0.f);
   if (capture) {
-    p.dbg_cell = dbg_cell;
-    p.dbg_leaf = dbg_leaf;
-    p.dbg_n = dbg_n;
-    p.dbg_cap = dbg_cap;
+    p.dbg_cell = cap->cell;
+    p.dbg_leaf = cap->leaf;
+    p.dbg_n = cap->n;
+    p.dbg_cap = cap->cap;
+    p.dbg_slot = cap->slot;
+    p.dbg_net = cap->net;
+    p.dbg_net_n = cap->net_n;
+    p.dbg_net_cap = cap->net_cap;
   }
   CUDA_TRY(cudaMemsetAsync(t->dev->ctl.p, 0, 8, st));
   const int nparts = split_parts(t, capture);
@@ -363,7 +368,7 @@ int forces_dev64(octgrav_tree* t, double eps, double theta, double G, double* ac
   if ((rc = t->dev->out.reserve(sizeof(float4) * t->n))) return rc;
   if ((rc = device_perm(t, st))) return rc;
   if (ev) CUDA_TRY(cudaEventRecord(ev[1], st));
-  if ((rc = launch(t, eps, theta, G, static_cast<float4*>(t->dev->out.p), st, false, nullptr, nullptr, nullptr, 0)))
+  if ((rc = launch(t, eps, theta, G, static_cast<float4*>(t->dev->out.p), st)))
     return rc;
   if (ev) CUDA_TRY(cudaEventRecord(ev[2], st));
   cudaError_t e = og::gpu_unpermute(static_cast<const float4*>(t->dev->out.p), static_cast<const int*>(t->dev->perm.p),
@@ -706,8 +711,7 @@ int octgrav_forces_device(octgrav_tree* t, double eps, double theta, double G, f
   if (!t || !acc4_dev) return fail(OCTGRAV_ERR_ARG, "NULL tree or output");
   int rc = check_params(eps, theta, G);
   if (rc) return rc;
-  return launch(t, eps, theta, G, reinterpret_cast<float4*>(acc4_dev), static_cast<cudaStream_t>(stream), false,
-                nullptr, nullptr, nullptr, 0);
+  return launch(t, eps, theta, G, reinterpret_cast<float4*>(acc4_dev), static_cast<cudaStream_t>(stream));
 }
 
 int octgrav_set_system_params(octgrav_tree* t, const double* eps, const double* theta) {
@@ -832,6 +836,43 @@ int octgrav_forces_gpu(const double* pos, const double* mass, int64_t n, double 
   rc = forces_host(t, eps, theta, G, acc, pot, st);
   octgrav_free_tree(t);
   return rc;
+}
+
+int octgrav_forces_batched_ex(int n_sys, const int64_t* offsets, const double* pos, const double* mass,
+                              const double* eps, const double* theta, double G, int n_leaf, int n_group,
+                              double* acc, double* pot, void* stream) {
+  if (n_sys < 1 || !offsets || !pos || !mass || !eps || !theta || !acc)
+    return fail(OCTGRAV_ERR_ARG, "NULL input or output, or n_sys < 1");
+  if (offsets[0] != 0) return fail(OCTGRAV_ERR_ARG, "offsets[0] must be 0");
+  for (int s = 0; s < n_sys; ++s) {
+    if (offsets[s + 1] <= offsets[s]) return fail(OCTGRAV_ERR_ARG, "empty or decreasing system %d", s);
+    int rc = check_params(eps[s], theta[s], G);
+    if (rc) return rc;
+  }
+  const int64_t n = offsets[n_sys];
+  if (n >= (1ll << 31) - 64) return fail(OCTGRAV_ERR_ARG, "too many particles");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Device& D = tl_device.get();
+  int cur = 0;
+  CUDA_TRY(cudaGetDevice(&cur));
+  if (D.device >= 0 && D.device != cur) D.release();
+  D.device = cur;
+  int rc;
+  if ((rc = D.in_pos.reserve(24 * n)) || (rc = D.in_mass.reserve(8 * n))) return rc;
+  CUDA_TRY(cudaMemcpyAsync(D.in_pos.p, pos, 24 * n, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(D.in_mass.p, mass, 8 * n, cudaMemcpyHostToDevice, st));
+  octgrav_tree* t = nullptr;
+  if ((rc = build_gpu_common(n_sys, offsets, static_cast<const double*>(D.in_pos.p),
+                             static_cast<const double*>(D.in_mass.p), n_leaf, n_group, st, &D, &t)))
+    return rc;
+  if (!(rc = octgrav_set_system_params(t, eps, theta))) rc = forces_host(t, eps[0], theta[0], G, acc, pot, st);
+  octgrav_free_tree(t);
+  return rc;
+}
+
+int octgrav_forces_batched(int n_sys, const int64_t* offsets, const double* pos, const double* mass,
+                           const double* eps, const double* theta, double* acc, double* pot, void* stream) {
+  return octgrav_forces_batched_ex(n_sys, offsets, pos, mass, eps, theta, 1.0, 16, 256, acc, pot, stream);
 }
 
 int octgrav_direct(const double* pos, const double* mass, int64_t n, const int64_t* targets, int64_t nt,
@@ -1079,41 +1120,93 @@ int octgrav_interaction_counts(octgrav_tree* t, int64_t* out, void* stream) {
   return OCTGRAV_OK;
 }
 
-int octgrav_debug_lists(octgrav_tree* t, double theta, int cap, uint64_t* cell_keys, int32_t* n_cell,
-                        uint64_t* leaf_keys, int32_t* n_leaf, void* stream) {
-  if (!t || cap < 1 || !cell_keys || !n_cell || !leaf_keys || !n_leaf) return fail(OCTGRAV_ERR_ARG, "bad argument");
+int octgrav_debug_walk(octgrav_tree* t, double theta, int64_t n_sel, const int64_t* items, int cap,
+                       uint64_t* cell_keys, int32_t* n_cell, uint64_t* leaf_keys, int32_t* n_leaf, int net_cap,
+                       uint64_t* net_keys, float* net_y, int32_t* n_net, void* stream) {
+  if (!t || cap < 1 || !cell_keys || !n_cell || !leaf_keys || !n_leaf || net_cap < 0 ||
+      (net_cap > 0 && (!net_keys || !net_y || !n_net)))
+    return fail(OCTGRAV_ERR_ARG, "bad argument");
   int rc = check_params(1.0, theta, 1.0);
   if (rc) return rc;
   if ((rc = host_images(t))) return rc;
+  const int64_t ni = static_cast<int64_t>(t->items.size());
+  const int64_t ns = items ? n_sel : ni;
+  if (ns < 0) return fail(OCTGRAV_ERR_ARG, "n_sel < 0");
+  std::vector<int> slot;
+  if (items) {
+    slot.assign(static_cast<size_t>(ni), -1);
+    for (int64_t r = 0; r < ns; ++r) {
+      if (items[r] < 0 || items[r] >= ni) return fail(OCTGRAV_ERR_ARG, "item %lld out of range", (long long)items[r]);
+      if (slot[items[r]] >= 0) return fail(OCTGRAV_ERR_ARG, "item %lld listed twice", (long long)items[r]);
+      slot[items[r]] = static_cast<int>(r);
+    }
+  }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const size_t ni = t->items.size();
   if (!t->uploaded || t->sysp_dirty) {
     if ((rc = upload(t, st))) return rc;
   }
   if ((rc = t->dev->out.reserve(sizeof(float4) * t->n))) return rc;
-  const size_t bytes = ni * cap * 8 + ni * sizeof(int2);
+  const size_t zs = static_cast<size_t>(ns), zc = static_cast<size_t>(cap), zn = static_cast<size_t>(net_cap);
+  const size_t bytes = zs * zc * 8 + zs * sizeof(int2) + zs * zn * sizeof(int2) + zs * 4 + slot.size() * 4 + 64;
   if ((rc = t->dev->dbg.reserve(bytes))) return rc;
-  int* dcell = static_cast<int*>(t->dev->dbg.p);
-  int* dleaf = dcell + ni * cap;
-  int2* dn = reinterpret_cast<int2*>(dleaf + ni * cap);
-  if ((rc = launch(t, 1.0, theta, 1.0, static_cast<float4*>(t->dev->out.p), st, true, dcell, dleaf, dn, cap)))
-    return rc;
-  std::vector<int> hc(ni * cap), hl(ni * cap);
-  std::vector<int2> hn(ni);
-  CUDA_TRY(cudaMemcpyAsync(hc.data(), dcell, 4 * ni * cap, cudaMemcpyDeviceToHost, st));
-  CUDA_TRY(cudaMemcpyAsync(hl.data(), dleaf, 4 * ni * cap, cudaMemcpyDeviceToHost, st));
-  CUDA_TRY(cudaMemcpyAsync(hn.data(), dn, sizeof(int2) * ni, cudaMemcpyDeviceToHost, st));
+  CaptureArgs ca;
+  ca.cell = static_cast<int*>(t->dev->dbg.p);
+  ca.leaf = ca.cell + zs * zc;
+  ca.n = reinterpret_cast<int2*>(ca.leaf + zs * zc);
+  ca.cap = cap;
+  ca.net = ca.n + zs;
+  ca.net_n = reinterpret_cast<int*>(ca.net + zs * zn);
+  ca.net_cap = net_cap;
+  int* dslot = ca.net_n + zs;
+  if (!items) {
+    ca.slot = nullptr;
+  } else {
+    ca.slot = dslot;
+    if (!slot.empty()) CUDA_TRY(cudaMemcpyAsync(dslot, slot.data(), 4 * slot.size(), cudaMemcpyHostToDevice, st));
+  }
+  if (zs) CUDA_TRY(cudaMemsetAsync(ca.net_n, 0, 4 * zs, st));
+  if (net_cap == 0) ca.net = nullptr, ca.net_n = nullptr;
+  if ((rc = launch(t, 1.0, theta, 1.0, static_cast<float4*>(t->dev->out.p), st, &ca))) return rc;
+  std::vector<int> hc(zs * zc), hl(zs * zc), hnn(zs);
+  std::vector<int2> hn(zs), hnet(zs * zn);
+  if (zs) {
+    CUDA_TRY(cudaMemcpyAsync(hc.data(), ca.cell, 4 * zs * zc, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(hl.data(), ca.leaf, 4 * zs * zc, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(hn.data(), ca.n, sizeof(int2) * zs, cudaMemcpyDeviceToHost, st));
+    if (net_cap > 0) {
+      CUDA_TRY(cudaMemcpyAsync(hnet.data(), ca.net, sizeof(int2) * zs * zn, cudaMemcpyDeviceToHost, st));
+      CUDA_TRY(cudaMemcpyAsync(hnn.data(), ca.net_n, 4 * zs, cudaMemcpyDeviceToHost, st));
+    }
+  }
   if ((rc = read_status(t, st))) return rc;
   bool trunc = false;
-  for (size_t k = 0; k < ni; ++k) {
+  for (size_t k = 0; k < zs; ++k) {
     n_cell[k] = hn[k].x;
     n_leaf[k] = hn[k].y;
     trunc |= hn[k].x > cap || hn[k].y > cap;
-    for (int e = 0; e < std::min(cap, hn[k].x); ++e) cell_keys[k * cap + e] = t->key[hc[k * cap + e]];
-    for (int e = 0; e < std::min(cap, hn[k].y); ++e) leaf_keys[k * cap + e] = t->key[hl[k * cap + e]];
+    for (int e = 0; e < std::min(cap, hn[k].x); ++e) cell_keys[k * zc + e] = t->key[hc[k * zc + e]];
+    for (int e = 0; e < std::min(cap, hn[k].y); ++e) leaf_keys[k * zc + e] = t->key[hl[k * zc + e]];
+    if (net_cap > 0) {
+      n_net[k] = hnn[k];
+      trunc |= hnn[k] > net_cap;
+      for (int e = 0; e < std::min(net_cap, hnn[k]); ++e) {
+        const int2 v = hnet[k * zn + e];
+        const bool in_range = v.x >= 0;
+        net_keys[k * zn + e] = t->key[in_range ? v.x : ~v.x];
+        float y;
+        std::memcpy(&y, &v.y, 4);
+        net_y[k * zn + e] = in_range ? y : NAN;
+      }
+    }
   }
-  if (trunc) return fail(OCTGRAV_ERR_LIST, "a list was longer than cap = %d", cap);
+  if (trunc) return fail(OCTGRAV_ERR_LIST, "a list was longer than its capture buffer");
   return OCTGRAV_OK;
+}
+
+int octgrav_debug_lists(octgrav_tree* t, double theta, int cap, uint64_t* cell_keys, int32_t* n_cell,
+                        uint64_t* leaf_keys, int32_t* n_leaf, void* stream) {
+  return octgrav_debug_walk(t, theta, 0, nullptr, cap, cell_keys, n_cell, leaf_keys, n_leaf, 0, nullptr, nullptr,
+                            nullptr, stream);
 }
 
 int octgrav_balance(octgrav_tree* t, int mode, void* stream) {
@@ -1178,11 +1271,14 @@ int octgrav_set_launch(octgrav_tree* t, int particles_per_lane, int ctas_per_sm)
 int octgrav_forces_noalloc(octgrav_tree* t, void* arena, size_t* arena_bytes, double eps, double theta,
                            double G, float* acc4_dev, void* stream) {
   if (!t || !arena_bytes) return fail(OCTGRAV_ERR_ARG, "NULL tree or arena_bytes");
-  if (int rc = host_images(t)) return rc;
+  // a GPU-built tree is copied device to device from its own arrays; a
+  // host-built one from its host images
+  const bool from_device = t->gpu;
+  const size_t n = static_cast<size_t>(t->n), nc = static_cast<size_t>(t->n_cells),
+               ni = static_cast<size_t>(t->n_items);
   // arena layout: the device arrays, each starting on a 256-byte boundary
-  const size_t sizes[7] = {t->parts.size() * sizeof(float4), t->geo.size() * sizeof(float4),
-                           t->link.size() * sizeof(int2),    t->mp.size() * sizeof(float4),
-                           t->items.size() * sizeof(int4),   t->ibox.size() * sizeof(float4),
+  const size_t sizes[7] = {2 * n * sizeof(float4), nc * sizeof(float4),     nc * sizeof(int2),
+                           4 * nc * sizeof(float4), ni * sizeof(int4),      4 * ni * sizeof(float4),
                            t->sysp.size() * sizeof(float4)};
   size_t offs[7], total = 0;
   for (int k = 0; k < 7; ++k) {
@@ -1196,18 +1292,32 @@ int octgrav_forces_noalloc(octgrav_tree* t, void* arena, size_t* arena_bytes, do
   if (*arena_bytes < total)
     return fail(OCTGRAV_ERR_ARG, "arena of %zu bytes is smaller than the %zu bytes needed", *arena_bytes, total);
   if (reinterpret_cast<uintptr_t>(arena) % 256) return fail(OCTGRAV_ERR_ARG, "arena must be 256-byte aligned");
-  if (t->items.size() > static_cast<size_t>(OCTGRAV_NOALLOC_MAX_ITEMS))
-    return fail(OCTGRAV_ERR_ARG, "tree has %zu work items; the allocation-free path takes at most %d",
-                t->items.size(), OCTGRAV_NOALLOC_MAX_ITEMS);
+  if (ni > static_cast<size_t>(OCTGRAV_NOALLOC_MAX_ITEMS))
+    return fail(OCTGRAV_ERR_ARG, "tree has %zu work items; the allocation-free path takes at most %d", ni,
+                OCTGRAV_NOALLOC_MAX_ITEMS);
   if (!acc4_dev) return fail(OCTGRAV_ERR_ARG, "NULL output");
   int rc = check_params(eps, theta, G);
   if (rc) return rc;
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (from_device && t->dev->device != dev)
+    return fail(OCTGRAV_ERR_STATE, "tree was built on device %d, current is %d", t->dev->device, dev);
+  if (t->learned && t->mlp_device != dev)
+    return fail(OCTGRAV_ERR_STATE, "the learned criterion was set on device %d, current is %d", t->mlp_device, dev);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   char* a = static_cast<char*>(arena);
-  const void* src[7] = {t->parts.data(), t->geo.data(), t->link.data(), t->mp.data(),
-                        t->items.data(), t->ibox.data(), t->sysp.data()};
-  for (int k = 0; k < 7; ++k)
-    if (sizes[k]) CUDA_TRY(cudaMemcpyAsync(a + offs[k], src[k], sizes[k], cudaMemcpyHostToDevice, st));
+  if (from_device) {
+    const Device& D = *t->dev;
+    const void* src[6] = {D.parts.p, D.geo.p, D.link.p, D.mp.p, D.items.p, D.ibox.p};
+    for (int k = 0; k < 6; ++k)
+      if (sizes[k]) CUDA_TRY(cudaMemcpyAsync(a + offs[k], src[k], sizes[k], cudaMemcpyDeviceToDevice, st));
+  } else {
+    const void* src[6] = {t->parts.data(), t->geo.data(), t->link.data(), t->mp.data(), t->items.data(),
+                          t->ibox.data()};
+    for (int k = 0; k < 6; ++k)
+      if (sizes[k]) CUDA_TRY(cudaMemcpyAsync(a + offs[k], src[k], sizes[k], cudaMemcpyHostToDevice, st));
+  }
+  if (sizes[6]) CUDA_TRY(cudaMemcpyAsync(a + offs[6], t->sysp.data(), sizes[6], cudaMemcpyHostToDevice, st));
   og::KParams p{};
   p.parts = reinterpret_cast<const float4*>(a + offs[0]);
   p.geo = reinterpret_cast<const float4*>(a + offs[1]);
@@ -1218,11 +1328,18 @@ int octgrav_forces_noalloc(octgrav_tree* t, void* arena, size_t* arena_bytes, do
   p.sysp = t->sysp.empty() ? nullptr : reinterpret_cast<const float4*>(a + offs[6]);
   p.sys0 = make_float4(static_cast<float>(theta * theta), static_cast<float>(eps * eps), static_cast<float>(G), 0.f);
   p.out = reinterpret_cast<float4*>(acc4_dev);
-  p.n_items = static_cast<int>(t->items.size());
-  p.n_cells = static_cast<int>(t->n_cells);
+  p.n_items = static_cast<int>(ni);
+  p.n_cells = static_cast<int>(nc);
   p.stage = t->stage;
+  p.n_group = t->n_group;
+  if (t->learned) {  // the network stays in the tree's own device memory (set_criterion)
+    p.mlp = static_cast<const og::MlpDevice*>(t->dev->mlp.p);
+    p.theta_lo2 = static_cast<float>(static_cast<double>(t->theta_lo) * t->theta_lo);
+    p.theta_hi2 = static_cast<float>(static_cast<double>(t->theta_hi) * t->theta_hi);
+    p.theta_fb2 = static_cast<float>(static_cast<double>(t->theta_fb) * t->theta_fb);
+  }
   {
-    cudaError_t e = og::encode_mp_map(&p.mp_map, a + offs[3], static_cast<int>(t->n_cells));
+    cudaError_t e = og::encode_mp_map(&p.mp_map, a + offs[3], static_cast<int>(nc));
     if (e != cudaSuccess) return fail(OCTGRAV_ERR_CUDA, "tensor map encode failed: %s", cudaGetErrorString(e));
   }
   int bits = 0;
@@ -1251,7 +1368,7 @@ int octgrav_graph_capture(octgrav_tree* t, double eps, double theta, double G, f
   cudaError_t e = og::prepare_walk_eval(t->ppl, t->stage, t->ctas_per_sm, &li);
   if (e != cudaSuccess) return fail(OCTGRAV_ERR_CUDA, "kernel preparation failed: %s", cudaGetErrorString(e));
   CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-  rc = launch(t, eps, theta, G, reinterpret_cast<float4*>(acc4_dev), st, false, nullptr, nullptr, nullptr, 0);
+  rc = launch(t, eps, theta, G, reinterpret_cast<float4*>(acc4_dev), st);
   cudaGraph_t graph = nullptr;
   e = cudaStreamEndCapture(st, &graph);
   if (rc) {
@@ -1319,12 +1436,12 @@ int octgrav_autotune(int n_sys, const int64_t* offsets, const double* pos, const
       if (split > max_split) break;
       if ((rc = octgrav_set_launch(t, ppl, 0)) || (rc = octgrav_set_split(t, split))) break;
       float4* out = static_cast<float4*>(outb.p);
-      if ((rc = launch(t, eps, theta, 1.0, out, st, false, nullptr, nullptr, nullptr, 0))) break;
+      if ((rc = launch(t, eps, theta, 1.0, out, st))) break;
       if ((rc = octgrav_balance(t, 1, st))) break;  // time the longest-first order
       std::vector<float> ms;
       for (int k = 0; k < 3 && rc == OCTGRAV_OK; ++k) {
         cudaEventRecord(e0, st);
-        rc = launch(t, eps, theta, 1.0, out, st, false, nullptr, nullptr, nullptr, 0);
+        rc = launch(t, eps, theta, 1.0, out, st);
         cudaEventRecord(e1, st);
         if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(OCTGRAV_ERR_CUDA, "event sync failed");
         float v = 0;

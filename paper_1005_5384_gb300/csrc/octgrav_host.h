@@ -335,6 +335,7 @@ struct octgrav_tree {
   int stage = og::STAGING_ASYNC;
   bool learned = false;             // learned opening criterion active
   float theta_lo = 0, theta_hi = 0, theta_fb = 0;
+  int mlp_device = -1;              // device holding the criterion's network (dev->mlp)
   CUtensorMap mp_map;
   std::vector<int64_t> sys_off;   // particle offsets per system (n_sys + 1)
   std::vector<int64_t> cell_off;  // cell offsets per system (n_sys + 1)
@@ -405,8 +406,21 @@ int check_inputs(const double* pos, const double* mass, int64_t n);
 // octgrav_host.cpp
 int upload(octgrav_tree* t, cudaStream_t st);
 int check_params(double eps, double theta, double G);
-int launch(octgrav_tree* t, double eps, double theta, double G, float4* out, cudaStream_t st, bool capture,
-           int* dbg_cell, int* dbg_leaf, int2* dbg_n, int dbg_cap);
+// Capture buffers of a debug launch (device arrays; see og::KParams).
+struct CaptureArgs {
+  int* cell = nullptr;
+  int* leaf = nullptr;
+  int2* n = nullptr;
+  int cap = 0;
+  const int* slot = nullptr;
+  int2* net = nullptr;
+  int* net_n = nullptr;
+  int net_cap = 0;
+};
+// One walk-and-evaluate launch of t into out (tree order); cap != nullptr runs
+// the capture variant.
+int launch(octgrav_tree* t, double eps, double theta, double G, float4* out, cudaStream_t st,
+           const CaptureArgs* cap = nullptr);
 int read_status(octgrav_tree* t, cudaStream_t st);
 int host_images(octgrav_tree* t);
 

@@ -71,6 +71,7 @@ int octgrav_set_criterion(octgrav_tree* t, const float* record, double tau, doub
   int rc = t->dev->mlp.reserve(sizeof D);
   if (rc) return rc;
   CUDA_TRY(cudaMemcpy(t->dev->mlp.p, &D, sizeof D, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaGetDevice(&t->mlp_device));
   t->learned = true;
   t->theta_lo = static_cast<float>(theta_lo);
   t->theta_hi = static_cast<float>(theta_hi);
@@ -141,7 +142,7 @@ int octgrav_mlp_samples(octgrav_tree* t, const int64_t* groups, int64_t n_groups
   const bool learned = t->learned;
   t->learned = false;
   if ((rc = t->dev->out.reserve(sizeof(float4) * t->n))) { t->learned = learned; return rc; }
-  rc = launch(t, eps, 0.3, 1.0, static_cast<float4*>(t->dev->out.p), st, false, nullptr, nullptr, nullptr, 0);
+  rc = launch(t, eps, 0.3, 1.0, static_cast<float4*>(t->dev->out.p), st);
   t->learned = learned;
   if (rc) return rc;
   if ((rc = read_status(t, st))) return rc;
@@ -293,11 +294,17 @@ int octgrav_mlp_train(const float* features, const float* labels, int64_t n, int
   CUDA_TRY(cudaMemcpyAsync(w.data(), bw.p, 4 * og::MLP_NPARAM, cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaMemcpyAsync(&l, bl.p, 4, cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
+  // The range limits are the training extremes widened by kRangeMargin standard
+  // deviations: an input equal to an extreme is in range however it is
+  // rounded (several inputs take discrete values -- counts, cell sizes -- that
+  // sit exactly on an extreme, and an FP32 and an FP64 evaluation of them
+  // differ in the last bits).
+  constexpr float kRangeMargin = 1e-3f;
   for (int i = 0; i < F; ++i) {
     record[i] = static_cast<float>(mu[i]);
     record[12 + i] = static_cast<float>(sd[i]);
-    record[24 + i] = xmin[i];
-    record[36 + i] = xmax[i];
+    record[24 + i] = xmin[i] - kRangeMargin;
+    record[36 + i] = xmax[i] + kRangeMargin;
   }
   std::memcpy(record + 48, w.data(), 4 * og::MLP_NPARAM);
   if (final_loss) *final_loss = l;

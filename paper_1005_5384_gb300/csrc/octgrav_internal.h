@@ -73,11 +73,19 @@ struct KParams {
   int nparts;
   int n;                 // particles (rows of one part_out slice)
   float4* part_out;
-  // capture mode (tests): per item up to dbg_cap cell indices
+  // capture mode (tests): per captured item up to dbg_cap cell indices. Item k
+  // is captured into row dbg_slot[k] (-1: not captured; dbg_slot == nullptr:
+  // row k for every item). The learned criterion's network steps also record,
+  // per captured item, up to dbg_net_cap candidates as (cell, prediction bits),
+  // or (~cell, 0) for a candidate whose inputs left the training range.
   int* dbg_cell;
   int* dbg_leaf;
   int2* dbg_n;
   int dbg_cap;
+  const int* dbg_slot;
+  int2* dbg_net;
+  int* dbg_net_n;
+  int dbg_net_cap;
 };
 
 struct LaunchInfo {

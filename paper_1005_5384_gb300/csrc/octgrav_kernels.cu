@@ -429,6 +429,8 @@ __global__ void __launch_bounds__(CtaWarps<MLP>::v * 32, MLP ? 1 : 2) walk_eval_
     if (SPLIT) part = __shfl_sync(FULL, part, 0);
     if (item >= p.n_items) break;
 
+    // capture mode: the row this item's lists go to (-1: not captured)
+    const int slot = CAPTURE ? (p.dbg_slot ? __ldg(p.dbg_slot + item) : item) : -1;
     const int4 it = __ldg(p.items + item);
     const float4 b0 = __ldg(p.ibox + 4 * item);
     const float4 b1 = __ldg(p.ibox + 4 * item + 1);
@@ -661,7 +663,7 @@ __global__ void __launch_bounds__(CtaWarps<MLP>::v * 32, MLP ? 1 : 2) walk_eval_
     {
       const int2 rl = __ldg(p.link + it.x);
       if (rl.y < 0) {  // the root is a leaf: it is the group itself (own pass above)
-        if (CAPTURE && lane == 0 && p.dbg_cap > 0) p.dbg_leaf[(size_t)item * p.dbg_cap] = it.x;
+        if (CAPTURE && slot >= 0 && lane == 0 && p.dbg_cap > 0) p.dbg_leaf[(size_t)slot * p.dbg_cap] = it.x;
         n_leafent = 1;
       } else {
         if (lane == 0) S.stack[0] = (rl.x << 3) | (rl.y - 1);
@@ -701,6 +703,7 @@ __global__ void __launch_bounds__(CtaWarps<MLP>::v * 32, MLP ? 1 : 2) walk_eval_
     // that the network classifies 32 at a time. A network step takes the place
     // of a stack step; its outcomes are handled like the test's.
     int mq = 0;
+    int n_net = 0;  // capture mode: network candidates recorded for this item
     auto network_step_next = [&]() { return MLP && (mq >= 32 || (top == 0 && mq > 0)); };
     if (top > 0 && !network_step_next()) prefetch();
     while (top > 0 || (MLP && mq > 0)) {
@@ -751,6 +754,12 @@ __global__ void __launch_bounds__(CtaWarps<MLP>::v * 32, MLP ? 1 : 2) walk_eval_
         const float y = mlp_eval(NW, smem_u32(&S.pbuf[0][0]), lane);
         __syncwarp();
         open = valid && (in_range ? !(y < NW.tau) : must_open(g, gmin, gmax, p.theta_fb2));
+        if (CAPTURE) {  // the valid candidates are lanes 0 .. nb-1
+          if (slot >= 0 && p.dbg_net && valid && n_net + lane < p.dbg_net_cap)
+            p.dbg_net[(size_t)slot * p.dbg_net_cap + n_net + lane] =
+                in_range ? make_int2(c, __float_as_int(y)) : make_int2(~c, 0);
+          n_net += nb;
+        }
       } else {
         top -= min(4, top);
         valid = nx_valid;
@@ -793,8 +802,8 @@ __global__ void __launch_bounds__(CtaWarps<MLP>::v * 32, MLP ? 1 : 2) walk_eval_
         nlq_all += __popc(m_lq);
       }
       if ((m_lq_use >> lane) & 1u) S.leafq[nlq + __popc(m_lq_use & lt)] = make_int2(lk.x, -lk.y);
-      if (CAPTURE && open && leaf && n_leafent + __popc(m_leaf & lt) < p.dbg_cap)
-        p.dbg_leaf[(size_t)item * p.dbg_cap + n_leafent + __popc(m_leaf & lt)] = c;
+      if (CAPTURE && slot >= 0 && open && leaf && n_leafent + __popc(m_leaf & lt) < p.dbg_cap)
+        p.dbg_leaf[(size_t)slot * p.dbg_cap + n_leafent + __popc(m_leaf & lt)] = c;
       nlq += __popc(m_lq_use);
       n_leafent += __popc(m_leaf);
       unsigned m_stage = m_acc;  // the accepted cells this warp evaluates
@@ -814,8 +823,8 @@ __global__ void __launch_bounds__(CtaWarps<MLP>::v * 32, MLP ? 1 : 2) walk_eval_
         } else {
           S.cidx[se] = c;
         }
-        if (CAPTURE && n_pc + __popc(m_acc & lt) < p.dbg_cap)
-          p.dbg_cell[(size_t)item * p.dbg_cap + n_pc + __popc(m_acc & lt)] = c;
+        if (CAPTURE && slot >= 0 && n_pc + __popc(m_acc & lt) < p.dbg_cap)
+          p.dbg_cell[(size_t)slot * p.dbg_cap + n_pc + __popc(m_acc & lt)] = c;
       }
       const int na = __popc(m_stage);
       const uint32_t old = app;
@@ -937,7 +946,10 @@ __global__ void __launch_bounds__(CtaWarps<MLP>::v * 32, MLP ? 1 : 2) walk_eval_
       } else {
         p.counts[item] = make_int2(n_pc, n_pp);
       }
-      if (CAPTURE) p.dbg_n[item] = make_int2(n_pc, n_leafent);
+      if (CAPTURE && slot >= 0) {
+        p.dbg_n[slot] = make_int2(n_pc, n_leafent);
+        if (MLP && p.dbg_net_n) p.dbg_net_n[slot] = n_net;
+      }
     }
     if (status & ST_STACK) break;
   }
@@ -1100,21 +1112,42 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[kMaxDevices] = {};
+CUcontext g_noalloc_ctx[kMaxDevices] = {};
+
+// The calling thread's current CUDA context (driver entry point looked up once).
+cudaError_t current_context(CUcontext* ctx) {
+  using GetFn = CUresult (*)(CUcontext*);
+  static const GetFn fn = []() -> GetFn {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<GetFn>(f);
+  }();
+  if (!fn) return cudaErrorNotSupported;
+  return fn(ctx) == CUDA_SUCCESS ? cudaSuccess : cudaErrorContextIsDestroyed;
+}
 
 // Device address of the scratch array on the current device. The first call on
 // a device looks it up (cudaGetSymbolAddress) with that device current; later
-// calls reuse the cached address.
+// calls reuse the address while the device's context is the same one (a
+// context created anew, e.g. after cudaDeviceReset, is looked up again).
 cudaError_t noalloc_scratch(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  CUcontext ctx = nullptr;  // null until the runtime has made the device's context current
+  if ((e = current_context(&ctx)) != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
+  if (!g_noalloc_ptr[dev] || !ctx || g_noalloc_ctx[dev] != ctx) {
     void* ptr = nullptr;
-    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);  // initialises the primary context if needed
     if (e != cudaSuccess) return e;
+    if ((e = current_context(&ctx)) != cudaSuccess) return e;
     g_noalloc_ptr[dev] = ptr;
+    g_noalloc_ctx[dev] = ctx;
   }
   *out = g_noalloc_ptr[dev];
   return cudaSuccess;

@@ -60,6 +60,9 @@ _SIGS = {
     "octgrav_sim_set_rebuild": (C.c_int, [_vp, C.c_int]),
     "octgrav_refit_tree_gpu": (C.c_int, [_vp, _vp, _vp, _vp]),
     "octgrav_direct": (C.c_int, [_vp, _vp, C.c_int64, _vp, C.c_int64, C.c_double, C.c_double, _vp, _vp, _vp]),
+    "octgrav_forces_batched": (C.c_int, [C.c_int, _i64, _vp, _vp, _f64, _f64, _vp, _vp, _vp]),
+    "octgrav_forces_batched_ex": (C.c_int, [C.c_int, _i64, _vp, _vp, _f64, _f64, C.c_double, C.c_int, C.c_int,
+                                            _vp, _vp, _vp]),
     "octgrav_status": (C.c_int, [_vp, _vp]),
     "octgrav_tree_stats": (C.c_int, [_vp, _i64, C.c_int]),
     "octgrav_tree_perm": (C.c_int, [_vp, _i64]),
@@ -68,6 +71,8 @@ _SIGS = {
     "octgrav_item_info": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "octgrav_interaction_counts": (C.c_int, [_vp, _i64, _vp]),
     "octgrav_debug_lists": (C.c_int, [_vp, C.c_double, C.c_int, _vp, _vp, _vp, _vp, _vp]),
+    "octgrav_debug_walk": (C.c_int, [_vp, C.c_double, C.c_int64, _vp, C.c_int, _vp, _vp, _vp, _vp, C.c_int, _vp,
+                                     _vp, _vp, _vp]),
     "octgrav_set_launch": (C.c_int, [_vp, C.c_int, C.c_int]),
     "octgrav_balance": (C.c_int, [_vp, C.c_int, _vp]),
     "octgrav_set_staging": (C.c_int, [_vp, C.c_int]),
@@ -396,6 +401,36 @@ class Tree:
                                           _stream_handle(stream)))
         return [(np.sort(ck[k, :nc[k]]), np.sort(lk[k, :nl[k]])) for k in range(ni)]
 
+    def debug_walk(self, theta: float, items=None, cap: int = 8192, net_cap: int = 0, stream=None):
+        """Capture the lists of the given work items (all when None). Returns one
+        dict per requested item: 'cells' and 'leaves' (sorted key arrays) and,
+        with net_cap > 0, 'net_keys' / 'net_y' (network candidates in walk
+        order; y = NaN where the inputs were out of range)."""
+        lib = load()
+        if items is None:
+            ns, ip = self.stats["n_items"], None
+        else:
+            arr = np.ascontiguousarray(items, dtype=np.int64)
+            ns, ip = len(arr), _p(arr)
+        ck = np.zeros((ns, cap), np.uint64)
+        lk = np.zeros((ns, cap), np.uint64)
+        nc = np.zeros(ns, np.int32)
+        nl = np.zeros(ns, np.int32)
+        nk = np.zeros((ns, max(net_cap, 1)), np.uint64)
+        ny = np.zeros((ns, max(net_cap, 1)), np.float32)
+        nn = np.zeros(ns, np.int32)
+        _check(lib.octgrav_debug_walk(self._h, float(theta), ns, ip, int(cap), _p(ck), _p(nc), _p(lk), _p(nl),
+                                      int(net_cap), _p(nk) if net_cap else None, _p(ny) if net_cap else None,
+                                      _p(nn) if net_cap else None, _stream_handle(stream)))
+        out = []
+        for r in range(ns):
+            d = dict(cells=np.sort(ck[r, :nc[r]]), leaves=np.sort(lk[r, :nl[r]]))
+            if net_cap:
+                d["net_keys"] = nk[r, :nn[r]].copy()
+                d["net_y"] = ny[r, :nn[r]].copy()
+            out.append(d)
+        return out
+
 
 def _out_arrays(n, out):
     if out is None:
@@ -450,6 +485,36 @@ def forces_gpu(pos, mass, eps: float, theta: float, n_leaf: int = 16, n_group: i
     _check(lib.octgrav_forces_gpu(_p(pos), _p(mass), n, float(eps), float(theta), float(G), int(n_leaf),
                                   int(n_group if n_group is not None else n_leaf), _p(acc), _p(pot),
                                   _stream_handle(stream)))
+    return acc, pot
+
+
+def forces_batched(systems, eps, theta, G: float = 1.0, n_leaf: int = 16, n_group: int = 256, out=None,
+                   stream=None):
+    """One-shot forces of many independent systems through octgrav_forces_batched_ex.
+
+    ``systems`` is a list of (pos [n_s,3], mass [n_s]) or a tuple (offsets, pos, mass)
+    of concatenated host arrays; ``eps`` and ``theta`` are scalars or one value
+    per system. Returns (acc [n,3], pot [n]) in input order. ``out`` may give
+    (acc, pot) host arrays (e.g. pinned torch tensors' numpy views) to fill."""
+    if isinstance(systems, tuple):
+        off, pos, mass = systems
+        off = np.ascontiguousarray(off, np.int64)
+        pos = np.ascontiguousarray(pos, np.float64).reshape(-1, 3)
+        mass = np.ascontiguousarray(mass, np.float64)
+    else:
+        off = np.zeros(len(systems) + 1, np.int64)
+        off[1:] = np.cumsum([len(m) for _, m in systems])
+        pos = np.ascontiguousarray(np.concatenate([p for p, _ in systems]), np.float64)
+        mass = np.ascontiguousarray(np.concatenate([m for _, m in systems]), np.float64)
+    ns = len(off) - 1
+    e = np.ascontiguousarray(np.broadcast_to(np.asarray(eps, np.float64), (ns,)))
+    t = np.ascontiguousarray(np.broadcast_to(np.asarray(theta, np.float64), (ns,)))
+    n = int(off[-1])
+    acc, pot = out if out is not None else (np.empty((n, 3)), np.empty(n))
+    _check(load().octgrav_forces_batched_ex(ns, off, pos.ctypes.data_as(_vp), mass.ctypes.data_as(_vp), e, t,
+                                            float(G), int(n_leaf), int(n_group), acc.ctypes.data_as(_vp),
+                                            None if pot is None else pot.ctypes.data_as(_vp),
+                                            _stream_handle(stream)))
     return acc, pot
 
 

@@ -86,3 +86,59 @@ def test_autotuner_returns_a_valid_configuration(torch, systems):
     acc, _ = T.forces(0.01, 0.6)
     ra, _, _, _, _ = O.Tree(pos, m, 16, best["n_group"]).forces(0.01, 0.6)
     assert O.rel_rms(acc, ra) <= TOL_RMS
+
+
+def test_one_shot_batched_call_matches_per_system_oracle(torch, systems):
+    """octgrav_forces_batched: host arrays and per-system eps / theta in, FP64
+    results in input order out; each system equals the oracle run on it alone,
+    and the whole equals the three-call path (batch build, per-system
+    parameters, forces) bit for bit."""
+    rng = np.random.default_rng(7)
+    eps = 0.005 + 0.015 * rng.random(len(systems))
+    theta = 0.4 + 0.4 * rng.random(len(systems))
+    acc, pot = G.forces_batched(systems, eps, theta, n_group=64)
+    off = np.zeros(len(systems) + 1, np.int64)
+    off[1:] = np.cumsum([len(m) for _, m in systems])
+    for s, (pos, m) in enumerate(systems):
+        ra, rp, _, _, _ = O.Tree(pos, m, 16, 64).forces(eps[s], theta[s])
+        a, p = acc[off[s]:off[s + 1]], pot[off[s]:off[s + 1]]
+        assert O.rel_rms(a, ra) <= TOL_RMS, s
+        assert float(np.linalg.norm(p - rp) / np.linalg.norm(rp)) <= TOL_RMS, s
+    T = G.Tree.build_batch(systems, 16, 64)
+    T.set_system_params(eps, theta)
+    a3, p3 = T.forces(1.0, 1.0)
+    assert np.array_equal(acc, a3) and np.array_equal(pot, p3)
+    # the defaults (N_leaf 16, N_group 256, G = 1) through the plain entry point
+    lib = G.load()
+    pos = np.ascontiguousarray(np.concatenate([p for p, _ in systems]))
+    mass = np.ascontiguousarray(np.concatenate([m for _, m in systems]))
+    a0 = np.empty_like(acc)
+    p0 = np.empty_like(pot)
+    rc = lib.octgrav_forces_batched(len(systems), off, pos.ctypes.data_as(G._vp), mass.ctypes.data_as(G._vp),
+                                    eps, theta, a0.ctypes.data_as(G._vp), p0.ctypes.data_as(G._vp), None)
+    assert rc == G.OK, lib.octgrav_last_error()
+    a1, p1 = G.forces_batched(systems, eps, theta, n_group=256)
+    assert np.array_equal(a0, a1) and np.array_equal(p0, p1)
+
+
+def test_one_shot_batched_call_refusals(torch, systems):
+    sub = systems[:3]
+    with pytest.raises(G.OctgravError) as e:
+        G.forces_batched(sub, [0.01, -1.0, 0.01], 0.5)
+    assert e.value.code == G.ERR_ARG
+    with pytest.raises(G.OctgravError) as e:
+        G.forces_batched(sub, 0.01, [0.5, np.nan, 0.5])
+    assert e.value.code == G.ERR_ARG
+    bad = [(p.copy(), m.copy()) for p, m in sub]
+    bad[1][0][5, 2] = np.inf
+    with pytest.raises(G.OctgravError) as e:
+        G.forces_batched(bad, 0.01, 0.5)
+    assert e.value.code == G.ERR_NONFINITE
+    pos = np.concatenate([p for p, _ in sub])
+    mass = np.concatenate([m for _, m in sub])
+    with pytest.raises(G.OctgravError) as e:
+        G.forces_batched((np.array([0, 5, 5, len(mass)]), pos, mass), 0.01, 0.5)
+    assert e.value.code == G.ERR_ARG
+    # the context stays usable
+    acc, _ = G.forces_batched(sub, 0.01, 0.5)
+    assert np.isfinite(acc).all()

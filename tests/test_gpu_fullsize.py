@@ -121,9 +121,8 @@ def test_sphere_disc_1m_learned_walk(torch):
     """C5's learned walk as the benchmark runs it (network trained on another
     seed from 64 groups, N_group 256, band theta 0.8-1.3, tau near the 1e-3
     point, longest-first items): on 200 sampled groups its forces equal the
-    FP64 evaluation of its own captured lists to 1e-5, and the oracle's own
-    network walk over the same groups gives the same interaction totals (2 %)
-    and forces (1e-3; decisions at the threshold may differ in FP32)."""
+    FP64 evaluation of its own captured lists to 1e-5. (Its decisions are
+    checked pair by pair against the oracle's network in test_gpu_decisions.py.)"""
     band = dict(theta_lo=0.8, theta_hi=1.3, theta_fb=1.0)
     tpos, tm = W.sphere_disc(1 << 20, seed=6)
     TT = G.Tree.build(tpos, tm, 16, 256)
@@ -155,12 +154,3 @@ def test_sphere_disc_1m_learned_walk(torch):
         den += float(np.sum(ra ** 2))
     assert len(done) == len(gsel)
     assert np.sqrt(num / den) <= TOL_RMS
-    rec64 = np.asarray(rec, np.float64)
-    net = dict(mu=rec64[:12], sigma=rec64[12:24], fmin=rec64[24:36], fmax=rec64[36:48], w=rec64[48:])
-    garr = np.array(sorted(gsel))
-    oa, _, _, onpc, _ = R.forces_mlp(0.01, net, tau, groups=garr, **band)
-    idx = np.concatenate([R.cell_members(int(R.groups[g])) for g in garr])
-    gpu_npc = sum(len(lists[k][0]) * int(info["count"][k]) for k in range(len(lists))
-                  if okey[int(info["group_key"][k])] in gsel)
-    assert abs(gpu_npc - int(onpc[idx].sum())) <= 0.02 * onpc[idx].sum()
-    assert O.rel_rms(acc[idx], oa[idx]) <= 1e-3

@@ -5,8 +5,8 @@
   oracle's for the same (group, cell) pairs;
 * the trained network predicts held-out labels;
 * a walk with the learned criterion: its forces equal the oracle's evaluation
-  of the same lists within 1e-5, and its decisions agree with the oracle's
-  network away from the threshold;
+  of the same lists within 1e-5 (its decisions are checked pair by pair in
+  test_gpu_decisions.py);
 * the gain: at an equal median relative force error of 1e-3 the learned walk
   needs fewer interactions and less time than the plain theta walk.
 """
@@ -67,8 +67,10 @@ def test_gpu_samples_match_oracle(trained):
     keys = T.cell_keys()
     gpu = {(int(g), int(keys[c])): k for k, (g, c) in enumerate(trained["pairs"])}
     ora = {(int(g), int(R.key[c])): k for k, (g, c) in enumerate(opairs)}
-    common = set(gpu) & set(ora)
-    assert len(common) >= 0.999 * max(len(gpu), len(ora))
+    # both sides take a pair when the FP32 test sees h > 0 and a nonzero gap
+    assert len(gpu) == len(trained["pairs"]) and len(ora) == len(opairs)
+    assert set(gpu) == set(ora)
+    common = set(gpu)
     gi = np.array([gpu[k] for k in common])
     oi = np.array([ora[k] for k in common])
     fg, fo = trained["f"][gi].astype(np.float64), of[oi]
@@ -100,7 +102,7 @@ def test_training_learns_the_labels(trained):
     assert rmse < 0.6, rmse
 
 
-def test_learned_walk_forces_and_decisions(torch, trained):
+def test_learned_walk_forces_on_its_lists(torch, trained):
     pos, m = W.sphere_disc(32768, seed=8)
     T = G.Tree.build(pos, m, 16, 64)
     tau = -3.5
@@ -123,12 +125,6 @@ def test_learned_walk_forces_and_decisions(torch, trained):
         num += float(np.sum((acc[mem] - ra) ** 2))
         den += float(np.sum(ra ** 2))
     assert np.sqrt(num / den) <= 1e-5
-    # the oracle's walk with the same network: same interaction totals up to decisions at the threshold
-    net = _net(trained["rec"])
-    oa, _, onpp, onpc, _ = R.forces_mlp(0.01, net, tau, **BAND)
-    c = T.interaction_counts()
-    assert abs(c["n_pc"] - int(onpc.sum())) <= 0.02 * onpc.sum()
-    assert O.rel_rms(acc, oa) <= 1e-3
 
 
 def _median_err(T, torch, out, eps, samp, ad, theta):
@@ -198,6 +194,8 @@ def test_learned_criterion_beats_theta_at_equal_median_error(torch):
     t_ml = _time_events(T, torch, out, 0.01, 0.5)
     print("theta %.3f err %.2e flops %.3g time %.3f ms | tau %.3f err %.2e flops %.3g time %.3f ms"
           % (th, e_th, f_th, t_th, tau, e_ml, f_ml, t_ml))
-    assert e_th <= 1.05e-3 and e_ml <= 1.05e-3
+    # the comparison is at equal error: both bisections end within 5 % of 1e-3
+    assert 0.95e-3 <= e_th <= 1.05e-3 and 0.95e-3 <= e_ml <= 1.05e-3
+    assert abs(e_ml - e_th) <= 0.05 * e_th
     assert f_ml < 0.8 * f_th
     assert t_ml < 0.95 * t_th

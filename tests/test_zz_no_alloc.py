@@ -88,3 +88,51 @@ def test_noalloc_with_a_gpu_built_tree(torch):
     out = torch.zeros_like(ref)
     T.forces_noalloc(0.01, 0.5, out, arena)
     assert np.array_equal(out.cpu().numpy().view(np.uint32), ref.cpu().numpy().view(np.uint32))
+
+
+def _random_record(seed):
+    """A criterion record with a random network whose inputs are never out of range."""
+    import oracle.mlp as M
+    rec = np.zeros(48 + M.NPARAM, np.float32)
+    rec[12:24] = 1.0                      # sigma
+    rec[24:36] = -1e30                    # standardised-input range
+    rec[36:48] = 1e30
+    rec[48:] = M.init(seed).astype(np.float32)
+    return rec
+
+
+@pytest.mark.parametrize("gpu_built", [False, True])
+def test_noalloc_applies_the_learned_criterion(torch, gpu_built):
+    """A tree with the learned criterion is walked with it: the results equal
+    octgrav_forces_device's bit for bit, on two calls in a row, and differ from
+    the plain walk's."""
+    pos, m = W.sphere_disc(40000, seed=6)
+    T = (G.Tree.build_gpu if gpu_built else G.Tree.build)(pos, m, 16, 64)
+    plain = torch.empty((T.n, 4), dtype=torch.float32, device="cuda")
+    T.forces_device(0.01, 0.5, plain)
+    T.set_criterion(_random_record(3), tau=0.0, theta_lo=0.4, theta_hi=1.2, theta_fb=0.7)
+    ref = torch.empty_like(plain)
+    T.forces_device(0.01, 0.5, ref)
+    torch.cuda.synchronize()
+    assert T.status() == G.OK
+    arena = torch.empty(T.noalloc_arena_bytes(), dtype=torch.uint8, device="cuda")
+    ref_bits = ref.cpu().numpy().view(np.uint32)
+    for call in range(2):
+        out = torch.full_like(ref, float("nan"))
+        T.forces_noalloc(0.01, 0.5, out, arena)
+        assert np.array_equal(out.cpu().numpy().view(np.uint32), ref_bits), call
+    assert not np.array_equal(plain.cpu().numpy().view(np.uint32), ref_bits)
+
+
+def test_noalloc_runs_a_split_tree_unsplit(torch):
+    """A list split needs a per-part buffer, so the allocation-free call runs the
+    tree unsplit: its result is the unsplit launch's, bit for bit."""
+    pos, m = W.plummer(16384, seed=1)
+    T = G.Tree.build(pos, m, 16, 64)
+    ref = torch.empty((T.n, 4), dtype=torch.float32, device="cuda")
+    T.forces_device(0.01, 0.5, ref)
+    T.set_split(4)
+    arena = torch.empty(T.noalloc_arena_bytes(), dtype=torch.uint8, device="cuda")
+    out = torch.full_like(ref, float("nan"))
+    T.forces_noalloc(0.01, 0.5, out, arena)
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), ref.cpu().numpy().view(np.uint32))
