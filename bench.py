@@ -68,13 +68,12 @@ def parse():
                          "by the costs of the first warm-up launch")
     ap.add_argument("--sweep-n", default="30000,100000,300000,1000000",
                     help="particle numbers of --leg accuracy (comma separated)")
-    ap.add_argument("--leg", default="", choices=["", "learned", "build", "accuracy", "pipes"],
+    ap.add_argument("--leg", default="", choices=["", "learned", "build", "accuracy"],
                     help="learned: train the criterion on the 1M sphere+disc and launch the learned walk "
                          "twice (a small driver for profilers; prints the interaction counts); build: "
                          "--warmup + --steps GPU tree builds of the workload (prints their wall times); "
                          "accuracy: error distribution and throughput over theta, N and N_leaf on the "
-                         "galaxy stand-in (one JSON line per configuration, then the fitted theta slopes); "
-                         "pipes: FP32 / MUFU / FP64 pipe throughput probe (paper_1005_5384_gb300/probes)")
+                         "galaxy stand-in (one JSON line per configuration, then the fitted theta slopes)")
     return ap.parse_args()
 
 
@@ -578,17 +577,6 @@ def run_accuracy_driver(a):
                       "fits": fits}), flush=True)
 
 
-def run_pipe_probe():
-    """Compile and run the arithmetic-pipe probe; it prints one JSON line per case."""
-    from paper_1005_5384_gb300 import build as B
-    src = os.path.join(ROOT, "paper_1005_5384_gb300", "probes", "pipe_probe.cu")
-    exe = os.path.join(B.BUILD, "pipe_probe")
-    os.makedirs(B.BUILD, exist_ok=True)
-    subprocess.run([os.path.join(B._cuda_home(), "bin", "nvcc"), *B.ARCH, "-O3", "-o", exe, src], check=True)
-    r = subprocess.run([exe], stdout=subprocess.PIPE, text=True, check=True)
-    sys.stdout.write(r.stdout)
-
-
 def run_reference(a, rank, world):
     if rank != 0:
         return
@@ -642,9 +630,6 @@ def main():
         return
     if a.leg == "accuracy":
         run_accuracy_driver(a)
-        return
-    if a.leg == "pipes":
-        run_pipe_probe()
         return
 
     import torch
