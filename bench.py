@@ -335,6 +335,7 @@ def extras(torch, G, a, pos, m, T, out, flush, stream, peak, steps):
     ST = G.Tree.build(spos, sm, a.n_leaf, stuned["n_group"])
     ST.set_launch(stuned["particles_per_lane"])
     ST.set_split(stuned["split"])
+    ST.set_staging(stuned["staging"])
     sout = torch.empty((ST.n, 4), dtype=torch.float32, device="cuda")
     ST.forces_device(a.eps, 0.5, sout, stream=stream)
     ST.balance(stream=stream)
@@ -343,6 +344,22 @@ def extras(torch, G, a, pos, m, T, out, flush, stream, peak, steps):
     res["plummer_16k"] = {"autotuned": stuned, "forces_per_s": ST.n / (ms * 1e-3), "ms": ms,
                           "frac_fp32_peak": c["flops"] / ms / 1e9 / peak, "flops_per_particle": c["flops"] / ST.n}
     del ST, sout
+    # C2 (theta 0.5) with each staging mode of the accepted cell records, the
+    # same tree and item order; results are bitwise identical across modes
+    ref_bits = None
+    stag = {}
+    for mode, name in ((1, "cp.async per lane"), (2, "TMA tile::gather4"), (0, "cp.async.bulk per record")):
+        T.set_staging(mode)
+        T.forces_device(a.eps, a.theta, out, stream=stream)
+        torch.cuda.synchronize()
+        bits = out.view(torch.int32).clone()
+        if ref_bits is None:
+            ref_bits = bits
+        stag[name] = {"mode": mode, "ms": time_kernel(torch, lambda: T.forces_device(a.eps, a.theta, out, stream=stream),
+                                                         flush, steps, stream),
+                      "bitwise_equal_to_cp_async": bool(torch.equal(bits, ref_bits))}
+    T.set_staging(1)
+    res["staging_modes_plummer_1M"] = stag
     # C2 at theta = 0.75
     T.forces_device(a.eps, 0.75, out, stream=stream)
     ms = time_kernel(torch, lambda: T.forces_device(a.eps, 0.75, out, stream=stream), flush, steps, stream)
@@ -396,6 +413,8 @@ def extras(torch, G, a, pos, m, T, out, flush, stream, peak, steps):
                       stream=stream)
     ET = G.Tree.build_batch(systems, a.n_leaf, best["n_group"])
     ET.set_launch(best["particles_per_lane"])
+    ET.set_split(best["split"])
+    ET.set_staging(best["staging"])
     eout = torch.empty((ET.n, 4), dtype=torch.float32, device="cuda")
     gstream = torch.cuda.Stream()
     with torch.cuda.stream(gstream):
@@ -682,6 +701,9 @@ def main():
         a.ppl = a.ppl if a.ppl > 0 else tuned["particles_per_lane"]
     T = G.Tree.build(pos, m, a.n_leaf, a.n_group)
     T.set_launch(a.ppl)
+    if tuned is not None and tuned["n_group"] == a.n_group and tuned["particles_per_lane"] == a.ppl:
+        T.set_split(tuned["split"])
+        T.set_staging(tuned["staging"])
     T.upload()
     out = torch.empty((T.n, 4), dtype=torch.float32, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")

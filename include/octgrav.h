@@ -371,12 +371,30 @@ int octgrav_graph_launch(octgrav_tree *t, void *stream);
  * 1, 2 and 4 (octgrav_set_split), and returns the fastest in best[0] =
  * n_group, best[1] = particles per lane, best[2] = list split, with its
  * median time in *best_ms (may be NULL).
- * Results are cached in-process per (n_sys, log2 N, theta, eps, n_leaf,
- * candidates). Builds temporary trees and device buffers. Synchronous.
+ * Results are cached in-process (see octgrav_autotune_ex for the key). Builds
+ * temporary trees and device buffers. Synchronous.
  * Errors: as octgrav_build_batch and octgrav_forces_device. */
 int octgrav_autotune(int n_sys, const int64_t *offsets, const double *pos, const double *mass,
                      int n_leaf, double eps, double theta, const int *n_group_cand, int n_cand,
                      int *best, double *best_ms, void *stream);
+
+/* The autotuner with every tuned dimension. First as octgrav_autotune: group
+ * size, particles per lane (the particle side of the evaluated tile: a warp
+ * covers 32 x particles-per-lane particles against slices of each 32-record
+ * tile of the list; the record side is the warp width) and list split; then,
+ * for the fastest of those without a split, the staging of the accepted cell
+ * records (octgrav_set_staging: 0 cp.async.bulk, 1 per-lane cp.async, 2 TMA
+ * tile::gather4), each timed the same way (median of three launches, items
+ * longest first). Writes min(n_best, 4) values: best[0] n_group, best[1]
+ * particles per lane, best[2] list split, best[3] staging mode. Both
+ * autotuners cache their results in-process per (n_sys, log2 N, theta, eps,
+ * n_leaf, candidates) and a coarse descriptor of the input distribution
+ * (quartiles of the particles' distances from their system's box centre over
+ * its half diagonal, log2 in halves, from up to 4096 particles). Synchronous.
+ * Errors: ERR_ARG (also n_best < 1), and those of octgrav_autotune. */
+int octgrav_autotune_ex(int n_sys, const int64_t *offsets, const double *pos, const double *mass,
+                        int n_leaf, double eps, double theta, const int *n_group_cand, int n_cand,
+                        int *best, int n_best, double *best_ms, void *stream);
 
 /* ---- Learned opening criterion (a small network consulted inside the walk).
  * Record layout (OCTGRAV_MLP_RECORD floats): input mean[12], standard

@@ -1393,27 +1393,69 @@ int octgrav_graph_launch(octgrav_tree* t, void* stream) {
   return OCTGRAV_OK;
 }
 
-int octgrav_autotune(int n_sys, const int64_t* offsets, const double* pos, const double* mass, int n_leaf,
-                     double eps, double theta, const int* n_group_cand, int n_cand, int* best, double* best_ms,
-                     void* stream) {
-  if (!offsets || !pos || !mass || !n_group_cand || n_cand < 1 || !best || n_sys < 1)
+// Coarse descriptor of how the particles are spread, for the autotuner's cache:
+// quartiles of the distance of (up to 4096, evenly strided) particles from
+// their system's bounding-box centre, over the box's half diagonal, as log2
+// rounded to halves. A Plummer sphere, a uniform cube and a thin disc differ.
+static std::vector<double> spread_descriptor(int n_sys, const int64_t* offsets, const double* pos) {
+  std::vector<double> r;
+  const int64_t n = offsets[n_sys];
+  const int64_t stride = std::max<int64_t>(1, n / 4096);
+  std::vector<double> lo(3 * n_sys, INFINITY), hi(3 * n_sys, -INFINITY);
+  int s = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    while (i >= offsets[s + 1]) ++s;
+    for (int k = 0; k < 3; ++k) {
+      lo[3 * s + k] = std::min(lo[3 * s + k], pos[3 * i + k]);
+      hi[3 * s + k] = std::max(hi[3 * s + k], pos[3 * i + k]);
+    }
+  }
+  s = 0;
+  for (int64_t i = 0; i < n; i += stride) {
+    while (i >= offsets[s + 1]) ++s;
+    double d2 = 0, h2 = 0;
+    for (int k = 0; k < 3; ++k) {
+      const double c = 0.5 * (lo[3 * s + k] + hi[3 * s + k]), h = 0.5 * (hi[3 * s + k] - lo[3 * s + k]);
+      d2 += (pos[3 * i + k] - c) * (pos[3 * i + k] - c);
+      h2 += h * h;
+    }
+    r.push_back(h2 > 0 ? std::sqrt(d2 / h2) : 0.0);
+  }
+  std::sort(r.begin(), r.end());
+  std::vector<double> q;
+  for (double f : {0.25, 0.5, 0.75}) {
+    const double v = r[static_cast<size_t>(f * (r.size() - 1))];
+    q.push_back(std::round(2.0 * std::log2(std::max(v, 1e-6))) / 2.0);
+  }
+  return q;
+}
+
+// The autotuner behind octgrav_autotune (tune_staging = false) and
+// octgrav_autotune_ex. Writes n_group, particles per lane, split, staging.
+static int autotune_common(int n_sys, const int64_t* offsets, const double* pos, const double* mass, int n_leaf,
+                           double eps, double theta, const int* n_group_cand, int n_cand, bool tune_staging,
+                           int* best4, double* best_ms, void* stream) {
+  if (!offsets || !pos || !mass || !n_group_cand || n_cand < 1 || !best4 || n_sys < 1)
     return fail(OCTGRAV_ERR_ARG, "bad argument");
   int rc = check_params(eps, theta, 1.0);
   if (rc) return rc;
-  // results are cached per (systems, log2 N, theta, eps, n_leaf, candidate set)
+  if (offsets[0] != 0) return fail(OCTGRAV_ERR_ARG, "offsets[0] must be 0");
+  for (int s = 0; s < n_sys; ++s)
+    if (offsets[s + 1] <= offsets[s]) return fail(OCTGRAV_ERR_ARG, "empty or decreasing system %d", s);
+  // results are cached per (systems, log2 N, theta, eps, n_leaf, spread of the
+  // particles, what is tuned, candidate set)
   static std::mutex mu;
   static std::vector<std::pair<std::vector<double>, std::vector<double>>> cache;
   std::vector<double> key = {static_cast<double>(n_sys), std::floor(std::log2(static_cast<double>(offsets[n_sys]))),
-                             theta, eps, static_cast<double>(n_leaf)};
+                             theta, eps, static_cast<double>(n_leaf), tune_staging ? 1.0 : 0.0};
+  for (double q : spread_descriptor(n_sys, offsets, pos)) key.push_back(q);
   for (int c = 0; c < n_cand; ++c) key.push_back(n_group_cand[c]);
   {
     std::lock_guard<std::mutex> g(mu);
     for (auto& kv : cache)
       if (kv.first == key) {
-        best[0] = static_cast<int>(kv.second[0]);
-        best[1] = static_cast<int>(kv.second[1]);
-        best[2] = static_cast<int>(kv.second[3]);
-        if (best_ms) *best_ms = kv.second[2];
+        for (int k = 0; k < 4; ++k) best4[k] = static_cast<int>(kv.second[k]);
+        if (best_ms) *best_ms = kv.second[4];
         return OCTGRAV_OK;
       }
   }
@@ -1423,8 +1465,29 @@ int octgrav_autotune(int n_sys, const int64_t* offsets, const double* pos, const
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0));
   CUDA_TRY(cudaEventCreate(&e1));
+  float4* out = static_cast<float4*>(outb.p);
+  // median of three timed launches, the items taken longest first
+  auto time_tree = [&](octgrav_tree* t, double* ms_out) -> int {
+    int r;
+    if ((r = launch(t, eps, theta, 1.0, out, st))) return r;
+    if ((r = octgrav_balance(t, 1, st))) return r;
+    std::vector<float> ms;
+    for (int k = 0; k < 3; ++k) {
+      cudaEventRecord(e0, st);
+      if ((r = launch(t, eps, theta, 1.0, out, st))) return r;
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) return fail(OCTGRAV_ERR_CUDA, "event sync failed");
+      float v = 0;
+      cudaEventElapsedTime(&v, e0, e1);
+      ms.push_back(v);
+    }
+    if ((r = read_status(t, st))) return r;
+    std::sort(ms.begin(), ms.end());
+    *ms_out = ms[1];
+    return OCTGRAV_OK;
+  };
   double bms = 1e300;
-  int bng = -1, bppl = 2, bsplit = 1;
+  int bng = -1, bppl = 2, bsplit = 1, bstage = og::STAGING_ASYNC;
   for (int c = 0; c < n_cand && rc == OCTGRAV_OK; ++c) {
     if (n_group_cand[c] < n_leaf) continue;
     octgrav_tree* t = nullptr;
@@ -1435,27 +1498,29 @@ int octgrav_autotune(int n_sys, const int64_t* offsets, const double* pos, const
       const int ppl = 1 + trial % 2, split = 1 << (trial / 2);
       if (split > max_split) break;
       if ((rc = octgrav_set_launch(t, ppl, 0)) || (rc = octgrav_set_split(t, split))) break;
-      float4* out = static_cast<float4*>(outb.p);
-      if ((rc = launch(t, eps, theta, 1.0, out, st))) break;
-      if ((rc = octgrav_balance(t, 1, st))) break;  // time the longest-first order
-      std::vector<float> ms;
-      for (int k = 0; k < 3 && rc == OCTGRAV_OK; ++k) {
-        cudaEventRecord(e0, st);
-        rc = launch(t, eps, theta, 1.0, out, st);
-        cudaEventRecord(e1, st);
-        if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(OCTGRAV_ERR_CUDA, "event sync failed");
-        float v = 0;
-        cudaEventElapsedTime(&v, e0, e1);
-        ms.push_back(v);
-      }
-      if (rc) break;
-      if ((rc = read_status(t, st))) break;
-      std::sort(ms.begin(), ms.end());
-      if (ms[1] < bms) {
-        bms = ms[1];
+      double ms = 0;
+      if ((rc = time_tree(t, &ms))) break;
+      if (ms < bms) {
+        bms = ms;
         bng = n_group_cand[c];
         bppl = ppl;
         bsplit = split;
+      }
+    }
+    octgrav_free_tree(t);
+  }
+  // the staging of the accepted cell records, for the winner (a split runs
+  // with per-lane cp.async staging only)
+  if (rc == OCTGRAV_OK && tune_staging && bng >= 0 && bsplit == 1) {
+    octgrav_tree* t = nullptr;
+    if (!(rc = build_common(n_sys, offsets, pos, mass, n_leaf, bng, &t)) && !(rc = octgrav_set_launch(t, bppl, 0))) {
+      for (int stage : {og::STAGING_BULK, og::STAGING_GATHER4}) {
+        double ms = 0;
+        if ((rc = octgrav_set_staging(t, stage)) || (rc = time_tree(t, &ms))) break;
+        if (ms < bms) {
+          bms = ms;
+          bstage = stage;
+        }
       }
     }
     octgrav_free_tree(t);
@@ -1465,13 +1530,38 @@ int octgrav_autotune(int n_sys, const int64_t* offsets, const double* pos, const
   outb.release();
   if (rc) return rc;
   if (bng < 0) return fail(OCTGRAV_ERR_ARG, "no candidate n_group >= n_leaf");
-  best[0] = bng;
-  best[1] = bppl;
-  best[2] = bsplit;
+  best4[0] = bng;
+  best4[1] = bppl;
+  best4[2] = bsplit;
+  best4[3] = bstage;
   if (best_ms) *best_ms = bms;
   std::lock_guard<std::mutex> g(mu);
-  cache.push_back({key, {static_cast<double>(bng), static_cast<double>(bppl), bms, static_cast<double>(bsplit)}});
+  cache.push_back({key, {static_cast<double>(bng), static_cast<double>(bppl), static_cast<double>(bsplit),
+                         static_cast<double>(bstage), bms}});
   return OCTGRAV_OK;
+}
+
+int octgrav_autotune(int n_sys, const int64_t* offsets, const double* pos, const double* mass, int n_leaf,
+                     double eps, double theta, const int* n_group_cand, int n_cand, int* best, double* best_ms,
+                     void* stream) {
+  int b[4];
+  int rc = autotune_common(n_sys, offsets, pos, mass, n_leaf, eps, theta, n_group_cand, n_cand, false, b, best_ms,
+                           stream);
+  if (rc == OCTGRAV_OK)
+    for (int k = 0; k < 3; ++k) best[k] = b[k];
+  return rc;
+}
+
+int octgrav_autotune_ex(int n_sys, const int64_t* offsets, const double* pos, const double* mass, int n_leaf,
+                        double eps, double theta, const int* n_group_cand, int n_cand, int* best, int n_best,
+                        double* best_ms, void* stream) {
+  if (n_best < 1 || !best) return fail(OCTGRAV_ERR_ARG, "no room for the result");
+  int b[4];
+  int rc = autotune_common(n_sys, offsets, pos, mass, n_leaf, eps, theta, n_group_cand, n_cand, true, b, best_ms,
+                           stream);
+  if (rc == OCTGRAV_OK)
+    for (int k = 0; k < std::min(n_best, 4); ++k) best[k] = b[k];
+  return rc;
 }
 
 int octgrav_set_split(octgrav_tree* t, int nparts) {

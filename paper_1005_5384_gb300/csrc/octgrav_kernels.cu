@@ -176,16 +176,17 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-// The learned criterion's network on the 32 rows of X (one candidate per lane;
-// 16 bf16 inputs per row, the last 4 zero): 12 -> 64 -> 64 -> 1 with ReLU,
-// bf16 weights and inputs, FP32 accumulation on the tensor cores. Returns the
-// prediction for row `lane`. Layer-1 accumulators become layer-2 A fragments
-// in registers (the C and A fragment layouts line up pairwise).
-__device__ float mlp_eval(const MlpDevice& W, uint32_t x_smem, int lane) {
+// The learned criterion's network on the first 16 * n16 rows of X (one
+// candidate per lane; 16 bf16 inputs per row, the last 4 zero): 12 -> 64 -> 64
+// -> 1 with ReLU, bf16 weights and inputs, FP32 accumulation on the tensor
+// cores. Returns the prediction for row `lane` (rows >= 16 * n16 are not
+// evaluated). Layer-1 accumulators become layer-2 A fragments in registers
+// (the C and A fragment layouts line up pairwise).
+__device__ float mlp_eval(const MlpDevice& W, uint32_t x_smem, int lane, int n16) {
   float y00 = 0.f, y01 = 0.f, y10 = 0.f, y11 = 0.f;
   const int q = 2 * (lane & 3);
 #pragma unroll 1
-  for (int t = 0; t < 2; ++t) {
+  for (int t = 0; t < n16; ++t) {
     uint32_t a[4];
     ldmatrix_x4(a, x_smem + 2u * ((16 * t + (lane & 15)) * 16 + (lane >> 4) * 8));
     uint32_t a2[4][4];
@@ -751,7 +752,7 @@ __global__ void __launch_bounds__(CtaWarps<MLP>::v * 32, MLP ? 1 : 2) walk_eval_
         xrow[0] = make_uint4(xw[0], xw[1], xw[2], xw[3]);
         xrow[1] = make_uint4(xw[4], xw[5], xw[6], xw[7]);
         __syncwarp();
-        const float y = mlp_eval(NW, smem_u32(&S.pbuf[0][0]), lane);
+        const float y = mlp_eval(NW, smem_u32(&S.pbuf[0][0]), lane, nb > 16 ? 2 : 1);
         __syncwarp();
         open = valid && (in_range ? !(y < NW.tau) : must_open(g, gmin, gmax, p.theta_fb2));
         if (CAPTURE) {  // the valid candidates are lanes 0 .. nb-1

@@ -89,6 +89,8 @@ _SIGS = {
     "octgrav_graph_launch": (C.c_int, [_vp, _vp]),
     "octgrav_autotune": (C.c_int, [C.c_int, _i64, _f64, _f64, C.c_int, C.c_double, C.c_double, _vp, C.c_int,
                                    _vp, _vp, _vp]),
+    "octgrav_autotune_ex": (C.c_int, [C.c_int, _i64, _f64, _f64, C.c_int, C.c_double, C.c_double, _vp, C.c_int,
+                                      _vp, C.c_int, _vp, _vp]),
     "octgrav_free_tree": (None, [_vp]),
     "octgrav_forces_noalloc": (C.c_int, [_vp, _vp, C.POINTER(C.c_size_t), C.c_double, C.c_double, C.c_double,
                                          _vp, _vp]),
@@ -614,8 +616,9 @@ def mlp_grad(params, x, t, stream=None):
 
 
 def autotune(systems, n_leaf: int = 16, eps: float = 0.01, theta: float = 0.5, candidates=(16, 32, 64, 128),
-             stream=None) -> dict:
-    """Pick n_group and particles-per-lane by timing the kernel on these systems.
+             staging: bool = True, stream=None) -> dict:
+    """Pick n_group, particles-per-lane, list split and (with ``staging``) the
+    staging mode of the cell records by timing the kernel on these systems.
 
     systems: list of (pos [n_s,3], mass [n_s]) pairs (one pair for a single system)."""
     lib = load()
@@ -624,11 +627,18 @@ def autotune(systems, n_leaf: int = 16, eps: float = 0.01, theta: float = 0.5, c
     off = np.zeros(len(systems) + 1, np.int64)
     off[1:] = np.cumsum([len(m) for _, m in systems])
     cand = np.ascontiguousarray(candidates, dtype=np.int32)
-    best = np.zeros(3, np.int32)
+    best = np.zeros(4, np.int32)
+    best[3] = 1
     ms = np.zeros(1)
-    _check(lib.octgrav_autotune(len(systems), off, pos.reshape(-1), mass, int(n_leaf), float(eps), float(theta),
-                                _p(cand), len(cand), _p(best), _p(ms), _stream_handle(stream)))
-    return dict(n_group=int(best[0]), particles_per_lane=int(best[1]), split=int(best[2]), ms=float(ms[0]))
+    if staging:
+        _check(lib.octgrav_autotune_ex(len(systems), off, pos.reshape(-1), mass, int(n_leaf), float(eps),
+                                       float(theta), _p(cand), len(cand), _p(best), 4, _p(ms),
+                                       _stream_handle(stream)))
+    else:
+        _check(lib.octgrav_autotune(len(systems), off, pos.reshape(-1), mass, int(n_leaf), float(eps),
+                                    float(theta), _p(cand), len(cand), _p(best), _p(ms), _stream_handle(stream)))
+    return dict(n_group=int(best[0]), particles_per_lane=int(best[1]), split=int(best[2]), staging=int(best[3]),
+                ms=float(ms[0]))
 
 
 def version() -> int:

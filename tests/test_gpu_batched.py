@@ -78,14 +78,35 @@ def test_graph_replay_equals_direct_launch(torch, systems):
 def test_autotuner_returns_a_valid_configuration(torch, systems):
     best = G.autotune(systems[:12], n_leaf=16, eps=0.01, theta=0.6, candidates=(16, 32, 64))
     assert best["n_group"] in (16, 32, 64) and best["particles_per_lane"] in (1, 2) and best["ms"] > 0
+    assert best["split"] in (1, 2, 4) and best["staging"] in (0, 1, 2)
+    assert best["split"] == 1 or best["staging"] == 1      # a split runs with cp.async staging
     again = G.autotune(systems[:12], n_leaf=16, eps=0.01, theta=0.6, candidates=(16, 32, 64))
     assert again == best                                   # cached
+    plain = G.autotune(systems[:12], n_leaf=16, eps=0.01, theta=0.6, candidates=(16, 32, 64), staging=False)
+    assert plain["staging"] == 1 and plain["n_group"] in (16, 32, 64)
     pos, m = systems[3]
     T = G.Tree.build(pos, m, 16, best["n_group"])
     T.set_launch(best["particles_per_lane"])
+    T.set_staging(best["staging"])
     acc, _ = T.forces(0.01, 0.6)
     ra, _, _, _, _ = O.Tree(pos, m, 16, best["n_group"]).forces(0.01, 0.6)
     assert O.rel_rms(acc, ra) <= TOL_RMS
+
+
+def test_autotuner_cache_tells_distributions_apart(torch):
+    """Same size, theta, eps and N_leaf but a different spread (Plummer sphere vs
+    uniform cube): the second call is tuned, not served from the cache."""
+    import time
+    a = W.plummer(20000, seed=31)
+    b = W.uniform_cube(20000, seed=31)
+    G.autotune([a], n_leaf=16, eps=0.01, theta=0.55, candidates=(32, 64))
+    t0 = time.perf_counter()
+    G.autotune([a], n_leaf=16, eps=0.01, theta=0.55, candidates=(32, 64))
+    cached = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    G.autotune([b], n_leaf=16, eps=0.01, theta=0.55, candidates=(32, 64))
+    tuned = time.perf_counter() - t0
+    assert tuned > 5 * cached
 
 
 def test_one_shot_batched_call_matches_per_system_oracle(torch, systems):
