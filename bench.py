@@ -507,7 +507,8 @@ def learned_leg(torch, G, a, flush, stream, peak, steps, ng=64, train_groups=128
 
 
 def run_learned_driver():
-    """Train on the sphere+disc (seed 6), launch the learned walk twice on seed 5."""
+    """Train on the sphere+disc (seed 6); on seed 5 launch the plain walk at
+    theta 0.93 (its median-1e-3 point) once, then the learned walk twice."""
     import torch
     from paper_1005_5384_gb300 import octgrav as G
     n = 1_048_576
@@ -519,12 +520,16 @@ def run_learned_driver():
     del TT
     pos, m = W.sphere_disc(n, seed=5)
     T = G.Tree.build(pos, m, 16, 256)
-    T.set_criterion(rec, tau=-3.57, theta_lo=0.8, theta_hi=1.3, theta_fb=1.0)
     out = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    T.forces_device(0.01, 0.93, out)
+    torch.cuda.synchronize()
+    plain = T.interaction_counts()
+    T.set_criterion(rec, tau=-3.57, theta_lo=0.8, theta_hi=1.3, theta_fb=1.0)
     for _ in range(2):
         T.forces_device(0.01, 0.5, out)
     torch.cuda.synchronize()
-    print(json.dumps({"status": T.status(), "counts": T.interaction_counts()}), flush=True)
+    print(json.dumps({"status": T.status(), "counts_theta_0.93": plain, "counts_learned": T.interaction_counts()}),
+          flush=True)
 
 
 def run_build_driver(a):
