@@ -368,7 +368,7 @@ int octgrav_graph_launch(octgrav_tree *t, void *stream);
  * fused kernel for every group size in n_group_cand[0..n_cand) (values below
  * n_leaf are skipped), particles-per-lane 1 and 2 and, where the work items
  * are too few to fill the GPU (fewer than 4 per warp slot), list splits of
- * 1, 2 and 4 (octgrav_set_split), and returns the fastest in best[0] =
+ * 1, 2, 4 and 8 (octgrav_set_split), and returns the fastest in best[0] =
  * n_group, best[1] = particles per lane, best[2] = list split, with its
  * median time in *best_ms (may be NULL).
  * Results are cached in-process (see octgrav_autotune_ex for the key). Builds

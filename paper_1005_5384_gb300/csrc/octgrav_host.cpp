@@ -1493,8 +1493,8 @@ static int autotune_common(int n_sys, const int64_t* offsets, const double* pos,
     octgrav_tree* t = nullptr;
     if ((rc = build_common(n_sys, offsets, pos, mass, n_leaf, n_group_cand[c], &t))) break;
     // list splits only where the work items are too few to fill the GPU
-    const int max_split = t->n_items < 4 * 152 * 16 ? 4 : 1;
-    for (int trial = 0; trial < 2 * 3 && rc == OCTGRAV_OK; ++trial) {
+    const int max_split = t->n_items < 4 * 152 * 16 ? 8 : 1;
+    for (int trial = 0; trial < 2 * 4 && rc == OCTGRAV_OK; ++trial) {
       const int ppl = 1 + trial % 2, split = 1 << (trial / 2);
       if (split > max_split) break;
       if ((rc = octgrav_set_launch(t, ppl, 0)) || (rc = octgrav_set_split(t, split))) break;

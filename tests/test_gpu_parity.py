@@ -315,15 +315,18 @@ def test_degenerate_geometries(_cuda, shape):
     assert np.array_equal(acc_g, acc)
 
 
-@pytest.mark.parametrize("nparts", [2, 4])
-def test_list_split_matches_unsplit_and_oracle(_cuda, nparts):
+@pytest.mark.parametrize("nparts,n,n_group,ppl", [(2, 16384, 16, 2), (4, 16384, 16, 2), (4, 16384, 128, 1),
+                                                  (8, 16384, 128, 1), (16, 16384, 64, 2), (4, 200, 16, 2)])
+def test_list_split_matches_unsplit_and_oracle(_cuda, nparts, n, n_group, ppl):
     """List split (a small system's work items walked by several warps, each
     evaluating a share of the lists): the same interaction counts as the
     unsplit launch, forces within FP32 rounding of it and within 1e-5 of the
-    oracle, bitwise reproducible, and the same through a captured graph."""
+    oracle, bitwise reproducible, and the same through a captured graph; from
+    2 to 16 parts, 1 or 2 particles per lane, and a tree of 200 particles."""
     torch = _cuda
-    pos, m = W.plummer(16384, seed=1)
-    T = G.Tree.build(pos, m, 16, 16)
+    pos, m = W.plummer(n, seed=1)
+    T = G.Tree.build(pos, m, 16, n_group)
+    T.set_launch(ppl)
     a1, p1 = T.forces(0.01, 0.5)
     c1 = T.interaction_counts()
     T.set_split(nparts)
@@ -331,7 +334,7 @@ def test_list_split_matches_unsplit_and_oracle(_cuda, nparts):
     c2 = T.interaction_counts()
     assert c1["n_pc"] == c2["n_pc"] and c1["n_pp"] == c2["n_pp"]
     assert O.rel_rms(a2, a1) <= 1e-6
-    R = O.Tree(pos, m, 16, 16)
+    R = O.Tree(pos, m, 16, n_group)
     ra, rp, _, _, _ = R.forces(0.01, 0.5)
     assert O.rel_rms(a2, ra) <= TOL_RMS
     assert float(np.linalg.norm(p2 - rp) / np.linalg.norm(rp)) <= TOL_RMS
@@ -350,3 +353,17 @@ def test_list_split_matches_unsplit_and_oracle(_cuda, nparts):
     assert torch.equal(out, ref)
     with pytest.raises(G.OctgravError):
         T.set_split(0)
+
+
+def test_list_split_on_a_batch(_cuda):
+    """A split launch over many systems in one tree: every system equals its
+    unsplit result within FP32 rounding and the interaction counts agree."""
+    systems = W.ensemble(12, seed=9, n_min=300, n_max=5000)
+    T = G.Tree.build_batch(systems, 16, 64)
+    a1, _ = T.forces(0.01, 0.6)
+    c1 = T.interaction_counts()
+    T.set_split(4)
+    a2, _ = T.forces(0.01, 0.6)
+    c2 = T.interaction_counts()
+    assert c1 == c2
+    assert O.rel_rms(a2, a1) <= 1e-6
