@@ -604,6 +604,41 @@ def mlp_train(features, labels, steps: int = 3000, batch: int = 4096, lr: float 
     return rec, float(loss[0])
 
 
+CRITERION_FORMAT = "octgrav-criterion-1"
+
+
+def save_criterion(path, record, tau: float, theta_lo: float, theta_hi: float, theta_fb: float, **meta):
+    """Save a trained criterion -- the FP32 record of mlp_train (input scaling,
+    training range, network) with the tau and theta band it is used with -- to
+    an .npz file. ``meta`` holds free-form scalars or strings (training system,
+    seed, ...). The network is rounded to BF16 only when the record is set on a
+    tree, so the file keeps the trained FP32 values."""
+    rec = np.ascontiguousarray(record, dtype=np.float32)
+    if rec.shape != (MLP_RECORD,) or not np.all(np.isfinite(rec[:24])):
+        raise ValueError("not a criterion record of %d floats" % MLP_RECORD)
+    band = np.array([tau, theta_lo, theta_hi, theta_fb], np.float64)
+    if not np.all(np.isfinite(band)):
+        raise ValueError("tau and the theta band must be finite")
+    np.savez(path, format=np.array(CRITERION_FORMAT), record=rec, band=band,
+             meta_keys=np.array(list(meta.keys()), dtype=str),
+             meta_values=np.array([str(v) for v in meta.values()], dtype=str))
+
+
+def load_criterion(path) -> dict:
+    """Load a criterion saved by save_criterion: dict(record, tau, theta_lo,
+    theta_hi, theta_fb, meta); ``Tree.set_criterion(**{k: d[k] for k in ...})``
+    applies it. Raises ValueError on a file of another format."""
+    with np.load(path, allow_pickle=False) as z:
+        if "format" not in z.files or str(z["format"]) != CRITERION_FORMAT:
+            raise ValueError("%s is not an octgrav criterion file" % path)
+        rec = z["record"].astype(np.float32)
+        if rec.shape != (MLP_RECORD,):
+            raise ValueError("criterion record has %d floats, expected %d" % (rec.size, MLP_RECORD))
+        tau, lo, hi, fb = (float(v) for v in z["band"])
+        meta = dict(zip((str(k) for k in z["meta_keys"]), (str(v) for v in z["meta_values"])))
+    return dict(record=rec, tau=tau, theta_lo=lo, theta_hi=hi, theta_fb=fb, meta=meta)
+
+
 def mlp_grad(params, x, t, stream=None):
     """GPU gradient of sum (y - t)^2 / (2n) at params over standardised inputs x [n,12]: (grad, loss)."""
     w = np.ascontiguousarray(params, dtype=np.float32)

@@ -162,3 +162,21 @@ def test_host_builds_from_threads_agree():
         assert np.array_equal(perm, ref_perm) and np.array_equal(keys, ref_keys)
         for name in ref_props:
             assert np.array_equal(props[name], ref_props[name]), name
+
+
+def test_criterion_file_round_trip(tmp_path):
+    """A trained criterion saved with its tau and band loads back bit for bit."""
+    rng = np.random.default_rng(4)
+    rec = rng.standard_normal(G.MLP_RECORD).astype(np.float32)
+    rec[12:24] = np.abs(rec[12:24]) + 0.1
+    path = str(tmp_path / "crit.npz")
+    G.save_criterion(path, rec, -3.25, 0.8, 1.3, 1.0, system="sphere+disc seed 6", groups=64)
+    d = G.load_criterion(path)
+    assert np.array_equal(d["record"].view(np.uint32), rec.view(np.uint32))
+    assert (d["tau"], d["theta_lo"], d["theta_hi"], d["theta_fb"]) == (-3.25, 0.8, 1.3, 1.0)
+    assert d["meta"] == {"system": "sphere+disc seed 6", "groups": "64"}
+    np.savez(str(tmp_path / "other.npz"), record=rec)
+    with pytest.raises(ValueError):
+        G.load_criterion(str(tmp_path / "other.npz"))
+    with pytest.raises(ValueError):
+        G.save_criterion(path, rec[:100], -3.0, 0.8, 1.3, 1.0)
