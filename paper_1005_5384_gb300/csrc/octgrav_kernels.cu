@@ -23,7 +23,10 @@
 // lanes (R particles per lane); the warp holds s = 32/w such slices, and slice
 // k evaluates list entries k, k+s, k+2s, ... . Partial sums of the slices are
 // combined with shuffles at the end, so small groups still fill the warp (the
-// paper lost ~70% of its threads to part-filled groups, Sec. 3.3).
+// paper lost ~70% of its threads to part-filled groups, Sec. 3.3). Every
+// arithmetic op is a packed FP32x2 op: with R = 2 its halves are the lane's two
+// particles and the cell or source fields are broadcast; with R = 1 its halves
+// are two records.
 //
 // Precision: positions are group-relative FP32, x' = (x_hi - C_hi) + (x_lo - C_lo)
 // with C the group centre kept as a hi/lo float pair; sums are accumulated in
@@ -33,6 +36,7 @@
 #include <stdint.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "../../include/octgrav.h"
 #include "octgrav_internal.h"
@@ -270,6 +274,7 @@ struct Acc4 {
 // below evaluates two interactions at once, halving the issued instructions.
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 rsqrt2(float2 a) { return make_float2(rsqrt_ftz(a.x), rsqrt_ftz(a.y)); }
@@ -332,6 +337,59 @@ __device__ __forceinline__ void body_body2(float2 X, float2 Y, float2 Z, float2 
   a.p = add2(a.p, nmr);       // -= m_j / r
 }
 
+// ---- particle-packed evaluation (two particles per lane): the halves of
+// every packed operation are two particles of the group, and the cell or
+// source quantities enter as one value broadcast to both halves.
+
+// One cell record for the particle-packed layout (48 bytes = three 16-byte
+// loads): centre of mass relative to the group centre, negated, -M, S3 = 3S
+// (xx, yy, zz, xy, xz, yz), 3T and T = tr(S)/2.
+struct CellRec {
+  float ncx, ncy, ncz, nM, sxx, syy, szz, sxy, sxz, syz, t3, t;
+};
+constexpr int CREC = 3;  // float4 per cell record in the evaluated tile
+static_assert(16 * CREC <= 64, "packed cell records must fit the tile's ring slots");
+static_assert(16 * 32 + 4 * 32 <= 32 * 32, "packed sources and indices must fit a chunk");
+
+// Particle-cell interaction of two particles (X, Y, Z halves) with one cell:
+// the same expansion as body_cell2.
+__device__ __forceinline__ void body_cellP(float2 X, float2 Y, float2 Z, float2 eps2, const CellRec& c,
+                                           Acc2& a) {
+  const float2 dx = add2(X, f2(c.ncx)), dy = add2(Y, f2(c.ncy)), dz = add2(Z, f2(c.ncz));
+  const float2 r2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, eps2)));
+  const float2 rinv = rsqrt2(r2);
+  const float2 rinv2 = mul2(rinv, rinv);
+  const float2 rinv3 = mul2(rinv, rinv2);
+  const float2 rinv5 = mul2(rinv3, rinv2);
+  const float2 sx = fma2(f2(c.sxx), dx, fma2(f2(c.sxy), dy, mul2(f2(c.sxz), dz)));
+  const float2 sy = fma2(f2(c.sxy), dx, fma2(f2(c.syy), dy, mul2(f2(c.syz), dz)));
+  const float2 sz = fma2(f2(c.sxz), dx, fma2(f2(c.syz), dy, mul2(f2(c.szz), dz)));
+  const float2 q = fma2(dx, sx, fma2(dy, sy, mul2(dz, sz)));
+  const float2 t1 = mul2(q, rinv2);
+  const float2 t2 = fma2(f2(-2.5f), t1, f2(c.t3));
+  const float2 cd = mul2(fma2(t2, rinv2, f2(c.nM)), rinv3);
+  a.x = fma2(cd, dx, fma2(rinv5, sx, a.x));
+  a.y = fma2(cd, dy, fma2(rinv5, sy, a.y));
+  a.z = fma2(cd, dz, fma2(rinv5, sz, a.z));
+  const float2 np2 = fma2(fma2(f2(-0.5f), t1, f2(c.t)), rinv2, f2(c.nM));
+  a.p = fma2(np2, rinv, a.p);
+}
+
+// Particle-particle interaction of two particles with one source (negated
+// relative position sx, sy, sz); nm = -m_j per half (0 drops a term).
+__device__ __forceinline__ void body_bodyP(float2 X, float2 Y, float2 Z, float2 eps2, float sx, float sy, float sz,
+                                           float2 nm, Acc2& a) {
+  const float2 dx = add2(X, f2(sx)), dy = add2(Y, f2(sy)), dz = add2(Z, f2(sz));
+  const float2 r2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, eps2)));
+  const float2 rinv = rsqrt2(r2);
+  const float2 nmr = mul2(nm, rinv);
+  const float2 nmr3 = mul2(nmr, mul2(rinv, rinv));
+  a.x = fma2(nmr3, dx, a.x);
+  a.y = fma2(nmr3, dy, a.y);
+  a.z = fma2(nmr3, dz, a.z);
+  a.p = add2(a.p, nmr);
+}
+
 // Error-free transformation: hi + t = s + e exactly.
 __device__ __forceinline__ void two_sum_into(float& hi, float& lo, float t) {
   const float s = hi + t;
@@ -361,6 +419,38 @@ struct Particles {
   }
 };
 
+// Packed TwoSum of both halves: hi + t = s + e exactly in each half.
+__device__ __forceinline__ void two_sum_into2(float2& hi, float2& lo, float2 t) {
+  const float2 s = add2(hi, t);
+  const float2 bp = sub2(s, hi);
+  const float2 e = add2(sub2(hi, sub2(s, bp)), sub2(t, bp));
+  hi = s;
+  lo = add2(lo, e);
+}
+
+// Two particles per lane in the halves of every register (particle-packed
+// layout): positions, partial sums since the last fold and compensated
+// accumulators (value = hi + lo), each half one particle.
+struct ParticlesP {
+  float2 X, Y, Z;
+  int idx[2];  // tree positions, -1 for an empty slot
+  Acc2 part;
+  Acc2 hi, lo;
+
+  __device__ __forceinline__ void fold() {
+    two_sum_into2(hi.x, lo.x, part.x);
+    two_sum_into2(hi.y, lo.y, part.y);
+    two_sum_into2(hi.z, lo.z, part.z);
+    two_sum_into2(hi.p, lo.p, part.p);
+    part.x = part.y = part.z = part.p = f2(0.f);
+  }
+};
+
+__device__ __forceinline__ CellRec load_cell_rec(const float4* q) {
+  const float4 a = q[0], b = q[1], c = q[2];
+  return CellRec{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+}
+
 __device__ __forceinline__ CellPair load_cell_pair(const float4* q) {
   const float4 a = q[0], b = q[1], c = q[2], d = q[3], e = q[4], f = q[5];
   return CellPair{make_float2(a.x, a.y), make_float2(a.z, a.w), make_float2(b.x, b.y), make_float2(b.z, b.w),
@@ -388,6 +478,7 @@ __global__ void __launch_bounds__(CtaWarps<MLP>::v * 32, MLP ? 1 : 2) walk_eval_
   constexpr int REC = RingStride<STAGE>::v;
   using WarpSmem = WarpSmemT<STAGE == STAGE_GATHER4, MLP>;
   constexpr int STK = MLP ? STACK_MLP : STACK;
+  constexpr bool PK = (R == 2);  // particle-packed evaluation
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   // align to 128 B by offsetting the shared array itself (keeps the
@@ -462,7 +553,10 @@ __global__ void __launch_bounds__(CtaWarps<MLP>::v * 32, MLP ? 1 : 2) walk_eval_
     const int wl = lane - sl * w;
     const bool act = sl < s;
 
-    Particles<R> P;
+    // two particles per lane are packed into the halves of every operation
+    // (PK); one particle per lane takes the records in pairs instead
+    std::conditional_t<PK, ParticlesP, Particles<R>> P;
+    float px[R], py[R], pz[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int k = wl + r * w;
@@ -476,11 +570,26 @@ __global__ void __launch_bounds__(CtaWarps<MLP>::v * 32, MLP ? 1 : 2) walk_eval_
         y = (h4.y - chi.y) + (l4.y - clo.y);
         z = (h4.z - chi.z) + (l4.z - clo.z);
       }
-      P.X[r] = f2(x);
-      P.Y[r] = f2(y);
-      P.Z[r] = f2(z);
-      P.part[r].x = P.part[r].y = P.part[r].z = P.part[r].p = f2(0.f);
-      P.hi[r] = P.lo[r] = Acc4{0.f, 0.f, 0.f, 0.f};
+      px[r] = x;
+      py[r] = y;
+      pz[r] = z;
+    }
+    if constexpr (PK) {
+      P.X = make_float2(px[0], px[1]);
+      P.Y = make_float2(py[0], py[1]);
+      P.Z = make_float2(pz[0], pz[1]);
+      P.part.x = P.part.y = P.part.z = P.part.p = f2(0.f);
+      P.hi = P.part;
+      P.lo = P.part;
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        P.X[r] = f2(px[r]);
+        P.Y[r] = f2(py[r]);
+        P.Z[r] = f2(pz[r]);
+        P.part[r].x = P.part[r].y = P.part[r].z = P.part[r].p = f2(0.f);
+        P.hi[r] = P.lo[r] = Acc4{0.f, 0.f, 0.f, 0.f};
+      }
     }
     int nsince = 0;  // tiles since the last fold
 
@@ -511,18 +620,39 @@ __global__ void __launch_bounds__(CtaWarps<MLP>::v * 32, MLP ? 1 : 2) walk_eval_
       }
       __syncwarp();
       const int npad = (n + 1) & ~1;
-      if (lane < npad) {
-        float* dst = reinterpret_cast<float*>(base) + 4 * CPAIR * (lane >> 1) + (lane & 1);
+      if constexpr (PK) {
+        // record e -> three float4 at 48-byte stride; an odd last record is
+        // followed by a zero record (M = 0, S = 0: no contribution)
+        if (lane < npad) {
+          float4* dst = base + CREC * lane;
+          dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+          dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+          dst[2] = make_float4(v[8], v[9], v[10], v[11]);
+        }
+        __syncwarp();
+        if (act) {
+          const float4* pb = base;
+          for (int k = sl; k < npad / 2; k += s) {  // records 2k and 2k+1
+            const CellRec c0 = load_cell_rec(pb + CREC * (2 * k));
+            const CellRec c1 = load_cell_rec(pb + CREC * (2 * k + 1));
+            body_cellP(P.X, P.Y, P.Z, E2, c0, P.part);
+            body_cellP(P.X, P.Y, P.Z, E2, c1, P.part);
+          }
+        }
+      } else {
+        if (lane < npad) {
+          float* dst = reinterpret_cast<float*>(base) + 4 * CPAIR * (lane >> 1) + (lane & 1);
 #pragma unroll
-        for (int f = 0; f < 12; ++f) dst[2 * f] = v[f];
-      }
-      __syncwarp();
-      if (act) {
-        const float4* pb = base;
-        for (int k = sl; k < npad / 2; k += s) {
-          const CellPair c = load_cell_pair(pb + CPAIR * k);
+          for (int f = 0; f < 12; ++f) dst[2 * f] = v[f];
+        }
+        __syncwarp();
+        if (act) {
+          const float4* pb = base;
+          for (int k = sl; k < npad / 2; k += s) {
+            const CellPair c = load_cell_pair(pb + CPAIR * k);
 #pragma unroll
-          for (int r = 0; r < R; ++r) body_cell2(P.X[r], P.Y[r], P.Z[r], E2, c, P.part[r]);
+            for (int r = 0; r < R; ++r) body_cell2(P.X[r], P.Y[r], P.Z[r], E2, c, P.part[r]);
+          }
         }
       }
       if (++nsince >= FOLD_EVERY * s) {
@@ -588,6 +718,34 @@ __global__ void __launch_bounds__(CtaWarps<MLP>::v * 32, MLP ? 1 : 2) walk_eval_
           nm = -h4.w;
         }
         __syncwarp();
+        if constexpr (PK) {
+          // source e -> one float4 (negated relative position, negated mass);
+          // an odd last source is followed by zeros (no contribution)
+          if (lane < npad) {
+            buf[lane] = make_float4(nx, ny, nz, nm);
+            if (own) reinterpret_cast<int*>(buf)[4 * PCH + lane] = j_cur;  // source index
+          }
+          __syncwarp();
+          if (act) {
+            if (own) {
+              const int* jj = reinterpret_cast<const int*>(buf) + 4 * PCH;
+              for (int e = sl; e < npad / 2; e += s) {
+                const float4 q0 = buf[2 * e], q1 = buf[2 * e + 1];
+                const int ja = jj[2 * e], jb = jj[2 * e + 1];
+                const float2 m0 = make_float2(ja == P.idx[0] ? 0.f : q0.w, ja == P.idx[1] ? 0.f : q0.w);
+                const float2 m1 = make_float2(jb == P.idx[0] ? 0.f : q1.w, jb == P.idx[1] ? 0.f : q1.w);
+                body_bodyP(P.X, P.Y, P.Z, E2, q0.x, q0.y, q0.z, m0, P.part);
+                body_bodyP(P.X, P.Y, P.Z, E2, q1.x, q1.y, q1.z, m1, P.part);
+              }
+            } else {
+              for (int e = sl; e < npad / 2; e += s) {
+                const float4 q0 = buf[2 * e], q1 = buf[2 * e + 1];
+                body_bodyP(P.X, P.Y, P.Z, E2, q0.x, q0.y, q0.z, f2(q0.w), P.part);
+                body_bodyP(P.X, P.Y, P.Z, E2, q1.x, q1.y, q1.z, f2(q1.w), P.part);
+              }
+            }
+          }
+        } else {
         if (lane < npad) {
           float* dst = reinterpret_cast<float*>(buf) + 4 * SPAIR * (lane >> 1) + (lane & 1);
           dst[0] = nx;
@@ -616,6 +774,7 @@ __global__ void __launch_bounds__(CtaWarps<MLP>::v * 32, MLP ? 1 : 2) walk_eval_
               for (int r = 0; r < R; ++r) body_body2(P.X[r], P.Y[r], P.Z[r], E2, q, q.nm, P.part[r]);
             }
           }
+        }
         }
         if (++nsince >= FOLD_EVERY * s) {
           P.fold();
@@ -906,24 +1065,38 @@ __global__ void __launch_bounds__(CtaWarps<MLP>::v * 32, MLP ? 1 : 2) walk_eval_
     if (nlq > 0) eval_leaves(nlq);
     P.fold();
 
+    // ---- per-particle compensated sums (value = hi + lo)
+    Acc4 H[R], L[R];
+    if constexpr (PK) {
+      H[0] = Acc4{P.hi.x.x, P.hi.y.x, P.hi.z.x, P.hi.p.x};
+      L[0] = Acc4{P.lo.x.x, P.lo.y.x, P.lo.z.x, P.lo.p.x};
+      H[1] = Acc4{P.hi.x.y, P.hi.y.y, P.hi.z.y, P.hi.p.y};
+      L[1] = Acc4{P.lo.x.y, P.lo.y.y, P.lo.z.y, P.lo.p.y};
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        H[r] = P.hi[r];
+        L[r] = P.lo[r];
+      }
+    }
     // ---- combine the slices (lane wl of slice 0 gathers lanes wl + k*w)
     for (int kk = 1; kk < s; ++kk) {
       const int src = min(31, lane + kk * w);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        const float hx = __shfl_sync(FULL, P.hi[r].x, src), lx = __shfl_sync(FULL, P.lo[r].x, src);
-        const float hy = __shfl_sync(FULL, P.hi[r].y, src), ly = __shfl_sync(FULL, P.lo[r].y, src);
-        const float hz = __shfl_sync(FULL, P.hi[r].z, src), lz = __shfl_sync(FULL, P.lo[r].z, src);
-        const float hp = __shfl_sync(FULL, P.hi[r].p, src), lp = __shfl_sync(FULL, P.lo[r].p, src);
+        const float hx = __shfl_sync(FULL, H[r].x, src), lx = __shfl_sync(FULL, L[r].x, src);
+        const float hy = __shfl_sync(FULL, H[r].y, src), ly = __shfl_sync(FULL, L[r].y, src);
+        const float hz = __shfl_sync(FULL, H[r].z, src), lz = __shfl_sync(FULL, L[r].z, src);
+        const float hp = __shfl_sync(FULL, H[r].p, src), lp = __shfl_sync(FULL, L[r].p, src);
         if (sl == 0) {
-          two_sum_into(P.hi[r].x, P.lo[r].x, hx);
-          P.lo[r].x += lx;
-          two_sum_into(P.hi[r].y, P.lo[r].y, hy);
-          P.lo[r].y += ly;
-          two_sum_into(P.hi[r].z, P.lo[r].z, hz);
-          P.lo[r].z += lz;
-          two_sum_into(P.hi[r].p, P.lo[r].p, hp);
-          P.lo[r].p += lp;
+          two_sum_into(H[r].x, L[r].x, hx);
+          L[r].x += lx;
+          two_sum_into(H[r].y, L[r].y, hy);
+          L[r].y += ly;
+          two_sum_into(H[r].z, L[r].z, hz);
+          L[r].z += lz;
+          two_sum_into(H[r].p, L[r].p, hp);
+          L[r].p += lp;
         }
       }
     }
@@ -931,8 +1104,8 @@ __global__ void __launch_bounds__(CtaWarps<MLP>::v * 32, MLP ? 1 : 2) walk_eval_
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         if (P.idx[r] >= 0) {
-          const float4 v = make_float4(G * (P.hi[r].x + P.lo[r].x), G * (P.hi[r].y + P.lo[r].y),
-                                       G * (P.hi[r].z + P.lo[r].z), G * (P.hi[r].p + P.lo[r].p));
+          const float4 v = make_float4(G * (H[r].x + L[r].x), G * (H[r].y + L[r].y),
+                                       G * (H[r].z + L[r].z), G * (H[r].p + L[r].p));
           if (SPLIT)
             p.part_out[static_cast<size_t>(part) * p.n + P.idx[r]] = v;
           else
