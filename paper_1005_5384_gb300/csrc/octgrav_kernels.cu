@@ -464,9 +464,11 @@ __device__ __forceinline__ SrcPair load_src_pair(const float4* q) {
 
 // ---------------------------------------------------------------- the kernel
 
-// The learned-criterion kernel runs one CTA of 12 warps per SM: the network
-// step needs registers beyond the 128 a two-CTA launch leaves per thread.
-constexpr int WARPS_MLP = 12;
+// The learned-criterion kernel runs one CTA of 16 warps per SM (at most 128
+// registers per thread, as the plain kernel's two CTAs of 8 warps): its
+// network fragments and feature inputs fit, and its larger shared memory
+// (the network, a candidate queue per warp) needs one CTA.
+constexpr int WARPS_MLP = 16;
 
 template <bool MLP>
 struct CtaWarps {
