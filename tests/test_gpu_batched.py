@@ -93,6 +93,27 @@ def test_autotuner_returns_a_valid_configuration(torch, systems):
     assert O.rel_rms(acc, ra) <= TOL_RMS
 
 
+def test_autotuner_ex_writes_at_most_n_best_values(torch, systems):
+    """octgrav_autotune_ex fills min(n_best, 4) values and refuses n_best < 1."""
+    import ctypes as C
+    lib = G.load()
+    sub = systems[:4]
+    pos = np.ascontiguousarray(np.concatenate([p for p, _ in sub]))
+    mass = np.ascontiguousarray(np.concatenate([m for _, m in sub]))
+    off = np.zeros(len(sub) + 1, np.int64)
+    off[1:] = np.cumsum([len(m) for _, m in sub])
+    cand = np.array([16, 32], np.int32)
+    best = np.full(6, -7, np.int32)
+    ms = np.zeros(1)
+    rc = lib.octgrav_autotune_ex(len(sub), off, pos.reshape(-1), mass, 16, 0.01, 0.6, cand.ctypes.data, 2,
+                                 best.ctypes.data, 2, ms.ctypes.data, None)
+    assert rc == G.OK, lib.octgrav_last_error()
+    assert best[0] in (16, 32) and best[1] in (1, 2) and np.all(best[2:] == -7) and ms[0] > 0
+    rc = lib.octgrav_autotune_ex(len(sub), off, pos.reshape(-1), mass, 16, 0.01, 0.6, cand.ctypes.data, 2,
+                                 best.ctypes.data, 0, ms.ctypes.data, None)
+    assert rc == G.ERR_ARG
+
+
 def test_autotuner_cache_tells_distributions_apart(torch):
     """Same size, theta, eps and N_leaf but a different spread (Plummer sphere vs
     uniform cube): the second call is tuned, not served from the cache."""

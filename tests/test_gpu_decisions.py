@@ -366,3 +366,25 @@ def test_list_parity_ensemble_batch(torch):
     for s in need:
         Rs[s] = O.Tree(systems[s][0], systems[s][1], 16, 256)
     _list_parity(T, Rs, 0.6, items, sys_of_item=True)
+
+
+def test_debug_walk_subset_equals_full_capture_and_refusals(torch):
+    """A capture of chosen work items returns exactly the rows of a full capture;
+    bad item lists are refused and the tree stays usable."""
+    pos, m = W.plummer(20000, seed=4)
+    T = G.Tree.build(pos, m, 16, 64)
+    full = T.debug_walk(0.5, cap=4096)
+    sel = np.array([7, 0, T.stats["n_items"] - 1, 123])
+    part = T.debug_walk(0.5, items=sel, cap=4096)
+    for r, it in enumerate(sel):
+        assert np.array_equal(part[r]["cells"], full[it]["cells"])
+        assert np.array_equal(part[r]["leaves"], full[it]["leaves"])
+    for bad in ([0, 0], [-1], [T.stats["n_items"]]):
+        with pytest.raises(G.OctgravError) as e:
+            T.debug_walk(0.5, items=np.array(bad), cap=4096)
+        assert e.value.code == G.ERR_ARG
+    with pytest.raises(G.OctgravError) as e:
+        T.debug_walk(0.5, items=sel, cap=2)  # lists longer than the capture buffer
+    assert e.value.code == G.ERR_LIST
+    assert T.debug_walk(0.5, items=sel[:1], cap=4096)[0]["cells"].size == full[7]["cells"].size
+    assert T.debug_walk(0.5, items=np.array([], np.int64), cap=16) == []
