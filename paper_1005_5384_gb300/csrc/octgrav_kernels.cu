@@ -352,25 +352,25 @@ static_assert(16 * CREC <= 64, "packed cell records must fit the tile's ring slo
 static_assert(16 * 32 + 4 * 32 <= 32 * 32, "packed sources and indices must fit a chunk");
 
 // Particle-cell interaction of two particles (X, Y, Z halves) with one cell:
-// the same expansion as body_cell2.
+// the same expansion as body_cell2, with the monopole folded into the bracket,
+//   a += (S3 d + (3T - 2.5 q/r^2 - M r^2) d) / r^5
+// (33 packed operations for two interactions).
 __device__ __forceinline__ void body_cellP(float2 X, float2 Y, float2 Z, float2 eps2, const CellRec& c,
                                            Acc2& a) {
   const float2 dx = add2(X, f2(c.ncx)), dy = add2(Y, f2(c.ncy)), dz = add2(Z, f2(c.ncz));
   const float2 r2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, eps2)));
   const float2 rinv = rsqrt2(r2);
   const float2 rinv2 = mul2(rinv, rinv);
-  const float2 rinv3 = mul2(rinv, rinv2);
-  const float2 rinv5 = mul2(rinv3, rinv2);
+  const float2 rinv5 = mul2(mul2(rinv, rinv2), rinv2);
   const float2 sx = fma2(f2(c.sxx), dx, fma2(f2(c.sxy), dy, mul2(f2(c.sxz), dz)));
   const float2 sy = fma2(f2(c.sxy), dx, fma2(f2(c.syy), dy, mul2(f2(c.syz), dz)));
   const float2 sz = fma2(f2(c.sxz), dx, fma2(f2(c.syz), dy, mul2(f2(c.szz), dz)));
   const float2 q = fma2(dx, sx, fma2(dy, sy, mul2(dz, sz)));
   const float2 t1 = mul2(q, rinv2);
-  const float2 t2 = fma2(f2(-2.5f), t1, f2(c.t3));
-  const float2 cd = mul2(fma2(t2, rinv2, f2(c.nM)), rinv3);
-  a.x = fma2(cd, dx, fma2(rinv5, sx, a.x));
-  a.y = fma2(cd, dy, fma2(rinv5, sy, a.y));
-  a.z = fma2(cd, dz, fma2(rinv5, sz, a.z));
+  const float2 cb = fma2(f2(c.nM), r2, fma2(f2(-2.5f), t1, f2(c.t3)));  // 3T - 2.5 q/r^2 - M r^2
+  a.x = fma2(rinv5, fma2(cb, dx, sx), a.x);
+  a.y = fma2(rinv5, fma2(cb, dy, sy), a.y);
+  a.z = fma2(rinv5, fma2(cb, dz, sz), a.z);
   const float2 np2 = fma2(fma2(f2(-0.5f), t1, f2(c.t)), rinv2, f2(c.nM));
   a.p = fma2(np2, rinv, a.p);
 }
