@@ -299,7 +299,13 @@ int octgrav_tree_cell_props(const octgrav_tree *t, double *bmin, double *bmax, d
                             double *mass, double *com, double *S, int64_t *count);
 
 /* Per work item: key of its group cell, first tree position, particle count,
- * system index (arrays of n_items entries; any may be NULL). */
+ * system index (arrays of n_items entries; any may be NULL). A group of c
+ * particles is cut into items of 32*ppl particles (octgrav_set_launch) and one
+ * item for the rest r = c mod 32*ppl; with two particles per lane and the
+ * plain criterion a rest of 33..56 becomes two items, 32 and r - 32
+ * (a 33..56-particle item would leave lanes of its warp idle). Under a learned
+ * criterion (octgrav_set_criterion) the rest stays whole: the network step
+ * would run for both pieces. The host and the GPU build cut the same items. */
 int octgrav_item_info(const octgrav_tree *t, uint64_t *group_key, int64_t *first,
                       int32_t *count, int32_t *sys);
 
@@ -336,8 +342,8 @@ int octgrav_debug_walk(octgrav_tree *t, double theta, int64_t n_sel, const int64
 
 /* Order in which later launches on this tree take the work items (the
  * persistent kernel's tail is shorter when the biggest items go first).
- * Every new tree (and every octgrav_set_launch that rebuilds the items)
- * starts with mode 2. mode 2: most particles first. mode 1: longest first by
+ * Every new tree (and every octgrav_set_launch or octgrav_set_criterion call
+ * that cuts the items again) starts with mode 2. mode 2: most particles first. mode 1: longest first by
  * the cost of each item in the last launch (its particles times 70 n_pc +
  * 38 n_pp, that launch's interaction counts) -- an N-body code evaluating
  * the same tree again, or reusing the previous step's costs. mode 0: tree
@@ -347,15 +353,20 @@ int octgrav_debug_walk(octgrav_tree *t, double theta, int64_t n_sel, const int64
 int octgrav_balance(octgrav_tree *t, int mode, void *stream);
 
 /* Choose the kernel variant: particles per lane (1 or 2; work items hold at
- * most 32*ppl particles) and CTAs per SM (0 = as many as fit). Applies to
- * later launches on this tree; n_items may change. Errors: ERR_ARG. */
+ * most 32*ppl particles, cut as octgrav_item_info says) and CTAs per SM
+ * (0 = as many as fit). Applies to later launches on this tree; a change of
+ * ppl cuts the work items again (n_items may change, the order returns to
+ * mode 2 of octgrav_balance, a captured graph is dropped).
+ * Errors: ERR_ARG, ERR_CUDA (GPU-built tree). */
 int octgrav_set_launch(octgrav_tree *t, int particles_per_lane, int ctas_per_sm);
 
 /* Capture one octgrav_forces_device call (status reset + the persistent
  * walk/evaluation kernel) into a CUDA graph owned by the tree, for replay
  * with octgrav_graph_launch. Uploads the tree first if needed. stream must
  * be a non-default stream; acc4_dev is baked into the graph. The arguments
- * follow octgrav_forces_device. Errors: ERR_ARG, ERR_CUDA. */
+ * follow octgrav_forces_device. A call that cuts the work items again
+ * (octgrav_set_launch, octgrav_set_criterion) drops the graph.
+ * Errors: ERR_ARG, ERR_CUDA. */
 int octgrav_graph_capture(octgrav_tree *t, double eps, double theta, double G, float *acc4_dev,
                           void *stream);
 
@@ -441,7 +452,10 @@ int octgrav_mlp_grad(const float *params, const float *x, const float *t, int64_
  * accepted when its cube has h = 0, and otherwise accepted iff the network's
  * prediction is below tau; a child whose standardised inputs leave the
  * training range falls back to the plain test with theta_fb. The launch's own
- * theta argument is then unused. Errors: ERR_ARG, ERR_CUDA. */
+ * theta argument is then unused. Switching between the plain and the learned
+ * criterion cuts the work items again (see octgrav_item_info; as after a
+ * change of ppl in octgrav_set_launch); a new record on a tree that already
+ * has one keeps them. Errors: ERR_ARG, ERR_CUDA. */
 int octgrav_set_criterion(octgrav_tree *t, const float *record, double tau, double theta_lo,
                           double theta_hi, double theta_fb);
 

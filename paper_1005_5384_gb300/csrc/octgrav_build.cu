@@ -961,17 +961,17 @@ __global__ void k_group_emit(int64_t n, const int* __restrict__ gmark, const int
 }
 
 __global__ void k_item_count(const int* __restrict__ n_groups, const int* __restrict__ group_cell,
-                             const int* __restrict__ pcount, int item_max, int* __restrict__ nitem) {
+                             const int* __restrict__ pcount, int item_max, int split, int* __restrict__ nitem) {
   const int ng = *n_groups;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x)
-    nitem[g] = (pcount[group_cell[g]] + item_max - 1) / item_max;
+    nitem[g] = item_count(pcount[group_cell[g]], item_max, split != 0);
 }
 
-// Work items of every group: at most item_max particles each, all with the
-// group's box, centre (hi/lo) and particle range.
+// Work items of every group, cut by next_item_size (at most item_max
+// particles each), all with the group's box, centre (hi/lo) and particle range.
 __global__ void k_items(const int* __restrict__ n_groups, const int* __restrict__ group_cell,
                         const int* __restrict__ group_sys, const int* __restrict__ ioff, const int64_t* __restrict__ cell_off,
-                        Props P, int item_max, int4* __restrict__ items, float4* __restrict__ ibox,
+                        Props P, int item_max, int split, int4* __restrict__ items, float4* __restrict__ ibox,
                         uint64_t* __restrict__ item_key, int* __restrict__ group_item) {
   const int ng = *n_groups;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
@@ -992,8 +992,9 @@ __global__ void k_items(const int* __restrict__ n_groups, const int* __restrict_
     const int root = static_cast<int>(cell_off[s]);
     int k = ioff[g];
     group_item[g] = k;
-    for (int off = 0; off < cnt; off += item_max, ++k) {
-      items[k] = make_int4(root, pf + off, min(item_max, cnt - off), s);
+    for (int off = 0, sz; off < cnt; off += sz, ++k) {
+      sz = next_item_size(cnt - off, item_max, split != 0);
+      items[k] = make_int4(root, pf + off, sz, s);
       ibox[4 * static_cast<int64_t>(k)] = b0;
       ibox[4 * static_cast<int64_t>(k) + 1] = b1;
       ibox[4 * static_cast<int64_t>(k) + 2] = b2;
@@ -1090,12 +1091,13 @@ cudaError_t enqueue_items(const GpuBuild& a, const Layout& Lo, int item_max, cud
   const int nmax = static_cast<int>(a.n);
   const int nb = static_cast<int>((a.n + TILE - 1) / TILE);
   Props P{a.bmin, a.bmax, a.cube, a.M, a.com, a.S, a.key, a.geo, a.link, a.mp, a.pcount, a.cfirst};
-  k_item_count<<<grid_for(a.n, TB), TB, 0, st>>>(&misc[M_NGROUPS], a.group_cell, a.pcount, item_max, nitem);
+  k_item_count<<<grid_for(a.n, TB), TB, 0, st>>>(&misc[M_NGROUPS], a.group_cell, a.pcount, item_max, a.item_split,
+                                                 nitem);
   k_scan_reduce<<<nb, TB, 0, st>>>(nitem, &misc[M_NGROUPS], nmax, sblk);
   k_scan_single<<<1, 1024, 0, st>>>(sblk, nullptr, nb, &misc[M_NITEMS]);
   k_scan_down<<<nb, TB, 0, st>>>(nitem, &misc[M_NGROUPS], nmax, sblk, ioff);
   k_items<<<grid_for(a.n, TB), TB, 0, st>>>(&misc[M_NGROUPS], a.group_cell, a.group_sys, ioff, a.cell_off, P,
-                                            item_max, a.items, a.ibox, a.item_key, a.group_item);
+                                            item_max, a.item_split, a.items, a.ibox, a.item_key, a.group_item);
   int* ihist = at<int>(a.scratch, Lo.ihist);
   cudaError_t e = cudaMemsetAsync(ihist, 0, 4 * 2 * IBINS, st);
   if (e != cudaSuccess) return e;
@@ -1281,7 +1283,8 @@ cudaError_t gpu_refit(const GpuBuild& a, cudaStream_t st) {
   k_leaf_props<<<gc, TB, 0, st>>>(C, at<int>(S, Lo.lorder), misc, ni, at<double>(S, Lo.xs), at<double>(S, Lo.ms), P);
   for (int L = MAXD - 1; L >= 0; --L) k_node_props<<<gc, TB, 0, st>>>(L, C, lvl, ni, P);
   k_items<<<grid_for(a.n, TB), TB, 0, st>>>(&misc[M_NGROUPS], a.group_cell, a.group_sys, at<int>(S, Lo.ioff),
-                                            a.cell_off, P, a.item_max, a.items, a.ibox, a.item_key, a.group_item);
+                                            a.cell_off, P, a.item_max, a.item_split, a.items, a.ibox, a.item_key,
+                                            a.group_item);
   k_finish<<<1, 1, 0, st>>>(lvl, misc, a.result);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return cudaSuccess;

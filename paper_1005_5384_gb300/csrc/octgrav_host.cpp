@@ -434,6 +434,7 @@ og::GpuBuild gpu_args(octgrav_tree* t, const int64_t* offsets, const double* pos
   a.n_leaf = t->n_leaf;
   a.n_group = t->n_group;
   a.item_max = 32 * t->ppl;
+  a.item_split = item_split(t) ? 1 : 0;
   a.max_level = OCTGRAV_MAX_DEPTH;
   a.cap = cap;
   a.scratch = D.scratch.p;
@@ -483,7 +484,7 @@ int reserve_gpu_tree(Device& D, int64_t n, int n_sys, int64_t cap) {
 std::vector<int64_t> build_key(const og::GpuBuild& a) {
   auto P = [](const void* q) { return static_cast<int64_t>(reinterpret_cast<uintptr_t>(q)); };
   std::vector<int64_t> k = {P(a.pos),     P(a.mass),     a.n,           a.n_sys,       a.n_leaf,       a.n_group,
-                            a.item_max,   a.max_level,   a.cap,         P(a.scratch),  static_cast<int64_t>(a.scratch_bytes),
+                            a.item_max,   a.item_split, a.max_level,   a.cap,         P(a.scratch),  static_cast<int64_t>(a.scratch_bytes),
                             P(a.parts),   P(a.perm),     P(a.key),      P(a.geo),      P(a.link),      P(a.mp),
                             P(a.bmin),    P(a.bmax),     P(a.cube),     P(a.M),        P(a.com),       P(a.S),
                             P(a.pcount),  P(a.cfirst),   P(a.group_cell), P(a.group_sys), P(a.group_item),
@@ -675,6 +676,30 @@ int host_images(octgrav_tree* t) {
   for (int64_t k = 0; k < n; ++k) t->perm[k] = p32[k];
   for (int64_t c = 0; c < nc; ++c) t->pcount[c] = c32[c];
   t->host_valid = true;
+  return OCTGRAV_OK;
+}
+
+// Cut the work items again (after a change of ppl or of the item rule) with
+// their default order, on the device for a GPU-built tree. A captured graph
+// refers to the old items and is dropped.
+int rebuild_items(octgrav_tree* t) {
+  if (t->gexec) {
+    cudaGraphExecDestroy(t->gexec);
+    t->gexec = nullptr;
+  }
+  if (t->gpu) {
+    const og::GpuBuild a = gpu_args(t, t->sys_off.data(), nullptr, nullptr);
+    cudaError_t e = og::gpu_build_items(a, nullptr);
+    if (e != cudaSuccess) return fail(OCTGRAV_ERR_CUDA, "GPU item build failed: %s", cudaGetErrorString(e));
+    int64_t res[og::GB_COUNT];
+    if (int rc = gpu_result(t, nullptr, res)) return rc;
+    t->n_items = res[og::GB_NITEMS];
+    t->ordered = true;
+    t->host_valid = false;
+    return t->dev->counts.reserve(t->n_items * sizeof(int2));
+  }
+  make_items(t);
+  t->uploaded = false;
   return OCTGRAV_OK;
 }
 
@@ -1250,20 +1275,7 @@ int octgrav_set_launch(octgrav_tree* t, int particles_per_lane, int ctas_per_sm)
   t->ctas_per_sm = ctas_per_sm;
   if (particles_per_lane != t->ppl) {
     t->ppl = particles_per_lane;
-    if (t->gpu) {  // items and their default order rebuilt on the device  // rebuild the work items on the device
-      const og::GpuBuild a = gpu_args(t, t->sys_off.data(), nullptr, nullptr);
-      cudaError_t e = og::gpu_build_items(a, nullptr);
-      if (e != cudaSuccess) return fail(OCTGRAV_ERR_CUDA, "GPU item build failed: %s", cudaGetErrorString(e));
-      int64_t res[og::GB_COUNT];
-      if (int rc = gpu_result(t, nullptr, res)) return rc;
-      t->n_items = res[og::GB_NITEMS];
-      t->ordered = true;
-      t->host_valid = false;
-      if (int rc = t->dev->counts.reserve(t->n_items * sizeof(int2))) return rc;
-    } else {
-      make_items(t);
-      t->uploaded = false;
-    }
+    return rebuild_items(t);
   }
   return OCTGRAV_OK;
 }

@@ -395,8 +395,14 @@ struct octgrav_sim {
 
 namespace ogh {
 
+// Work items are cut with og::next_item_size's split except under a learned
+// criterion, whose network step a split item would repeat.
+inline bool item_split(const octgrav_tree* t) { return !t->learned; }
 // Work items of every group, and their default processing order.
 void make_items(octgrav_tree* t);
+// make_items again (host-built tree) or the GPU build's item step (GPU-built
+// tree), after a change of ppl or of item_split(t); drops a captured graph.
+int rebuild_items(octgrav_tree* t);
 // Concatenate the systems' trees into the device-array images;
 // particles_done: a one-system build already wrote perm, perm32 and parts.
 int assemble(octgrav_tree* t, std::vector<SysTree>& sys, bool particles_done = false);

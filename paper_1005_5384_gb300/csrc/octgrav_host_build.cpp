@@ -429,15 +429,18 @@ int build_system(const double* pos, const double* mass, int64_t n, int n_leaf, i
   return OCTGRAV_OK;
 }
 
-// Split every group into work items of at most 32 * ppl particles.
+// Split every group into work items of at most 32 * ppl particles, cut by
+// og::next_item_size (a 33..56-particle rest split in two unless the tree has
+// a learned criterion, which would repeat its network for both pieces).
 void make_items(octgrav_tree* t) {
   const int item_max = 32 * t->ppl;
+  const bool split = item_split(t);
   const int64_t ng = static_cast<int64_t>(t->group_cell.size());
   t->group_item.assign(ng, 0);
   int64_t ni = 0;
   for (int64_t g = 0; g < ng; ++g) {
     t->group_item[g] = static_cast<int32_t>(ni);
-    ni += (t->pcount[t->group_cell[g]] + item_max - 1) / item_max;
+    ni += og::item_count(t->pcount[t->group_cell[g]], item_max, split);
   }
   t->items.resize(ni);
   t->ibox.resize(4 * ni);
@@ -467,9 +470,9 @@ void make_items(octgrav_tree* t) {
       std::memcpy(&grange.y, &gr[1], 4);
       grange.z = grange.w = 0.f;
       int64_t k = t->group_item[g];
-      for (int64_t off = 0; off < cnt; off += item_max, ++k) {
-        t->items[k] = make_int4(static_cast<int>(root), static_cast<int>(pf + off),
-                                static_cast<int>(std::min<int64_t>(item_max, cnt - off)), s);
+      for (int64_t off = 0, sz; off < cnt; off += sz, ++k) {
+        sz = og::next_item_size(static_cast<int>(cnt - off), item_max, split);
+        t->items[k] = make_int4(static_cast<int>(root), static_cast<int>(pf + off), static_cast<int>(sz), s);
         t->ibox[4 * k] = bx[0];
         t->ibox[4 * k + 1] = bx[1];
         t->ibox[4 * k + 2] = bx[2];

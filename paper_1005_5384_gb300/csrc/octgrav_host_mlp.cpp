@@ -24,8 +24,9 @@ int octgrav_set_criterion(octgrav_tree* t, const float* record, double tau, doub
                           double theta_fb) {
   if (!t) return fail(OCTGRAV_ERR_ARG, "tree is NULL");
   if (!record) {
+    if (!t->learned) return OCTGRAV_OK;
     t->learned = false;
-    return OCTGRAV_OK;
+    return ogh::rebuild_items(t);  // plain-criterion items (item_split)
   }
   if (!(theta_lo >= 0 && theta_hi >= theta_lo && theta_fb >= 0) || !std::isfinite(tau) || !std::isfinite(theta_hi))
     return fail(OCTGRAV_ERR_ARG, "need 0 <= theta_lo <= theta_hi, theta_fb >= 0 and a finite tau");
@@ -72,11 +73,12 @@ int octgrav_set_criterion(octgrav_tree* t, const float* record, double tau, doub
   if (rc) return rc;
   CUDA_TRY(cudaMemcpy(t->dev->mlp.p, &D, sizeof D, cudaMemcpyHostToDevice));
   CUDA_TRY(cudaGetDevice(&t->mlp_device));
+  const bool was = t->learned;
   t->learned = true;
   t->theta_lo = static_cast<float>(theta_lo);
   t->theta_hi = static_cast<float>(theta_hi);
   t->theta_fb = static_cast<float>(theta_fb);
-  return OCTGRAV_OK;
+  return was ? OCTGRAV_OK : ogh::rebuild_items(t);  // learned-criterion items (item_split)
 }
 
 // Host copy of the walk's FP32 opening test (same operations, no contraction).

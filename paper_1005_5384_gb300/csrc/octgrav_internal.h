@@ -10,6 +10,29 @@ namespace og {
 
 struct MlpDevice;
 
+#ifdef __CUDACC__
+#define OG_HD __host__ __device__
+#else
+#define OG_HD
+#endif
+
+// Particles of the next work item of a group with `rest` particles left:
+// item_max, or all of them when fewer. With `split` (item_max 64, two
+// particles per lane) a rest of 33..56 particles becomes an item of 32 (two
+// list slices of 16 lanes) followed by one of rest - 32 (more slices): a
+// single item of that size leaves 4..15 lanes of its warp idle during the
+// whole evaluation. Host and GPU builds both cut their items with this rule.
+OG_HD inline int next_item_size(int rest, int item_max, bool split) {
+  if (split && item_max == 64 && rest > 32 && rest <= 56) return 32;
+  return rest < item_max ? rest : item_max;
+}
+// Number of items next_item_size cuts a group of cnt particles into: the full
+// items first, then the rest r = cnt mod item_max as one item or two.
+OG_HD inline int item_count(int cnt, int item_max, bool split) {
+  const int r = cnt % item_max;
+  return cnt / item_max + (r > 0) + (r > 0 && next_item_size(r, item_max, split) < r);
+}
+
 // Device status bits (OR-ed into the status word by the kernel).
 enum : int {
   ST_STACK = 1,    // node stack overflow in a walk
@@ -176,6 +199,7 @@ struct GpuBuild {
   int n_sys;
   const int64_t* offsets;
   int n_leaf, n_group, item_max;
+  int item_split;  // cut items with next_item_size(..., split = item_split != 0)
   int max_level;  // deepest level the level loop builds (21 = no cap)
   int64_t cap;
   void* scratch;

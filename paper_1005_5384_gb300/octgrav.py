@@ -367,13 +367,15 @@ class Tree:
 
     def set_criterion(self, record=None, tau: float = -3.5, theta_lo: float = 0.5, theta_hi: float = 4.0,
                       theta_fb: float = 1.0):
-        """Enable the learned criterion (record from mlp_train) or restore the plain test (None)."""
+        """Enable the learned criterion (record from mlp_train) or restore the plain test (None).
+        Switching between the two cuts the work items again (n_items may change)."""
         if record is None:
             _check(load().octgrav_set_criterion(self._h, None, 0.0, 0.0, 0.0, 0.0))
-            return
-        r = np.ascontiguousarray(record, dtype=np.float32)
-        _check(load().octgrav_set_criterion(self._h, _p(r), float(tau), float(theta_lo), float(theta_hi),
-                                            float(theta_fb)))
+        else:
+            r = np.ascontiguousarray(record, dtype=np.float32)
+            _check(load().octgrav_set_criterion(self._h, _p(r), float(tau), float(theta_lo), float(theta_hi),
+                                                float(theta_fb)))
+        self.stats = self._stats()
 
     def capture_graph(self, eps: float, theta: float, out, G: float = 1.0, stream=None):
         """Capture one forces_device call into a CUDA graph (needs a non-default stream)."""

@@ -133,6 +133,44 @@ def test_item_split_for_large_groups():
     assert T.item_info()["count"].max() <= 32
 
 
+def _expected_cuts(c, item_max, split):
+    """Items of a group of c particles: full items, then the rest r whole or,
+    with split at 64 per item, as 32 + (r - 32) when r is 33..56."""
+    out = [item_max] * (c // item_max)
+    r = c % item_max
+    if r:
+        out += [32, r - 32] if split and item_max == 64 and 32 < r <= 56 else [r]
+    return out
+
+
+def _check_item_cuts(T, item_max, split):
+    info = T.item_info()
+    keys, first, count = info["group_key"], info["first"], info["count"]
+    starts = np.flatnonzero(np.r_[True, keys[1:] != keys[:-1]])
+    ends = np.r_[starts[1:], len(keys)]
+    n_cut = 0
+    for a, b in zip(starts, ends):
+        c = int(count[a:b].sum())
+        assert list(count[a:b]) == _expected_cuts(c, item_max, split)
+        assert np.array_equal(first[a:b], first[a] + np.r_[0, np.cumsum(count[a:b - 1])])
+        n_cut += b - a > (c + item_max - 1) // item_max
+    return n_cut
+
+
+def test_items_follow_the_cutting_rule():
+    """Two particles per lane: a 33..56-particle rest is cut into 32 + the
+    rest; one particle per lane: items of 32 and the rest, nothing else."""
+    pos, m = W.plummer(20000, seed=4)
+    T = G.Tree.build(pos, m, 16, 128)
+    n_cut = _check_item_cuts(T, 64, True)
+    assert n_cut > 10  # the case occurs on this input
+    assert T.stats["n_items"] == len(T.item_info()["count"])
+    T.set_launch(1)
+    assert _check_item_cuts(T, 32, True) == 0
+    T.set_launch(2)
+    assert _check_item_cuts(T, 64, True) == n_cut
+
+
 def test_host_builds_from_threads_agree():
     """Host builds started from four threads at once share the library's thread
     pool (one parallel region at a time) and give the single-thread tree: the

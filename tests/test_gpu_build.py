@@ -394,3 +394,48 @@ def test_refit_refusals(torch):
     with pytest.raises(G.OctgravError) as e:
         B.refit(bad, m)
     assert e.value.code == G.ERR_NONFINITE
+
+
+def _runs(info):
+    k = info["group_key"]
+    starts = np.flatnonzero(np.r_[True, k[1:] != k[:-1]])
+    return starts, np.r_[starts[1:], len(k)]
+
+
+def test_learned_criterion_keeps_rests_whole(torch):
+    """Setting a learned criterion cuts the items again without the 32 + rest
+    split (one item per 33..56-particle rest), on the host-built and the
+    GPU-built tree alike (the same items, byte for byte); a new record keeps
+    them; clearing the criterion restores the split items; a graph captured
+    before is dropped; the forces of the plain criterion are unchanged."""
+    import oracle.mlp as M
+    pos, m = W.plummer(30000, seed=12)
+    A = G.Tree.build(pos, m, 16, 128)
+    B = G.Tree.build_gpu(pos, m, 16, 128)
+    plain = A.item_info()
+    f0 = _device_forces(torch, B, 0.01, 0.6)
+    s = torch.cuda.Stream()
+    out = torch.empty((B.n, 4), dtype=torch.float32, device="cuda")
+    B.capture_graph(0.01, 0.6, out, stream=s)
+    rec = np.concatenate([np.zeros(12), np.ones(12), np.full(12, -1e3), np.full(12, 1e3), M.init(2)]).astype(np.float32)
+    for T in (A, B):
+        T.set_criterion(rec, tau=-3.0, theta_lo=0.5, theta_hi=1.0, theta_fb=0.7)
+    ia, ib = A.item_info(), B.item_info()
+    for k in ia:
+        assert np.array_equal(ia[k], ib[k]), k
+    assert A.stats == B.stats and A.stats["n_items"] < len(plain["count"])
+    for a, b in zip(*_runs(ia)):
+        c = int(ia["count"][a:b].sum())
+        assert b - a == (c + 63) // 64 and ia["count"][a:b].max() <= 64
+    with pytest.raises(G.OctgravError) as e:
+        B.launch_graph(stream=s)
+    assert e.value.code == G.ERR_STATE
+    B.set_criterion(rec, tau=-2.0, theta_lo=0.5, theta_hi=1.0, theta_fb=0.7)
+    assert np.array_equal(B.item_info()["count"], ib["count"])
+    for T in (A, B):
+        T.set_criterion(None)
+        back = T.item_info()
+        for k in plain:
+            assert np.array_equal(back[k], plain[k]), k
+    assert np.array_equal(_device_forces(torch, B, 0.01, 0.6), f0)
+
