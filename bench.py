@@ -518,7 +518,7 @@ def learned_leg(torch, G, a, flush, stream, peak, steps, ng=64, train_groups=128
     th = bisect(med, 0.3, 2.0)
     e_th = med(th)
     c_th = T.interaction_counts()
-    ni_th = T.stats["n_items"]  # 33..56-particle rests cut 32 + rest
+    ni_th = T.stats["n_items"]  # 33..48-particle rests cut 32 + rest
     T.balance(stream=stream)  # both walks timed longest first, from their own last launch
     ms_th = time_kernel(torch, lambda: T.forces_device(0.01, th, out, stream=stream), flush, steps, stream)
     T.balance(0)

@@ -302,8 +302,8 @@ int octgrav_tree_cell_props(const octgrav_tree *t, double *bmin, double *bmax, d
  * system index (arrays of n_items entries; any may be NULL). A group of c
  * particles is cut into items of 32*ppl particles (octgrav_set_launch) and one
  * item for the rest r = c mod 32*ppl; with two particles per lane and the
- * plain criterion a rest of 33..56 becomes two items, 32 and r - 32
- * (a 33..56-particle item would leave lanes of its warp idle). Under a learned
+ * plain criterion a rest of 33..48 becomes two items, 32 and r - 32
+ * (a 33..48-particle item would leave lanes of its warp idle). Under a learned
  * criterion (octgrav_set_criterion) the rest stays whole: the network step
  * would run for both pieces. The host and the GPU build cut the same items. */
 int octgrav_item_info(const octgrav_tree *t, uint64_t *group_key, int64_t *first,

@@ -430,7 +430,7 @@ int build_system(const double* pos, const double* mass, int64_t n, int n_leaf, i
 }
 
 // Split every group into work items of at most 32 * ppl particles, cut by
-// og::next_item_size (a 33..56-particle rest split in two unless the tree has
+// og::next_item_size (a 33..48-particle rest split in two unless the tree has
 // a learned criterion, which would repeat its network for both pieces).
 void make_items(octgrav_tree* t) {
   const int item_max = 32 * t->ppl;

@@ -18,12 +18,14 @@ struct MlpDevice;
 
 // Particles of the next work item of a group with `rest` particles left:
 // item_max, or all of them when fewer. With `split` (item_max 64, two
-// particles per lane) a rest of 33..56 particles becomes an item of 32 (two
-// list slices of 16 lanes) followed by one of rest - 32 (more slices): a
-// single item of that size leaves 4..15 lanes of its warp idle during the
-// whole evaluation. Host and GPU builds both cut their items with this rule.
+// particles per lane) a rest of 33..48 particles becomes an item of 32 (two
+// list slices of 16 lanes) followed by one of rest - 32 <= 16 (four or more
+// slices): a single item of that size leaves 8..15 lanes of its warp idle
+// during the whole evaluation, which costs more than the second item's walk.
+// (A rest of 49..56 would leave a second item of two or three slices and gains
+// less than that walk costs.) Host and GPU builds both cut with this rule.
 OG_HD inline int next_item_size(int rest, int item_max, bool split) {
-  if (split && item_max == 64 && rest > 32 && rest <= 56) return 32;
+  if (split && item_max == 64 && rest > 32 && rest <= 48) return 32;
   return rest < item_max ? rest : item_max;
 }
 // Number of items next_item_size cuts a group of cnt particles into: the full

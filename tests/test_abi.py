@@ -135,11 +135,11 @@ def test_item_split_for_large_groups():
 
 def _expected_cuts(c, item_max, split):
     """Items of a group of c particles: full items, then the rest r whole or,
-    with split at 64 per item, as 32 + (r - 32) when r is 33..56."""
+    with split at 64 per item, as 32 + (r - 32) when r is 33..48."""
     out = [item_max] * (c // item_max)
     r = c % item_max
     if r:
-        out += [32, r - 32] if split and item_max == 64 and 32 < r <= 56 else [r]
+        out += [32, r - 32] if split and item_max == 64 and 32 < r <= 48 else [r]
     return out
 
 
@@ -158,7 +158,7 @@ def _check_item_cuts(T, item_max, split):
 
 
 def test_items_follow_the_cutting_rule():
-    """Two particles per lane: a 33..56-particle rest is cut into 32 + the
+    """Two particles per lane: a 33..48-particle rest is cut into 32 + the
     rest; one particle per lane: items of 32 and the rest, nothing else."""
     pos, m = W.plummer(20000, seed=4)
     T = G.Tree.build(pos, m, 16, 128)

@@ -404,7 +404,7 @@ def _runs(info):
 
 def test_learned_criterion_keeps_rests_whole(torch):
     """Setting a learned criterion cuts the items again without the 32 + rest
-    split (one item per 33..56-particle rest), on the host-built and the
+    split (one item per 33..48-particle rest), on the host-built and the
     GPU-built tree alike (the same items, byte for byte); a new record keeps
     them; clearing the criterion restores the split items; a graph captured
     before is dropped; the forces of the plain criterion are unchanged."""
