@@ -348,6 +348,29 @@ def test_list_parity_plummer_1m_n_group_512(torch):
     _list_parity(T, [O.Tree(pos, m, 16, 512)], 0.5, items)
 
 
+def test_list_parity_plummer_1m_n_group_256_cut_items(torch):
+    """C2 as the benchmark runs it now (the autotuner's N_group 256, items
+    longest first): a group's 33..48-particle rest is cut into 32 + the rest,
+    and both pieces walk the group's lists. The sample holds both pieces of
+    20 cut groups besides 300 random items."""
+    pos, m = W.plummer(1 << 20, seed=1)
+    T = G.Tree.build(pos, m, 16, 256)
+    out = torch.empty((T.n, 4), dtype=torch.float32, device="cuda")
+    T.forces_device(0.01, 0.5, out)
+    T.balance()
+    info = T.item_info()
+    k, cnt = info["group_key"], info["count"]
+    starts = np.flatnonzero(np.r_[True, k[1:] != k[:-1]])
+    ends = np.r_[starts[1:], len(k)]
+    cut = [(a, b) for a, b in zip(starts, ends)
+           if b - a >= 2 and cnt[b - 2] == 32 and 1 <= cnt[b - 1] <= 16 and int(cnt[a:b].sum()) % 64 != 0]
+    assert len(cut) > 100
+    pick = np.random.default_rng(5).choice(len(cut), 20, replace=False)
+    pieces = [i for j in pick for i in (cut[j][1] - 2, cut[j][1] - 1)]
+    items = np.union1d(_sample_items(T, 300, 24), pieces)
+    _list_parity(T, [O.Tree(pos, m, 16, 256)], 0.5, items)
+
+
 def test_list_parity_clustered_4m(torch):
     """C3: 64 Plummer spheres, 4M particles, eps = 1e-3 (lists do not depend on eps)."""
     pos, m = W.clustered()
