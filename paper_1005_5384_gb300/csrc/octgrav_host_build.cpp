@@ -422,8 +422,28 @@ int build_system(const double* pos, const double* mass, int64_t n, int n_leaf, i
       T.groups.insert(T.groups.end(), found[k].begin(), found[k].end());
     }
   }
-  std::sort(T.groups.begin(), T.groups.end(),
-            [&](int32_t a, int32_t b) { return T.pfirst[a] < T.pfirst[b]; });
+  // Order the groups by first particle. They were found level by level, and a
+  // level's cells are in key order, i.e. in first-particle order: the list is a
+  // few sorted runs (one per level), merged pairwise here (first particles are
+  // distinct, so this is the order a full sort would give).
+  {
+    auto by_first = [&](int32_t a, int32_t b) { return T.pfirst[a] < T.pfirst[b]; };
+    std::vector<size_t> bounds = {0};
+    for (size_t i = 1; i < T.groups.size(); ++i)
+      if (by_first(T.groups[i], T.groups[i - 1])) bounds.push_back(i);
+    bounds.push_back(T.groups.size());
+    while (bounds.size() > 2) {
+      std::vector<size_t> next = {0};
+      const size_t runs = bounds.size() - 1;
+      for (size_t k = 0; k < runs; k += 2) {
+        if (k + 1 < runs)
+          std::inplace_merge(T.groups.begin() + bounds[k], T.groups.begin() + bounds[k + 1],
+                             T.groups.begin() + bounds[k + 2], by_first);
+        next.push_back(bounds[std::min(k + 2, runs)]);
+      }
+      bounds.swap(next);
+    }
+  }
   for (int32_t g : T.groups) T.max_group = std::max(T.max_group, T.pcount[g]);
   mark(6);
   return OCTGRAV_OK;
