@@ -66,18 +66,24 @@ inline uint64_t spread21(uint64_t v) {
   return v;
 }
 
-// Stable LSD radix sort of (key, val) by key (63 significant bits, 9-bit digits).
+// Stable sort of (key, val) by key (63 significant bits). An LSD radix sort
+// with 9-bit digits orders the top 45 bits (five passes instead of seven);
+// runs of keys equal in those bits (particles sharing a cell of level 15, rare
+// unless particles nearly coincide) are then sorted stably by the low 18 bits.
+// The result is the order of a full stable sort: by key, equal keys in input
+// order.
+constexpr int kLowBits = 18;
 void radix_sort(hvec<uint64_t>& key, hvec<uint32_t>& val, hvec<uint64_t>& k2, hvec<uint32_t>& v2,
                 bool parallel) {
   const int64_t n = static_cast<int64_t>(key.size());
   k2.resize(n);
   v2.resize(n);
-  constexpr int BITS = 9, B = 1 << BITS, PASSES = (63 + BITS - 1) / BITS;
+  constexpr int BITS = 9, B = 1 << BITS, PASSES = (63 - kLowBits + BITS - 1) / BITS;
   const int T = parallel ? std::max(1, std::min<int>(Pool::get().size(), static_cast<int>(n / 65536))) : 1;
   std::vector<int64_t> hist(static_cast<size_t>(T) * B);
   const int64_t step = (n + T - 1) / T;
   for (int pass = 0; pass < PASSES; ++pass) {
-    const int sh = pass * BITS;
+    const int sh = kLowBits + pass * BITS;
     auto body_hist = [&](int t) {
       int64_t* h = &hist[static_cast<size_t>(t) * B];
       std::fill(h, h + B, 0);
@@ -105,6 +111,39 @@ void radix_sort(hvec<uint64_t>& key, hvec<uint32_t>& val, hvec<uint64_t>& k2, hv
     key.swap(k2);
     val.swap(v2);
   }
+  // Runs of equal top bits, each found by the chunk holding its first key (a
+  // read-only pass), then sorted by their chunk (disjoint ranges).
+  const int chunks = T;
+  const int64_t cstep = (n + chunks - 1) / chunks;
+  std::vector<std::vector<std::pair<int64_t, int64_t>>> runs(chunks);
+  auto top = [&](int64_t i) { return key[i] >> kLowBits; };
+  auto body_find = [&](int t) {
+    const int64_t lo = t * cstep, hi = std::min(n, lo + cstep);
+    for (int64_t i = lo; i < hi; ++i) {
+      if (i > 0 && top(i) == top(i - 1)) continue;  // not the first key of its run
+      int64_t j = i + 1;
+      while (j < n && top(j) == top(i)) ++j;
+      if (j - i > 1) runs[t].emplace_back(i, j);
+      i = j - 1;
+    }
+  };
+  if (chunks > 1) Pool::get().run(chunks, body_find); else body_find(0);
+  auto body_fix = [&](int t) {
+    std::vector<std::pair<uint64_t, uint32_t>> r;
+    for (const auto& [i, j] : runs[t]) {
+      r.clear();
+      for (int64_t k = i; k < j; ++k) r.emplace_back(key[k], val[k]);
+      std::stable_sort(r.begin(), r.end(),
+                       [](const std::pair<uint64_t, uint32_t>& x, const std::pair<uint64_t, uint32_t>& y) {
+                         return x.first < y.first;
+                       });
+      for (int64_t k = i; k < j; ++k) {
+        key[k] = r[k - i].first;
+        val[k] = r[k - i].second;
+      }
+    }
+  };
+  if (chunks > 1) Pool::get().run(chunks, body_fix); else body_fix(0);
 }
 
 int build_system(const double* pos, const double* mass, int64_t n, int n_leaf, int n_group,
