@@ -131,6 +131,20 @@ void radix_sort(hvec<uint64_t>& key, hvec<uint32_t>& val, hvec<uint64_t>& k2, hv
   auto body_fix = [&](int t) {
     std::vector<std::pair<uint64_t, uint32_t>> r;
     for (const auto& [i, j] : runs[t]) {
+      if (j - i <= 32) {  // the usual case, two or three keys: insertion sort (stable)
+        for (int64_t a = i + 1; a < j; ++a) {
+          const uint64_t k = key[a];
+          const uint32_t v = val[a];
+          int64_t b = a;
+          for (; b > i && key[b - 1] > k; --b) {
+            key[b] = key[b - 1];
+            val[b] = val[b - 1];
+          }
+          key[b] = k;
+          val[b] = v;
+        }
+        continue;
+      }
       r.clear();
       for (int64_t k = i; k < j; ++k) r.emplace_back(key[k], val[k]);
       std::stable_sort(r.begin(), r.end(),

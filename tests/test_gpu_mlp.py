@@ -176,7 +176,7 @@ def test_learned_criterion_beats_theta_at_equal_median_error(torch):
     T = G.Tree.build(pos, m, 16, 256)
     out = torch.empty((T.n, 4), dtype=torch.float32, device="cuda")
     samp = W.sample_indices(T.n, 1024, seed=23)
-    ad, _ = O.direct(pos, m, 0.01, targets=samp)  # the judge: FP64 direct sums of the oracle
+    ad, _ = O.direct(pos, m, 0.01, targets=samp)  # the error reference: FP64 direct sums of the oracle
     th = _bisect(lambda x: _median_err(T, torch, out, 0.01, samp, ad, x), 0.3, 2.0, iters=14)
     e_th = _median_err(T, torch, out, 0.01, samp, ad, th)
     f_th = T.interaction_counts()["flops"]
