@@ -223,12 +223,20 @@ int build_system(const double* pos, const double* mass, int64_t n, int n_leaf, i
   hvec<uint32_t>& idx = T.perm;
   code.resize(n);
   idx.resize(n);
+  const double rscale = (1.0 / side) * scale;
   parallel_for(n, grain, [&](int64_t a, int64_t b) {
     for (int64_t i = a; i < b; ++i) {
       uint64_t q[3];
       for (int d = 0; d < 3; ++d) {
-        const double u = (pos[3 * i + d] - lo[d]) / side;
-        const double v = std::floor(u * scale);
+        // q = floor(fl(fl(x - lo) / side) * 2^21) without the division where
+        // it is safe: c = fl(x - lo) * rscale lies within 4 ulp (< 2^-29, for
+        // c <= 2^21) of fl(fl(x - lo) / side) * 2^21, so the floors agree
+        // unless an integer lies within 2^-28 of c; then the division decides
+        // (the GPU build takes the same steps)
+        const double dx = pos[3 * i + d] - lo[d];
+        const double c = dx * rscale;
+        double v = std::floor(c - 0x1p-28);
+        if (v != std::floor(c + 0x1p-28)) v = std::floor((dx / side) * scale);
         q[d] = v <= 0 ? 0 : (v >= static_cast<double>(qmax) ? qmax : static_cast<uint64_t>(v));
       }
       code[i] = spread21(q[0]) | (spread21(q[1]) << 1) | (spread21(q[2]) << 2);
