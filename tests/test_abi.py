@@ -171,6 +171,27 @@ def test_items_follow_the_cutting_rule():
     assert _check_item_cuts(T, 64, True) == n_cut
 
 
+def test_item_cut_at_the_rule_boundaries():
+    """Nine clumps of coincident particles (each a leaf at the depth limit, and
+    with N_leaf = N_group = 4 a group of its own) whose counts sit on both sides
+    of every bound of the cutting rule (32, 48, 64 per item)."""
+    counts = [32, 33, 48, 49, 56, 64, 65, 80, 81]
+    rng = np.random.default_rng(8)
+    centres = rng.random((len(counts), 3))
+    pos = np.concatenate([np.tile(c, (k, 1)) for c, k in zip(centres, counts)])
+    m = np.full(len(pos), 1.0 / len(pos))
+    T = G.Tree.build(pos, m, 4, 4)
+    assert T.stats["n_groups"] == len(counts)
+    info = T.item_info()
+    k = info["group_key"]
+    starts = np.flatnonzero(np.r_[True, k[1:] != k[:-1]])
+    ends = np.r_[starts[1:], len(k)]
+    got = sorted(tuple(int(c) for c in info["count"][a:b]) for a, b in zip(starts, ends))
+    want = sorted(tuple(_expected_cuts(c, 64, True)) for c in counts)
+    assert got == want
+    assert (32, 1) in got and (32, 16) in got and (49,) in got and (64, 1) in got and (64, 16) in got and (64, 17) in got
+
+
 def test_host_builds_from_threads_agree():
     """Host builds started from four threads at once share the library's thread
     pool (one parallel region at a time) and give the single-thread tree: the
