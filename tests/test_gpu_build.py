@@ -57,6 +57,14 @@ def _coincident(n):
     return np.tile([[0.25, -0.5, 0.125]], (n, 1)), np.full(n, 1.0 / n)
 
 
+def _clumps():
+    """Clumps of coincident particles whose sizes sit on the work-item cut's bounds."""
+    counts = [32, 33, 48, 49, 56, 64, 65, 80, 81]
+    centres = np.random.default_rng(8).random((len(counts), 3))
+    pos = np.concatenate([np.tile(c, (k, 1)) for c, k in zip(centres, counts)])
+    return pos, np.full(len(pos), 1.0 / len(pos))
+
+
 CASES = {
     "plummer_16k": (lambda: W.plummer(16384, seed=1), 16, 16, 0.01),
     "plummer_100k_ng64": (lambda: W.plummer(100000, seed=2), 16, 64, 0.01),
@@ -67,6 +75,7 @@ CASES = {
     "one_particle": (lambda: (np.array([[0.3, 0.2, 0.1]]), np.array([1.0])), 1, 1, 0.01),
     "two_coincident": (lambda: _coincident(2), 1, 1, 0.01),
     "coincident_100": (lambda: _coincident(100), 4, 8, 0.01),
+    "clumps_at_item_bounds": (_clumps, 4, 4, 0.01),
     "ragged_37": (lambda: W.plummer(37, seed=7), 4, 8, 0.01),
     "chunk_edges_8193": (lambda: W.plummer(8193, seed=8), 16, 32, 0.01),
     "galaxy_60k": (lambda: W.galaxy(60000, seed=9), 16, 64, 0.01),
