@@ -69,12 +69,13 @@ def parse():
                          "by the costs of the first warm-up launch")
     ap.add_argument("--sweep-n", default="30000,100000,300000,1000000",
                     help="particle numbers of --leg accuracy (comma separated)")
-    ap.add_argument("--leg", default="", choices=["", "learned", "build", "accuracy"],
+    ap.add_argument("--leg", default="", choices=["", "learned", "build", "accuracy", "small"],
                     help="learned: train the criterion on the 1M sphere+disc and launch the learned walk "
                          "twice (a small driver for profilers; prints the interaction counts); build: "
                          "--warmup + --steps GPU tree builds of the workload (prints their wall times); "
                          "accuracy: error distribution and throughput over theta, N and N_leaf on the "
-                         "galaxy stand-in (one JSON line per configuration, then the fitted theta slopes)")
+                         "galaxy stand-in (one JSON line per configuration, then the fitted theta slopes); "
+                         "small: C1 with the autotuner's launch shape, one launch then four (a profiler driver)")
     return ap.parse_args()
 
 
@@ -546,6 +547,26 @@ def learned_leg(torch, G, a, flush, stream, peak, steps, ng=64, train_groups=128
             "speedup_learned_over_theta": ms_th / ms_ml}
 
 
+def run_small_driver():
+    """C1 as the autotuner launches it (16k Plummer, N_group 128, one particle per
+    lane, lists split over 4 warps): one launch, the order by its costs, then four
+    more (a small driver for profilers)."""
+    import torch
+    from paper_1005_5384_gb300 import octgrav as G
+    n = 16384
+    pos, m = W.plummer(n, seed=1)
+    T = G.Tree.build(pos, m, 16, 128)
+    T.set_launch(1)
+    T.set_split(4)
+    out = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    T.forces_device(0.01, 0.5, out)
+    T.balance()
+    for _ in range(4):
+        T.forces_device(0.01, 0.5, out)
+    torch.cuda.synchronize()
+    print(json.dumps({"leg": "small", "status": T.status(), "counts": T.interaction_counts()}), flush=True)
+
+
 def run_learned_driver():
     """Train on the sphere+disc (seed 6); on seed 5 launch the plain walk at
     theta 0.93 (its median-1e-3 point) once, then the learned walk twice."""
@@ -717,6 +738,9 @@ def main():
         return
     if a.leg == "learned":
         run_learned_driver()
+        return
+    if a.leg == "small":
+        run_small_driver()
         return
     if a.leg == "build":
         run_build_driver(a)
