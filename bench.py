@@ -599,7 +599,7 @@ def run_learned_driver():
     T.forces_device(0.01, 0.93, out)
     torch.cuda.synchronize()
     plain = T.interaction_counts()
-    T.set_criterion(rec, tau=-3.23, theta_lo=0.85, theta_hi=1.5, theta_fb=1.0)  # the C5 leg's band and tau
+    T.set_criterion(rec, tau=-3.6, theta_lo=0.85, theta_hi=1.5, theta_fb=1.0)  # the C5 leg's band and tau
     for _ in range(2):
         T.forces_device(0.01, 0.5, out)
     torch.cuda.synchronize()
