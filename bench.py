@@ -478,7 +478,7 @@ def extras(torch, G, a, pos, m, T, out, flush, stream, peak, steps):
     # N_group 256: the fastest group size for both walks here (64: 403 / 454 M forces/s,
     # 512: 439 / 491 M with 96 training groups)
     res["learned_criterion_sphere_disc_1M"] = learned_leg(torch, G, a, flush, stream, peak, steps, ng=256,
-                                                          train_groups=64)
+                                                          train_groups=256)
     return res
 
 

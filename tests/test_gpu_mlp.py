@@ -161,7 +161,7 @@ def _time_events(T, torch, out, eps, theta, reps=9):
 
 def test_learned_criterion_beats_theta_at_equal_median_error(torch):
     """C5 as the benchmark runs it: the network trained on another seed of the
-    same kind of system (64 groups; its samples with cell size over distance
+    same kind of system (256 groups; their samples with cell size over distance
     at least 0.7 theta_lo), N_group 256; the plain walk and the learned
     walk each tuned to a median Delta a/a of 1e-3 against FP64 direct sums at
     1024 particles; both timed with CUDA events after ordering their items
@@ -169,7 +169,7 @@ def test_learned_criterion_beats_theta_at_equal_median_error(torch):
     at least 5 % faster (measured: ~38 % and ~16-20 %)."""
     tpos, tm = W.sphere_disc(1 << 20, seed=6)
     TT = G.Tree.build(tpos, tm, 16, 256)
-    groups = np.sort(np.random.default_rng(0).choice(TT.stats["n_groups"], 64, replace=False))
+    groups = np.sort(np.random.default_rng(0).choice(TT.stats["n_groups"], 256, replace=False))
     f, lab, _ = TT.mlp_samples(groups, 0.35, 0.01)
     keep = f[:, 3] >= 0.7 * BAND["theta_lo"]  # pairs the plain test accepts never reach the network
     rec, _ = G.mlp_train(np.ascontiguousarray(f[keep]), np.ascontiguousarray(lab[keep]), steps=3000, batch=4096,
